@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here touches the CUDA path: the oracle is checked against the paper's
+worked examples (Figures 4 and 6), hand-worked Eq. (1) tables, closed forms,
+invariants and brute-force enumeration of every monotone alignment.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import brute
+from paper_1512_01641_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _identity_sim(rows, cols):
+    return np.array([[1.0 if r == c else 0.0 for c in cols] for r in rows])
+
+
+def _path_cells(moves, N, M):
+    """0-based cells visited by the path (the X marks of Figures 3-4)."""
+    i = j = 0
+    cells = []
+    for m in moves[::-1]:
+        if m == oracle.MOVE_DIAG:
+            i, j = i + 1, j + 1
+        elif m == oracle.MOVE_UP:
+            i += 1
+        else:
+            j += 1
+        cells.append((i - 1 if i else 0, j - 1 if j else 0))
+    return cells
+
+
+# ---------------------------------------------------------------- Section 5.1
+def test_figure4_path_and_tie_rule():
+    g = _load("fig4_nw.json")
+    s = _identity_sim(g["rows"], g["cols"])
+    H, mv, diag = oracle.nw(s, g["gap"])
+    assert H[-1, -1] == g["score"]
+    assert diag == [tuple(x) for x in g["diag"]]
+    assert _path_cells(mv, 5, 5) == [tuple(x) for x in g["path_cells"]]
+    # the printed two-line alignment
+    cols, rows = [], []
+    i = j = 0
+    for m in mv[::-1]:
+        if m == oracle.MOVE_DIAG:
+            cols.append(g["cols"][j]); rows.append(g["rows"][i]); i += 1; j += 1
+        elif m == oracle.MOVE_UP:
+            cols.append("-"); rows.append(g["rows"][i]); i += 1
+        else:
+            cols.append(g["cols"][j]); rows.append("-"); j += 1
+    assert cols == g["alignment_cols"] and rows == g["alignment_rows"]
+    # brute force: two optimal alignments exist; the figure shows the one the
+    # UP-first tie rule picks
+    best, arg = brute.hard(s.tolist(), g["gap"])
+    assert best == g["score"] and len(arg) == g["n_optimal_alignments"]
+    assert tuple(map(tuple, g["diag"])) in arg
+
+
+def test_figure6_unique_optimum():
+    g = _load("fig6_nw.json")
+    s = _identity_sim(g["rows"], g["cols"])
+    H, mv, diag = oracle.nw(s, g["gap"])
+    assert H[-1, -1] == g["score"]
+    assert diag == [tuple(x) for x in g["diag"]]
+    best, arg = brute.hard(s.tolist(), g["gap"])
+    assert best == g["score"] and len(arg) == 1 and list(arg[0]) == diag
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_eq1_hand_worked(case):
+    c = _load("eq1_hand.json")["cases"][case]
+    s = np.array([[1.0 if a == b else -1.0 for b in c["cols"]] for a in c["rows"]])
+    H, mv, diag = oracle.nw(s, c["gap"])
+    assert np.array_equal(H, np.array(c["H"], float))
+    assert H[-1, -1] == c["score"]
+    assert diag == [tuple(x) for x in c["diag"]]
+
+
+def test_gap_tie_prefers_up():
+    # H(1,1) = max(-5, -2, -2): UP and LEFT tie; the oracle walks UP first.
+    H, mv, diag = oracle.nw(np.array([[-5.0]]), 1.0)
+    assert H[1, 1] == -2.0 and list(mv) == [oracle.MOVE_UP, oracle.MOVE_LEFT] and diag == []
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_brute_force_hard(seed):
+    rng = np.random.default_rng(seed)
+    N, M = rng.integers(1, 7, size=2)
+    if seed % 2:  # a small value set makes exact ties common
+        s = rng.choice([0.0, 0.25, 0.5, 0.75, 1.0], size=(N, M))
+        p = 0.125
+    else:
+        s = rng.random((N, M))
+        p = float(rng.choice([0.05, 0.3, 0.6]))
+    H, mv, diag = oracle.nw(s, p)
+    best, arg = brute.hard(s.tolist(), p)
+    assert abs(H[-1, -1] - best) < 1e-12
+    assert tuple(diag) in arg
+    assert abs(oracle.path_score(s, p, diag) - best) < 1e-12
+
+
+def test_empty_sides():
+    for N, M in [(0, 0), (0, 4), (3, 0)]:
+        H, mv, diag = oracle.nw(np.zeros((N, M)), 0.3)
+        assert H[-1, -1] == pytest.approx(-0.3 * (N + M)) and diag == []
+        assert len(mv) == N + M
+
+
+@pytest.mark.parametrize("N,M,c,p", [(5, 9, 0.7, 0.3), (12, 4, 0.2, 0.1), (7, 7, -0.1, 0.3), (1, 6, 0.9, 0.5)])
+def test_constant_similarity_closed_form(N, M, c, p):
+    # with c + 2p > 0 a diagonal step beats an UP+LEFT detour, so the optimum
+    # takes min(N,M) diagonals and |N-M| gaps
+    H, _, diag = oracle.nw(np.full((N, M), c), p)
+    assert H[-1, -1] == pytest.approx(min(N, M) * c - p * abs(N - M), abs=1e-12)
+    assert len(diag) == min(N, M)
+
+
+def test_single_row_closed_form():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        M = int(rng.integers(1, 12))
+        s = rng.random((1, M)) * 2 - 1
+        p = float(rng.random())
+        expect = max(s.max() - p * (M - 1), -p * (M + 1))
+        H, _, _ = oracle.nw(s, p)
+        assert H[-1, -1] == pytest.approx(expect, abs=1e-12)
+        H2, _, _ = oracle.nw(s.T.copy(), p)
+        assert H2[-1, -1] == pytest.approx(expect, abs=1e-12)
+
+
+# ---------------------------------------------------------------- features
+def _dic(lists, v_tgt=100):
+    off = np.zeros(len(lists) + 1, np.int32)
+    off[1:] = np.cumsum([len(l) for l in lists])
+    return synth.Dictionary(len(lists), v_tgt, off, np.asarray([t for l in lists for t in sorted(l)], np.int32))
+
+
+def test_counts_hand_worked():
+    # source ids 0..4; 0->{10,11}, 1->{12}, 2->{13,14,15}, 3->{10}, 4->{16}
+    dic = _dic([[10, 11], [12], [13, 14, 15], [10], [16]])
+    # src [0,0,1,3]: positions 0,1 (id 0: 10/11), 2 (id 1: 12), 3 (id 3: 10)
+    # tgt [10,10,12,20]: 10 hits positions 0,1,3; 12 hits position 2
+    assert oracle.counts([0, 0, 1, 3], [10, 10, 12, 20], dic) == (4, 3)
+    # tgt [11,13]: 11 via id 0 (positions 0,1); 13 not a translation of src
+    assert oracle.counts([0, 0, 1, 3], [11, 13], dic) == (2, 1)
+    assert oracle.counts([2, 4], [13, 15, 16, 16], dic) == (2, 4)
+    assert oracle.counts([1], [10, 11], dic) == (0, 0)
+
+
+def test_counts_invariants_and_swap_symmetry():
+    rng = np.random.default_rng(3)
+    v_src, v_tgt = 30, 25
+    lists = [sorted(set(rng.integers(0, v_tgt, size=int(rng.integers(1, 4))).tolist())) for _ in range(v_src)]
+    dic = _dic(lists, v_tgt)
+    # inverse dictionary: target id -> source ids translating to it
+    inv = [[] for _ in range(v_tgt)]
+    for s_id, l in enumerate(lists):
+        for t in l:
+            inv[t].append(s_id)
+    inv = [l if l else [] for l in inv]
+    dinv = _dic(inv, v_src)
+    for _ in range(300):
+        src = sorted(rng.integers(0, v_src, size=int(rng.integers(1, 12))).tolist())
+        tgt = sorted(rng.integers(0, v_tgt, size=int(rng.integers(1, 12))).tolist())
+        ms, mt = oracle.counts(src, tgt, dic)
+        assert 0 <= ms <= len(src) and 0 <= mt <= len(tgt)
+        # t is a translation of s iff s is an inverse translation of t, so the
+        # roles of ms and mt swap
+        ms2, mt2 = oracle.counts(tgt, src, dinv)
+        assert (ms2, mt2) == (mt, ms)
+
+
+def test_counts_full_translation():
+    # a target built by translating every source position hits every position
+    rng = np.random.default_rng(5)
+    b = synth.make_batch(11, 4, v_src=500, v_tgt=500)
+    for _ in range(100):
+        src = np.sort(rng.integers(0, 500, size=int(rng.integers(5, 31)))).astype(np.int32)
+        tgt = np.sort([rng.choice(b.dic.translations(v)) for v in src]).astype(np.int32)
+        assert oracle.counts(src, tgt, b.dic) == (len(src), len(tgt))
+
+
+def test_counts_multiplicity():
+    dic = _dic([[5], [6]])
+    # repeated source tokens count once per position; repeated targets too
+    assert oracle.counts([0, 0, 0, 1], [5, 5], dic) == (3, 2)
+    assert oracle.counts([0], [5, 5, 5, 7], dic) == (1, 3)
+
+
+def test_float32_ratio_equals_rounded_double():
+    # the CUDA path divides in FP32 with IEEE rounding; the oracle rounds the
+    # FP64 quotient.  For every ratio that can occur (counts <= length <= 64)
+    # the two agree bit for bit.
+    a = np.arange(65)
+    A, B = np.meshgrid(a, a[1:], indexing="ij")
+    q32 = A.astype(np.float32) / B.astype(np.float32)
+    q64 = (A.astype(np.float64) / B.astype(np.float64)).astype(np.float32)
+    assert np.array_equal(q32.view(np.uint32), q64.view(np.uint32))
+
+
+def test_features_and_similarity():
+    f = oracle.features(3, 2, 6, 4)
+    assert np.allclose(f, [0.5, 0.5, 2 / 6, 4 / 6], rtol=0, atol=1e-15)
+    w = [4.0, 4.0, -2.0, 1.0]
+    z = 4 * 0.5 + 4 * 0.5 - 2 * (2 / 6) + (4 / 6) - 3.0
+    assert oracle.similarity(f, w, -3.0) == pytest.approx(1 / (1 + math.exp(-z)), rel=1e-15)
+    # |ls-lt|/max + min/max == 1 always
+    for ls in range(1, 40):
+        for lt in range(1, 40):
+            g = oracle.features(0, 0, ls, lt)
+            assert g[2] + g[3] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_mine_links_are_thresholded_path():
+    b = synth.single_pair()
+    w = [4.0, 4.0, -2.0, 1.0]
+    r = oracle.mine(b, w, -3.0, 0.3, 0.5, want_counts=True)
+    ms, mt = r["counts"][0][..., 0], r["counts"][0][..., 1]
+    src, tgt = b.src.doc(0), b.tgt.doc(0)
+    # counts from the batch driver equal the single-pair routine
+    for i in range(0, 40, 7):
+        for j in range(0, 45, 5):
+            assert (ms[i, j], mt[i, j]) == oracle.counts(src[i], tgt[j], b.dic)
+    S = np.array([[oracle.similarity(oracle.features(ms[i, j], mt[i, j], len(src[i]), len(tgt[j])), w, -3.0)
+                   for j in range(45)] for i in range(40)])
+    H, _, diag = oracle.nw(S, 0.3)
+    assert r["score"][0] == H[-1, -1]
+    assert [(i, j) for i, j, _ in r["diag"][0]] == diag
+    assert all(s >= 0.5 for _, _, s in r["links"][0])
+    assert [x for x in r["diag"][0] if x[2] >= 0.5] == r["links"][0]
+
+
+# ---------------------------------------------------------------- soft NW
+def test_soft_closed_form_zero_scores():
+    # s = 0, p = 0: every alignment scores 0, so V = gamma ln D(N,M) and a cell
+    # is taken diagonally by D(i-1,j-1) D(N-i,M-j) of the D(N,M) paths
+    for N, M in [(1, 1), (3, 5), (6, 6), (8, 3)]:
+        for g in [1.0, 0.1]:
+            V, E, _ = oracle.soft_nw(np.zeros((N, M)), 0.0, g)
+            D = brute.delannoy(N, M)
+            assert V[-1, -1] == pytest.approx(g * math.log(D), rel=1e-12)
+            for i in range(1, N + 1):
+                for j in range(1, M + 1):
+                    e = brute.delannoy(i - 1, j - 1) * brute.delannoy(N - i, M - j) / D
+                    assert E[i - 1, j - 1] == pytest.approx(e, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_soft_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    N, M = rng.integers(1, 6, size=2)
+    s = rng.random((N, M))
+    p = float(rng.choice([0.05, 0.3]))
+    g = float(rng.choice([1.0, 0.1, 0.01]))
+    V, E, dp = oracle.soft_nw(s, p, g)
+    v, Eb = brute.soft(s.tolist(), p, g)
+    assert V[-1, -1] == pytest.approx(v, rel=1e-12, abs=1e-12)
+    assert np.allclose(E, np.array(Eb), rtol=1e-9, atol=1e-12)
+    # dV/dp = -(expected number of gap steps) = -(N + M - 2 * expected diagonals)
+    assert dp == pytest.approx(-(N + M - 2 * np.sum(Eb)), rel=1e-9, abs=1e-12)
+    # hard value <= soft value <= hard value + gamma ln D
+    H, _, _ = oracle.nw(s, p)
+    assert H[-1, -1] - 1e-12 <= V[-1, -1] <= H[-1, -1] + g * math.log(brute.delannoy(N, M)) + 1e-12
+
+
+@pytest.mark.slow
+def test_soft_brute_force_8x8():
+    rng = np.random.default_rng(8)
+    s = rng.random((8, 8))
+    V, E, _ = oracle.soft_nw(s, 0.3, 0.1)
+    v, Eb = brute.soft(s.tolist(), 0.3, 0.1)
+    assert V[-1, -1] == pytest.approx(v, rel=1e-12)
+    assert np.allclose(E, np.array(Eb), rtol=1e-9, atol=1e-12)
+
+
+def test_soft_tends_to_hard():
+    rng = np.random.default_rng(9)
+    s = rng.random((9, 11))
+    H, _, diag = oracle.nw(s, 0.3)
+    V, E, _ = oracle.soft_nw(s, 0.3, 1e-3)
+    assert V[-1, -1] == pytest.approx(H[-1, -1], abs=1e-3 * math.log(brute.delannoy(9, 11)) + 1e-9)
+    hard = np.zeros_like(s)
+    for i, j in diag:
+        hard[i, j] = 1
+    assert np.abs(E - hard).max() < 1e-6
+
+
+def test_soft_adjoint_equals_autograd():
+    torch = pytest.importorskip("torch")
+    from oracle import softgrad
+    rng = np.random.default_rng(12)
+    s = rng.random((6, 7))
+    V, E, dp = oracle.soft_nw(s, 0.3, 0.1)
+    st = torch.tensor(s, requires_grad=True)
+    pt = torch.tensor(0.3, dtype=torch.float64, requires_grad=True)
+    v = softgrad.soft_value(st, pt, 0.1)
+    gs, gp = torch.autograd.grad(v, [st, pt])
+    assert float(v.detach()) == pytest.approx(V[-1, -1], rel=1e-12)
+    assert np.allclose(gs.numpy(), E, rtol=1e-10, atol=1e-13)
+    assert float(gp) == pytest.approx(dp, rel=1e-10)
+
+
+def _soft_pairs(seed, n_pairs=3, n=8):
+    b = synth.make_batch(seed, n_pairs, v_src=300, v_tgt=300, planted_frac=1.0,
+                         src_sizes=np.full(n_pairs, n), p_ins=0.0, p_sdrop=0.0)
+    r = oracle.mine(b, [4, 4, -2, 1], -3, 0.3, 0.5, want_counts=True)
+    pairs = []
+    for k in range(n_pairs):
+        c = r["counts"][k]
+        ls = [len(x) for x in b.src.doc(k)]
+        lt = [len(x) for x in b.tgt.doc(k)]
+        gold = np.zeros(c.shape[:2])
+        for i, j in b.gold[k]:
+            gold[i, j] = 1
+        pairs.append((c[..., 0], c[..., 1], ls, lt, gold))
+    return pairs
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+def test_soft_loss_gradient_central_differences(gamma):
+    pytest.importorskip("torch")
+    from oracle import softgrad
+    pairs = _soft_pairs(21)
+    theta = np.array([4.0, 4.0, -2.0, 1.0, -3.0, 0.3, 0.5])
+    L, g = softgrad.loss_and_grad(pairs, theta, gamma, 0.05)
+    h = 1e-6
+    for k in range(7):
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (softgrad.loss_value(pairs, tp, gamma, 0.05) - softgrad.loss_value(pairs, tm, gamma, 0.05)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-4, abs=1e-7), k
