@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of the batched mining hot path on GB300.
+
+Workload (default): the large uneven batch -- 100,000 Wikipedia-shaped
+document pairs (lognormal sentence counts, median 60, sigma 0.8, clipped
+5..800, half planted) plus 8 pairs of 5,000 x 5,000 sentences, all in one
+plan; sentences of 5..30 Zipf(1.1) token ids over 50k-id vocabularies.  One
+step = one mine_pairs call over the whole batch: overlap counts, similarity,
+Needleman-Wunsch fill, traceback + threshold, link compaction.
+
+Prints one JSON line (rank 0).  ``value`` is DP cell-updates per second over
+all ranks (sum over pairs of N*M per step), inputs resident in HBM;
+``e2e`` is the same metric through the public API from pinned host buffers
+(upload, plan, mine, download of links and scores inside the timed region).
+
+--impl reference times the FP64 CPU oracle (the correctness reference) on a
+bounded random sample of the same workload, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_1512_01641_gb300 import synth  # noqa: E402
+
+METRIC = "DP cell-updates/s (batched hard-NW mining)"
+UNIT = "cell-updates/s"
+N_SMS = 152
+LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes issue per clock
+# algorithmic lane-operations per cell, see the design doc (roofline model)
+OPS_SIM = 11   # 4 quotients, 4 multiply-adds, exp, add, reciprocal
+OPS_DP = 8     # 3 candidates, 2 max, 2 compare/select, 1 pack
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pairs", type=int, default=100_000, help="Wikipedia-shaped pairs per rank")
+    ap.add_argument("--long", type=int, default=8, help="5000x5000 pairs per rank")
+    ap.add_argument("--long-n", type=int, default=5000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-pairs", type=int, default=8000, help="pairs in the oracle's timed sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", 0))
+    w = int(os.environ.get("WORLD_SIZE", 1))
+    lr = int(os.environ.get("LOCAL_RANK", 0))
+    return r, w, lr
+
+
+def workload(args, rank):
+    b = synth.uneven_batch(n_pairs=args.pairs, n_long=args.long, long_n=args.long_n,
+                           seed=synth.SEED_BASE + 2 + 1000 * rank)
+    desc = {"workload": f"uneven batch: {args.pairs} Wikipedia-shaped pairs + {args.long} x "
+                        f"{args.long_n}x{args.long_n} pairs per GPU",
+            "pairs_per_gpu": b.n_pairs, "cells_per_gpu": b.cells(),
+            "tokens_per_gpu": int(len(b.src.tok) + len(b.tgt.tok)),
+            "params": {"w": [4, 4, -2, 1], "b": -3, "gap": 0.3, "thr": 0.5},
+            "l2": "inputs larger than L2 (no flush)"}
+    return b, desc
+
+
+def merge_compare_ops(batch):
+    """Sum over cells of |T_i| + lt_j: the compares of a sorted-merge intersection
+    of source sentence i's translations with target sentence j."""
+    dic = batch.dic
+    fan = np.diff(dic.off.astype(np.int64))
+    tr_per_tok = fan[batch.src.tok]
+    s_off = batch.src.sent_tok_off
+    tr_per_sent = np.add.reduceat(tr_per_tok, s_off[:-1]) if len(tr_per_tok) else np.zeros(0)
+    d_off = batch.src.doc_sent_off
+    n_src = np.diff(d_off)
+    t_len = np.diff(batch.tgt.sent_tok_off)
+    tr_doc = np.add.reduceat(np.append(tr_per_sent, 0), d_off[:-1])[: batch.n_pairs] * (n_src > 0)
+    tl_doc = np.add.reduceat(np.append(t_len, 0), batch.tgt.doc_sent_off[:-1])[: batch.n_pairs] * \
+        (np.diff(batch.tgt.doc_sent_off) > 0)
+    M = np.diff(batch.tgt.doc_sent_off)
+    return int((tr_doc * M + tl_doc * n_src).sum())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            time.sleep(0.3)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(batch, n_pairs, seed=0):
+    import oracle
+    rng = np.random.default_rng(seed)
+    small = np.nonzero(batch.src.doc_sizes() * batch.tgt.doc_sizes() < 1_000_000)[0]
+    pick = np.sort(rng.choice(small, size=min(n_pairs, len(small)), replace=False))
+    sub = batch.subset(pick)
+    cells = sub.cells()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.mine(sub, [4, 4, -2, 1], -3.0, 0.3, 0.5, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": int(r["threads"]), "kind": "oracle",
+            "sample": f"{len(pick)} random pairs of the workload (long pairs excluded), {cells} cells, "
+                      f"{dt:.1f} s", "seconds": dt, "cells": cells}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    batch, desc = workload(args, 0)
+    rng = np.random.default_rng(1)
+    vals = []
+    threads = os.cpu_count() or 1
+    per_step = max(1, args.cpu_pairs // 4)
+    import oracle
+    small = np.nonzero(batch.src.doc_sizes() * batch.tgt.doc_sizes() < 1_000_000)[0]
+    tot_cells = tot_t = 0.0
+    for step in range(args.warmup + args.steps):
+        pick = np.sort(rng.choice(small, size=min(per_step, len(small)), replace=False))
+        sub = batch.subset(pick)
+        t0 = time.perf_counter()
+        oracle.mine(sub, [4, 4, -2, 1], -3.0, 0.3, 0.5, n_threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            tot_cells += sub.cells()
+            tot_t += dt
+    v = tot_cells / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step {per_step} random pairs of the workload (long pairs excluded)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def e2e_run(batch, params, steps):
+    """Public API from pinned host buffers: upload, plan, mine, download."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    host = [batch.src.doc_sent_off, batch.src.sent_tok_off, batch.src.tok, batch.tgt.doc_sent_off,
+            batch.tgt.sent_tok_off, batch.tgt.tok, batch.dic.off, batch.dic.tgt]
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host]
+    h2d = sum(t.numel() * t.element_size() for t in pinned)
+    times, d2h = [], 0
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dev = [t.to("cuda", non_blocking=True) for t in pinned]
+        db = miner.DeviceBatch(*dev, batch.dic.v_src, batch.dic.v_tgt)
+        plan = miner.Plan(db)
+        out = plan.mine(params)
+        n = int(out["link_off"][-1].item())
+        res = {"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"].cpu(),
+               "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(), "link_s": out["link_s"][:n].cpu()}
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        d2h = 8 + sum(t.numel() * t.element_size() for t in res.values())
+        plan.close()
+        del dev, db, out
+    return float(np.median(times)), h2d, d2h
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, lrank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(lrank)
+    from paper_1512_01641_gb300 import miner
+    miner.lib(build_if_missing=True)
+
+    batch, desc = workload(args, rank)
+    params = miner.MineParams()
+    db = miner.DeviceBatch.from_batch(batch)
+    plan = miner.Plan(db)
+    out = plan.new_output()
+    for _ in range(args.warmup):
+        plan.mine(params, out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    plan.set_timing(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(lrank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.mine(params, out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    secs = ev0.elapsed_time(ev1) / 1000.0
+    kt = plan.kernel_times()
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([secs], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    cells_step = plan.n_cells * world
+    value = cells_step * args.steps / secs
+    pairs_s = plan.n_pairs * world * args.steps / secs
+    launches = sum(n for _, n in kt.values())
+
+    # roofline of the dominant kernel (ALU issue bound)
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(kt[dom][1], 1)
+    n_cells = plan.n_cells
+    if dom == "count":
+        ops = merge_compare_ops(batch)
+    else:
+        ops = (OPS_SIM + OPS_DP) * n_cells
+    achieved = ops / (dom_ms / 1000.0) / 1e12
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = N_SMS * LANES_PER_SM * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "ops_per_launch": ops, "ms_per_launch": dom_ms,
+                "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lane-ops/clk x {sm_max:.0f} MHz"}
+
+    e2e = None
+    if not args.no_e2e:
+        plan_keep = plan
+        e_t, h2d, d2h = e2e_run(batch, params, args.e2e_steps)
+        e2e = {"value": cells_step / world / e_t * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e_t,
+               "includes": "H2D of inputs, plan creation (validation, geometry, scratch), mine_pairs, D2H of links"}
+        plan = plan_keep
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(batch, args.cpu_pairs)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded, Wikipedia-shaped)", "config": desc,
+                "pairs_per_s": pairs_s, "gpu_launches": launches,
+                "kernel_ms": {k: v[0] / max(args.steps, 1) for k, v in kt.items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

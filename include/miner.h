@@ -1,0 +1,157 @@
+/*
+ * miner.h - C ABI of the GB300 comparable-corpus miner.
+ *
+ * The method (Wolk & Marasek, arXiv:1512.01641):
+ *   - every source x target sentence pair of a topic-aligned document pair gets
+ *     a similarity in [0,1]: a linear classifier's decision value over
+ *     dictionary/length features squashed by a sigmoid (Section 4);
+ *   - the two sentence sequences are globally aligned by Needleman-Wunsch
+ *     under a gap penalty (Section 5.1, Figure 1, Eq. 1): S(0,0) = 0, border
+ *     cells initialised with the penalty, every other cell the max of
+ *     diagonal + similarity, up - penalty and left - penalty;
+ *   - aligned pairs whose similarity is below the acceptance threshold are
+ *     dropped (Section 4; the threshold of Section 5.2).
+ *
+ * Conventions for every entry point:
+ *   - all array pointers are DEVICE pointers unless the name says host_;
+ *     buffers are owned by the caller, except what a plan allocates itself;
+ *   - calls taking a stream are asynchronous on it, unless stated otherwise;
+ *   - a negative return value is an error code (mine_strerror); 0 is success;
+ *   - document pair k is source document k with target document k.
+ *
+ * Input corpus layout (CSR): document d owns sentences
+ * doc_sent_off[d] .. doc_sent_off[d+1]-1; sentence s owns tokens
+ * tok[sent_tok_off[s] .. sent_tok_off[s+1]-1], sorted ascending, 1..255 of
+ * them.  The dictionary maps source id v to the sorted, distinct target ids
+ * tgt[off[v] .. off[v+1]-1].
+ *
+ * Cell (i, j) of pair k is (source sentence i, target sentence j), 0-based.
+ * Per-cell buffers are row-major per pair, pair k starting at cell offset
+ * sum_{k'<k} N_k' * M_k' (mine_plan_cell_offsets).
+ */
+#ifndef GB300_MINER_H
+#define GB300_MINER_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *miner_stream_t; /* same handle as cudaStream_t */
+
+/* error codes */
+#define MINE_OK 0
+#define MINE_EINVAL (-1)   /* malformed input (offsets, ids, ordering, sizes) */
+#define MINE_ENOMEM (-2)   /* device or host allocation failed */
+#define MINE_ECUDA (-3)    /* a CUDA call failed (mine_last_cuda_error) */
+#define MINE_ETIMEOUT (-4) /* a device-side bounded wait gave up */
+#define MINE_ENOTSUP (-5)  /* request outside what this build supports */
+
+typedef struct {
+    int64_t n_docs;               /* number of documents */
+    int64_t n_sents;              /* total sentences (= doc_sent_off[n_docs]) */
+    int64_t n_tok;                /* total tokens (= sent_tok_off[n_sents]) */
+    const int64_t *doc_sent_off;  /* n_docs+1, device */
+    const int64_t *sent_tok_off;  /* n_sents+1, device */
+    const int32_t *tok;           /* n_tok, device, sorted per sentence */
+} mine_corpus;
+
+typedef struct {
+    int32_t v_src;                /* source vocabulary size */
+    int32_t v_tgt;                /* target vocabulary size */
+    int64_t n_entries;            /* = off[v_src] */
+    const int32_t *off;           /* v_src+1, device */
+    const int32_t *tgt;           /* n_entries, device, sorted distinct per id */
+} mine_dict;
+
+/* Classifier and alignment parameters (Section 4 / Section 5.2):
+ * similarity s = 1 / (1 + exp(-(w . f + b))) with
+ * f = [ms/ls, mt/lt, |ls-lt|/max(ls,lt), min(ls,lt)/max(ls,lt)],
+ * gap = penalty p per unmatched sentence, thr = acceptance threshold. */
+typedef struct {
+    float w[4];
+    float b;
+    float gap;
+    float thr;
+} mine_params;
+
+/* Output of mine_pairs / mine_align (all device, caller-allocated).
+ * Links of pair k are entries link_off[k] .. link_off[k+1]-1 of link_i,
+ * link_j, link_s, ascending in i and j.  link_capacity must be at least
+ * mine_plan_link_capacity() (the sum over pairs of min(N_k, M_k)). */
+typedef struct {
+    int64_t *link_off;     /* n_docs+1, filled by the library */
+    int32_t *link_i;       /* source sentence index within the document */
+    int32_t *link_j;       /* target sentence index within the document */
+    float *link_s;         /* similarity of the linked pair (>= thr) */
+    float *pair_score;     /* n_docs: Needleman-Wunsch value H(N_k, M_k) */
+    int64_t link_capacity; /* entries available in link_i/link_j/link_s */
+} mine_out;
+
+typedef struct mine_plan mine_plan;
+
+/* Validate the inputs and build a plan for mining every document pair:
+ * document sizes, work order, per-pair offsets and the plan-owned scratch
+ * (traceback bits, cached counts, boundary rows).  The input buffers must
+ * stay alive and unchanged while the plan is used.  SYNCHRONOUS on the stream
+ * (it reads the document offsets back and waits for the validation kernel).
+ * Returns MINE_EINVAL for: n_docs mismatch, offsets not starting at 0 or not
+ * monotone, an empty sentence or one longer than 255 tokens, a token id
+ * outside its vocabulary, tokens not sorted within a sentence, dictionary
+ * lists unsorted or repeated or out of range. */
+int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                     mine_plan **out, miner_stream_t stream);
+void mine_plan_destroy(mine_plan *plan);
+
+int64_t mine_plan_n_pairs(const mine_plan *plan);
+int64_t mine_plan_n_cells(const mine_plan *plan);       /* sum N_k * M_k */
+int64_t mine_plan_link_capacity(const mine_plan *plan); /* sum min(N_k, M_k) */
+/* host_out: n_pairs+1 entries (host memory), cell offsets of each pair. */
+int mine_plan_cell_offsets(const mine_plan *plan, int64_t *host_out);
+
+/* Overlap counts of every cell (Section 4 similarity inputs, feature reading
+ * above): counts[2*c] = ms, counts[2*c+1] = mt for cell c, uint8 each, exact
+ * integers.  ms = source positions with a translation present in the target
+ * sentence; mt = target positions whose token translates some source token.
+ * counts must hold 2 * mine_plan_n_cells() bytes. */
+int mine_count(mine_plan *plan, uint8_t *counts, miner_stream_t stream);
+
+/* Features and similarity of every cell from counts (the unfused debug path of
+ * Section 4's classifier): s[c] (FP32) and, if feat is not NULL, feat[4*c+k]
+ * the four features, each an IEEE-rounded FP32 quotient. */
+int mine_score(mine_plan *plan, const mine_params *params, const uint8_t *counts,
+               float *s, float *feat, miner_stream_t stream);
+
+/* Needleman-Wunsch alignment + threshold filter (Section 5.1, Eq. 1; Section
+ * 4 threshold) of every pair from precomputed counts.  Ties in the traceback
+ * prefer UP (source sentence unmatched), then LEFT, then DIAG (Figure 4). */
+int mine_align(mine_plan *plan, const mine_params *params, const uint8_t *counts,
+               mine_out *out, miner_stream_t stream);
+
+/* The whole hot path: overlap counts, similarity, alignment, threshold
+ * filter, for every document pair of the plan.  Uses plan-owned scratch; no
+ * allocation after plan creation. */
+int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
+               miner_stream_t stream);
+
+/* Per-kernel timing (profiling aid).  When enabled, every kernel launch of the
+ * plan is bracketed by CUDA events on the launching stream and its duration is
+ * accumulated per kernel kind.  mine_plan_kernel_times synchronises the last
+ * stream used, then writes up to n totals (milliseconds) into host_ms and the
+ * matching launch counts into host_launches (either may be NULL); it returns
+ * the number of kernel kinds (MINE_KERNEL_KINDS).  Kinds, in order: count,
+ * align-fill, traceback, link-scan, link-copy, score. */
+#define MINE_KERNEL_KINDS 6
+int mine_plan_set_timing(mine_plan *plan, int enable);
+int mine_plan_kernel_times(mine_plan *plan, float *host_ms, int64_t *host_launches, int n);
+
+const char *mine_strerror(int code);
+/* The cudaError_t value behind the last MINE_ECUDA of this thread. */
+int mine_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_MINER_H */

@@ -61,7 +61,7 @@ def lib():
             L.oracle_mine.argtypes = [C.c_int64, i64p, i64p, i64p, i32p, i64p, i64p, i32p,
                                       i32p, i32p, f64p, C.c_double, C.c_double,
                                       i64p, f64p, i64p, i32p, i32p, f64p,
-                                      C.c_void_p, C.c_void_p, C.c_int]
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
             L.oracle_mine.restype = C.c_int
             _lib = L
     return _lib
@@ -154,12 +154,13 @@ def path_score(s, p, diag) -> float:
 # ---------------------------------------------------------------------------
 # whole batches
 # ---------------------------------------------------------------------------
-def mine(batch, w, b, gap, thr, pairs=None, n_threads=None, want_counts=False):
+def mine(batch, w, b, gap, thr, pairs=None, n_threads=None, want_counts=False, want_sim=False):
     """Mine the listed pairs of a synth.Batch.
 
     Returns a dict with, per listed pair: ``score`` (H(N,M)), ``diag`` (list of
     (i, j, s) on the optimal path, ascending), ``links`` (the diag cells with
-    s >= thr) and optionally ``counts`` (N x M x 2 int32: ms, mt)."""
+    s >= thr) and optionally ``counts`` (N x M x 2 int32: ms, mt) and ``sim``
+    (N x M float64 similarities)."""
     src, tgt, dic = batch.src, batch.tgt, batch.dic
     if pairs is None:
         pairs = np.arange(batch.n_pairs)
@@ -176,11 +177,13 @@ def mine(batch, w, b, gap, thr, pairs=None, n_threads=None, want_counts=False):
     dj = np.zeros(max(tot, 1), np.int32)
     ds = np.zeros(max(tot, 1), np.float64)
     cnt = None
-    cell_off = None
+    sim = None
+    cell_off = np.zeros(len(pairs) + 1, np.int64)
+    np.cumsum(N * M, out=cell_off[1:])
     if want_counts:
-        cell_off = np.zeros(len(pairs) + 1, np.int64)
-        np.cumsum(N * M, out=cell_off[1:])
         cnt = np.zeros(max(int(cell_off[-1]) * 2, 1), np.int32)
+    if want_sim:
+        sim = np.zeros(max(int(cell_off[-1]), 1), np.float64)
     if n_threads is None:
         n_threads = os.cpu_count() or 1
     used = lib().oracle_mine(len(pairs), pairs,
@@ -190,7 +193,8 @@ def mine(batch, w, b, gap, thr, pairs=None, n_threads=None, want_counts=False):
                              _c(w, np.float64), float(b), float(gap),
                              out_off, score, nd, di, dj, ds,
                              cnt.ctypes.data if cnt is not None else None,
-                             cell_off.ctypes.data if cell_off is not None else None,
+                             sim.ctypes.data if sim is not None else None,
+                             cell_off.ctypes.data,
                              int(n_threads))
     res = {"score": score, "diag": [], "links": [], "threads": used}
     for k in range(len(pairs)):
@@ -202,4 +206,6 @@ def mine(batch, w, b, gap, thr, pairs=None, n_threads=None, want_counts=False):
     if want_counts:
         res["counts"] = [cnt[2 * cell_off[k]:2 * cell_off[k + 1]].reshape(N[k], M[k], 2)
                          for k in range(len(pairs))]
+    if want_sim:
+        res["sim"] = [sim[cell_off[k]:cell_off[k + 1]].reshape(N[k], M[k]) for k in range(len(pairs))]
     return res

@@ -199,6 +199,7 @@ typedef struct {
     int32_t *diag_i, *diag_j;
     double *diag_s;
     int32_t *counts;        /* optional: 2 ints per cell, per processed pair at cell_off */
+    double *sim;            /* optional: similarity per cell, per processed pair at cell_off */
     const int64_t *cell_off;
     int64_t next;           /* shared work counter */
     pthread_mutex_t lock;
@@ -227,6 +228,7 @@ static void mine_one(mine_job *J, int64_t idx) {
             }
             oracle_features(ms, mt, ls, lt, f);
             S[i * M + j] = oracle_similarity(f, J->w, J->bias);
+            if (J->sim) J->sim[J->cell_off[idx] + i * M + j] = S[i * M + j];
         }
     }
     oracle_nw_fill(N, M, S, J->gap, H);
@@ -266,8 +268,9 @@ static void *mine_worker(void *arg) {
 /* Mine the listed pairs.  For processed pair idx (0-based in pairs[]), the
  * diagonal cells of the chosen optimal path are written at out_off[idx] in
  * ascending order (capacity min(N,M)), with their similarity; pair_score[idx]
- * is H(N,M).  counts (optional, NULL to skip) receives (ms, mt) per cell,
- * row-major per pair at cell_off[idx].  Returns the number of threads used. */
+ * is H(N,M).  counts and sim (optional, NULL to skip) receive (ms, mt) and the
+ * similarity per cell, row-major per pair at cell_off[idx].  Returns the number
+ * of threads used. */
 int oracle_mine(int64_t n_pairs, const int64_t *pairs,
                 const int64_t *s_doc, const int64_t *s_sent, const int32_t *s_tok,
                 const int64_t *t_doc, const int64_t *t_sent, const int32_t *t_tok,
@@ -275,7 +278,7 @@ int oracle_mine(int64_t n_pairs, const int64_t *pairs,
                 const double *w, double bias, double gap,
                 const int64_t *out_off, double *pair_score, int64_t *n_diag,
                 int32_t *diag_i, int32_t *diag_j, double *diag_s,
-                int32_t *counts, const int64_t *cell_off, int n_threads) {
+                int32_t *counts, double *sim, const int64_t *cell_off, int n_threads) {
     mine_job J;
     memset(&J, 0, sizeof J);
     J.n_pairs = n_pairs; J.pairs = pairs;
@@ -286,7 +289,7 @@ int oracle_mine(int64_t n_pairs, const int64_t *pairs,
     J.bias = bias; J.gap = gap;
     J.out_off = out_off; J.pair_score = pair_score; J.n_diag = n_diag;
     J.diag_i = diag_i; J.diag_j = diag_j; J.diag_s = diag_s;
-    J.counts = counts; J.cell_off = cell_off;
+    J.counts = counts; J.sim = sim; J.cell_off = cell_off;
     pthread_mutex_init(&J.lock, NULL);
     if (n_threads < 1) n_threads = 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);

@@ -1,0 +1,103 @@
+// Device helpers shared by the mining kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "miner.h"
+
+namespace gbm {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int32_t kEmpty = -1;
+
+// Traceback direction codes, 2 bits per cell.
+constexpr uint32_t kDiag = 0, kUp = 1, kLeft = 2;
+
+struct DevParams {
+    float w[4];
+    float b;
+    float gap;
+    float thr;
+};
+
+inline DevParams to_dev(const mine_params &p) {
+    DevParams d;
+    for (int k = 0; k < 4; ++k) d.w[k] = p.w[k];
+    d.b = p.b;
+    d.gap = p.gap;
+    d.thr = p.thr;
+    return d;
+}
+
+// The four features of Section 4's classifier input, each an IEEE-rounded
+// FP32 quotient of two small integers:
+//   f0 = ms/ls, f1 = mt/lt, f2 = |ls-lt|/max(ls,lt), f3 = min(ls,lt)/max(ls,lt).
+__device__ __forceinline__ void features(int ms, int mt, int ls, int lt, float f[4]) {
+    int mx = max(ls, lt), mn = min(ls, lt);
+    f[0] = __fdiv_rn((float)ms, (float)ls);
+    f[1] = __fdiv_rn((float)mt, (float)lt);
+    f[2] = __fdiv_rn((float)(mx - mn), (float)mx);
+    f[3] = __fdiv_rn((float)mn, (float)mx);
+}
+
+// Similarity s = sigmoid(w . f + b) (Section 4: a linear decision value
+// squashed into [0,1]).  Every kernel that needs s calls this one function with
+// explicitly rounded operations, so all of them produce the same float.
+__device__ __forceinline__ float similarity(int ms, int mt, int ls, int lt, const DevParams &P) {
+    float f[4];
+    features(ms, mt, ls, lt, f);
+    float z = __fmaf_rn(P.w[0], f[0], P.b);
+    z = __fmaf_rn(P.w[1], f[1], z);
+    z = __fmaf_rn(P.w[2], f[2], z);
+    z = __fmaf_rn(P.w[3], f[3], z);
+    return __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-z)));
+}
+
+// Multiplicative hash of a token id into a table of 2^log_slots slots.
+__device__ __forceinline__ uint32_t hash_slot(int32_t t, int log_slots) {
+    return ((uint32_t)t * 0x9E3779B1u) >> (32 - log_slots);
+}
+
+// Bit-sliced counters: plane k holds bit k of 32 independent counters (one
+// per bit position).  add() adds a 0/1 word into all 32 counters at once.
+template <int K>
+struct BitCounter {
+    uint32_t p[K];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = 0u;
+    }
+    __device__ __forceinline__ void add(uint32_t x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            uint32_t c = p[k] & x;
+            p[k] ^= x;
+            x = c;
+        }
+    }
+    // Counter for bit position 4m+r lands in byte r of out[m].
+    __device__ __forceinline__ void to_bytes(uint32_t out[8]) const {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                uint32_t nib = (p[k] >> (4 * m)) & 0xFu;
+                w |= ((nib * 0x00204081u) & 0x01010101u) << k;
+            }
+            out[m] = w;
+        }
+    }
+};
+
+// Error bits of the device status word.
+constexpr uint32_t kStBadDocOff = 1u << 0;
+constexpr uint32_t kStBadSentOff = 1u << 1;
+constexpr uint32_t kStBadToken = 1u << 2;
+constexpr uint32_t kStUnsorted = 1u << 3;
+constexpr uint32_t kStBadDict = 1u << 4;
+constexpr uint32_t kStTableFull = 1u << 5;
+constexpr uint32_t kStTimeout = 1u << 6;
+
+}  // namespace gbm

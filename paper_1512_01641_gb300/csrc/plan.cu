@@ -1,0 +1,430 @@
+// Plan creation, input validation and the C ABI entry points of miner.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "kernels.h"
+#include "miner.h"
+
+namespace gbm {
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+// ---------------------------------------------------------------- validation
+__global__ void validate_corpus_kernel(DevCorpus c, int64_t n_sents, int64_t n_tok, int32_t vocab,
+                                       uint32_t *status, int32_t *max_len) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_sents; s += stride) {
+        const int64_t a = c.sent[s], b = c.sent[s + 1];
+        if (a < 0 || b > n_tok || b - a < 1 || b - a > 255) {
+            atomicOr(status, kStBadSentOff);
+            continue;
+        }
+        atomicMax(max_len, (int32_t)(b - a));
+        int32_t prev = -1;
+        for (int64_t x = a; x < b; ++x) {
+            const int32_t t = c.tok[x];
+            if (t < 0 || t >= vocab) atomicOr(status, kStBadToken);
+            if (t < prev) atomicOr(status, kStUnsorted);
+            prev = t;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (c.sent[0] != 0 || c.sent[n_sents] != n_tok) atomicOr(status, kStBadSentOff);
+    }
+}
+
+__global__ void validate_dict_kernel(DevDict d, int32_t v_src, int32_t v_tgt, int64_t n_entries,
+                                     uint32_t *status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < v_src; v += stride) {
+        const int64_t a = d.off[v], b = d.off[v + 1];
+        if (a < 0 || b > n_entries || b < a) {
+            atomicOr(status, kStBadDict);
+            continue;
+        }
+        int32_t prev = -1;
+        for (int64_t e = a; e < b; ++e) {
+            const int32_t t = d.tgt[e];
+            if (t < 0 || t >= v_tgt || t <= prev) atomicOr(status, kStBadDict);
+            prev = t;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (d.off[0] != 0 || d.off[v_src] != n_entries) atomicOr(status, kStBadDict);
+    }
+}
+
+// Largest token total of any 32-sentence target block (sizes the count hash).
+__global__ void block_tokens_kernel(DevCorpus tgt, const PairGeom *geom, int64_t n_pairs, int32_t *out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride) {
+        const int M = geom[k].m;
+        const int64_t base = tgt.doc[k];
+        for (int c0 = 0; c0 < M; c0 += 32) {
+            const int c1 = min(M, c0 + 32);
+            const int64_t tot = tgt.sent[base + c1] - tgt.sent[base + c0];
+            atomicMax(out, (int32_t)tot);
+        }
+    }
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+}  // namespace
+
+cudaError_t launch_validate_corpus(const DevCorpus &c, int64_t n_sents, int64_t n_tok, int32_t vocab,
+                                   uint32_t *status, int32_t *max_len, cudaStream_t st) {
+    int64_t blocks = std::min<int64_t>((n_sents + 255) / 256, 4096);
+    validate_corpus_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(c, n_sents, n_tok, vocab,
+                                                                                   status, max_len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_tokens(const DevCorpus &tgt, const PairGeom *geom, int64_t n_pairs,
+                                int32_t *max_block_tokens, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    int64_t blocks = std::min<int64_t>((n_pairs + 255) / 256, 4096);
+    block_tokens_kernel<<<(unsigned)blocks, 256, 0, st>>>(tgt, geom, n_pairs, max_block_tokens);
+    return cudaGetLastError();
+}
+
+}  // namespace gbm
+
+using namespace gbm;
+
+struct mine_plan {
+    DevCorpus src{}, tgt{};
+    DevDict dict{};
+    int64_t n_pairs = 0, n_cells = 0, link_cap = 0, n_items = 0;
+    std::vector<int64_t> cell_off_h;
+    PairGeom *geom = nullptr;
+    int32_t *order = nullptr;
+    CountItem *items = nullptr;
+    uint8_t *counts = nullptr;
+    uint64_t *tb = nullptr;
+    float *hrow = nullptr;
+    int32_t *scr_i = nullptr, *scr_j = nullptr;
+    float *scr_s = nullptr;
+    int32_t *n_links = nullptr;
+    uint32_t *status = nullptr;
+    int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens]
+    int log_slots = 11, planes = 5, n_sms = 1, device = 0;
+    // per-kernel timing hook
+    bool timing = false;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double total_ms[kKinds] = {};
+    int64_t launches[kKinds] = {};
+};
+
+// Launch f() on stream st; with timing enabled, bracket it by two events.
+template <class F>
+static cudaError_t timed(mine_plan *p, int kind, cudaStream_t st, F &&f) {
+    if (!p->timing) return f();
+    mine_plan::Pending q{kind, nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&q.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&q.b);
+    if (e == cudaSuccess) e = cudaEventRecord(q.a, st);
+    if (e == cudaSuccess) e = f();
+    if (e == cudaSuccess) e = cudaEventRecord(q.b, st);
+    if (e == cudaSuccess) {
+        p->pending.push_back(q);
+    } else {
+        if (q.a) cudaEventDestroy(q.a);
+        if (q.b) cudaEventDestroy(q.b);
+    }
+    return e;
+}
+
+static void drain_pending(mine_plan *p) {
+    for (auto &q : p->pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            p->total_ms[q.kind] += ms;
+            p->launches[q.kind] += 1;
+        }
+        cudaEventDestroy(q.a);
+        cudaEventDestroy(q.b);
+    }
+    p->pending.clear();
+}
+
+#define MINE_CK(x)                                   \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
+        if (e_ != cudaSuccess) {                     \
+            g_last_cuda = (int)e_;                   \
+            return MINE_ECUDA;                       \
+        }                                            \
+    } while (0)
+
+static void plan_free(mine_plan *p) {
+    if (!p) return;
+    drain_pending(p);
+    void *bufs[] = {p->geom, p->order, p->items, p->counts, p->tb, p->hrow, p->scr_i,
+                    p->scr_j, p->scr_s, p->n_links, p->status, p->stats};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st);
+
+extern "C" {
+
+int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                     mine_plan **out, miner_stream_t stream) {
+    if (!src || !tgt || !dict || !out) return MINE_EINVAL;
+    *out = nullptr;
+    if (src->n_docs != tgt->n_docs || src->n_docs < 0 || src->n_sents < 0 || tgt->n_sents < 0 ||
+        src->n_tok < 0 || tgt->n_tok < 0 || dict->v_src <= 0 || dict->v_tgt <= 0 || dict->n_entries < 0)
+        return MINE_EINVAL;
+    if (src->n_docs > INT32_MAX) return MINE_ENOTSUP;
+    cudaStream_t st = (cudaStream_t)stream;
+    mine_plan *p = new (std::nothrow) mine_plan();
+    if (!p) return MINE_ENOMEM;
+    auto fail = [&](int code) {
+        plan_free(p);
+        return code;
+    };
+    cudaError_t e;
+#define PLAN_CK(x)                       \
+    do {                                 \
+        e = (x);                         \
+        if (e != cudaSuccess) {          \
+            g_last_cuda = (int)e;        \
+            return fail(e == cudaErrorMemoryAllocation ? MINE_ENOMEM : MINE_ECUDA); \
+        }                                \
+    } while (0)
+    PLAN_CK(cudaGetDevice(&p->device));
+    PLAN_CK(cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device));
+    p->src = {src->doc_sent_off, src->sent_tok_off, src->tok};
+    p->tgt = {tgt->doc_sent_off, tgt->sent_tok_off, tgt->tok};
+    p->dict = {dict->off, dict->tgt};
+    const int64_t n = src->n_docs;
+    p->n_pairs = n;
+
+    // document sizes (synchronous read-back)
+    std::vector<int64_t> sd(n + 1), td(n + 1);
+    PLAN_CK(cudaMemcpyAsync(sd.data(), src->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PLAN_CK(cudaMemcpyAsync(td.data(), tgt->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PLAN_CK(cudaStreamSynchronize(st));
+    if (sd[0] != 0 || td[0] != 0 || sd[n] != src->n_sents || td[n] != tgt->n_sents) return fail(MINE_EINVAL);
+    for (int64_t k = 0; k < n; ++k)
+        if (sd[k + 1] < sd[k] || td[k + 1] < td[k] || sd[k + 1] - sd[k] > INT32_MAX / 2 ||
+            td[k + 1] - td[k] > INT32_MAX / 2)
+            return fail(MINE_EINVAL);
+
+    // validation kernels
+    PLAN_CK(dalloc(&p->status, 4));
+    PLAN_CK(dalloc(&p->stats, 4));
+    PLAN_CK(cudaMemsetAsync(p->status, 0, 4 * sizeof(uint32_t), st));
+    PLAN_CK(cudaMemsetAsync(p->stats, 0, 4 * sizeof(int32_t), st));
+    if (src->n_sents > 0)
+        PLAN_CK(launch_validate_corpus(p->src, src->n_sents, src->n_tok, dict->v_src, p->status, p->stats + 0, st));
+    if (tgt->n_sents > 0)
+        PLAN_CK(launch_validate_corpus(p->tgt, tgt->n_sents, tgt->n_tok, dict->v_tgt, p->status, p->stats + 1, st));
+    {
+        int r = validate_dict(dict, p->status, st);
+        if (r != MINE_OK) return fail(r);
+    }
+
+    // geometry
+    std::vector<PairGeom> geom(n);
+    p->cell_off_h.assign(n + 1, 0);
+    int64_t cell = 0, tbw = 0, link = 0, hrow = 0, items = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        PairGeom &g = geom[k];
+        g.n = (int32_t)(sd[k + 1] - sd[k]);
+        g.m = (int32_t)(td[k + 1] - td[k]);
+        g.cell_off = cell;
+        g.tb_off = tbw;
+        g.link_off = link;
+        g.hrow_off = hrow;
+        p->cell_off_h[k] = cell;
+        const int64_t ns = (g.n + 31) / 32, nb = (g.m + 31) / 32;
+        cell += (int64_t)g.n * g.m;
+        tbw += ns * nb * 32;
+        link += std::min(g.n, g.m);
+        hrow += g.m;
+        items += ns * nb;
+        if (ns > 0xFFFF || nb > 0xFFFF) return fail(MINE_ENOTSUP);
+    }
+    p->cell_off_h[n] = cell;
+    p->n_cells = cell;
+    p->link_cap = link;
+    p->n_items = items;
+    PLAN_CK(dalloc(&p->geom, n));
+    PLAN_CK(cudaMemcpyAsync(p->geom, geom.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
+
+    // work order: largest pairs first
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (int64_t)geom[a].n * geom[a].m > (int64_t)geom[b].n * geom[b].m;
+    });
+    PLAN_CK(dalloc(&p->order, n));
+    PLAN_CK(cudaMemcpyAsync(p->order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    std::vector<CountItem> it;
+    it.reserve(items);
+    for (int32_t k : order) {
+        const int ns = (geom[k].n + 31) / 32, nb = (geom[k].m + 31) / 32;
+        for (int s = 0; s < ns; ++s)
+            for (int b = 0; b < nb; ++b) it.push_back({k, (s << 16) | b});
+    }
+    PLAN_CK(dalloc(&p->items, items));
+    PLAN_CK(cudaMemcpyAsync(p->items, it.data(), items * sizeof(CountItem), cudaMemcpyHostToDevice, st));
+
+    // scratch
+    PLAN_CK(dalloc(&p->counts, 2 * cell));
+    PLAN_CK(dalloc(&p->tb, tbw));
+    PLAN_CK(dalloc(&p->hrow, hrow));
+    PLAN_CK(dalloc(&p->scr_i, link));
+    PLAN_CK(dalloc(&p->scr_j, link));
+    PLAN_CK(dalloc(&p->scr_s, link));
+    PLAN_CK(dalloc(&p->n_links, n));
+    PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
+
+    uint32_t status[4];
+    int32_t stats[4];
+    PLAN_CK(cudaMemcpyAsync(status, p->status, sizeof status, cudaMemcpyDeviceToHost, st));
+    PLAN_CK(cudaMemcpyAsync(stats, p->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
+    PLAN_CK(cudaStreamSynchronize(st));
+    if (status[0] != 0) return fail(MINE_EINVAL);
+    const int maxlen = std::max(stats[0], stats[1]);
+    p->planes = maxlen <= 31 ? 5 : 8;
+    const int btok = std::max(stats[2], 1);
+    int ls = 10;
+    while ((1 << ls) < btok + btok / 2 && ls < 13) ++ls;
+    p->log_slots = ls;
+    *out = p;
+#undef PLAN_CK
+    return MINE_OK;
+}
+
+void mine_plan_destroy(mine_plan *plan) { plan_free(plan); }
+
+int64_t mine_plan_n_pairs(const mine_plan *p) { return p ? p->n_pairs : 0; }
+int64_t mine_plan_n_cells(const mine_plan *p) { return p ? p->n_cells : 0; }
+int64_t mine_plan_link_capacity(const mine_plan *p) { return p ? p->link_cap : 0; }
+
+int mine_plan_cell_offsets(const mine_plan *p, int64_t *host_out) {
+    if (!p || !host_out) return MINE_EINVAL;
+    std::memcpy(host_out, p->cell_off_h.data(), p->cell_off_h.size() * sizeof(int64_t));
+    return MINE_OK;
+}
+
+int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
+    if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
+    if (p->n_items == 0) return MINE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    MINE_CK(timed(p, kKCount, st, [&] {
+        return launch_count(p->src, p->tgt, p->dict, p->geom, p->items, p->n_items, p->log_slots, p->planes,
+                            counts, p->status, p->n_sms, st);
+    }));
+    return MINE_OK;
+}
+
+int mine_score(mine_plan *p, const mine_params *params, const uint8_t *counts, float *s, float *feat,
+               miner_stream_t stream) {
+    if (!p || !params || ((!counts || !s) && p->n_cells > 0)) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams P = to_dev(*params);
+    MINE_CK(timed(p, kKScore, st,
+                  [&] { return launch_score(p->src, p->tgt, p->geom, p->n_pairs, P, counts, s, feat, st); }));
+    return MINE_OK;
+}
+
+int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, mine_out *out,
+               miner_stream_t stream) {
+    if (!p || !params || !out || !out->link_off || !out->pair_score) return MINE_EINVAL;
+    if (out->link_capacity < p->link_cap) return MINE_EINVAL;
+    if (p->link_cap > 0 && (!out->link_i || !out->link_j || !out->link_s)) return MINE_EINVAL;
+    if (p->n_cells > 0 && !counts) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams P = to_dev(*params);
+    MINE_CK(timed(p, kKFill, st, [&] {
+        return launch_nw_counts(p->src, p->tgt, p->geom, p->order, p->n_pairs, P, counts, p->tb, p->hrow, p->n_sms,
+                                st);
+    }));
+    MINE_CK(timed(p, kKTraceback, st, [&] {
+        return launch_traceback(p->src, p->tgt, p->dict, p->geom, p->n_pairs, P, p->tb, p->scr_i, p->scr_j,
+                                p->scr_s, p->n_links, out->pair_score, st);
+    }));
+    MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(p->n_links, p->n_pairs, out->link_off, st); }));
+    MINE_CK(timed(p, kKCopy, st, [&] {
+        return launch_copy_links(p->geom, p->n_pairs, p->n_links, p->scr_i, p->scr_j, p->scr_s, out->link_off,
+                                 out->link_i, out->link_j, out->link_s, st);
+    }));
+    return MINE_OK;
+}
+
+int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_stream_t stream) {
+    if (!p) return MINE_EINVAL;
+    int r = mine_count(p, p->counts, stream);
+    if (r != MINE_OK) return r;
+    return mine_align(p, params, p->counts, out, stream);
+}
+
+int mine_plan_set_timing(mine_plan *p, int enable) {
+    if (!p) return MINE_EINVAL;
+    drain_pending(p);
+    p->timing = enable != 0;
+    for (int k = 0; k < kKinds; ++k) {
+        p->total_ms[k] = 0.0;
+        p->launches[k] = 0;
+    }
+    return MINE_OK;
+}
+
+int mine_plan_kernel_times(mine_plan *p, float *host_ms, int64_t *host_launches, int n) {
+    if (!p) return MINE_EINVAL;
+    drain_pending(p);
+    for (int k = 0; k < kKinds && k < n; ++k) {
+        if (host_ms) host_ms[k] = (float)p->total_ms[k];
+        if (host_launches) host_launches[k] = p->launches[k];
+    }
+    return kKinds;
+}
+
+const char *mine_strerror(int code) {
+    switch (code) {
+        case MINE_OK: return "ok";
+        case MINE_EINVAL: return "invalid argument or malformed input";
+        case MINE_ENOMEM: return "out of memory";
+        case MINE_ECUDA: return "CUDA error";
+        case MINE_ETIMEOUT: return "device-side wait timed out";
+        case MINE_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+int mine_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"
+
+static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st) {
+    if (d->v_src <= 0) return MINE_EINVAL;
+    int64_t blocks = std::min<int64_t>((d->v_src + 255) / 256, 4096);
+    gbm::validate_dict_kernel<<<(unsigned)blocks, 256, 0, st>>>(DevDict{d->off, d->tgt}, d->v_src, d->v_tgt,
+                                                                d->n_entries, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return MINE_ECUDA;
+    }
+    return MINE_OK;
+}

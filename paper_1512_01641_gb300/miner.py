@@ -1,0 +1,275 @@
+"""Python binding of libminer.so (include/miner.h): argument marshalling only.
+
+Every step of the mining path runs in the library's CUDA kernels; this module
+only passes torch CUDA tensors' device pointers and the current stream through
+ctypes.  There is no CPU fallback: if the library is missing or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MINE_OK, MINE_EINVAL, MINE_ENOMEM, MINE_ECUDA, MINE_ETIMEOUT, MINE_ENOTSUP = 0, -1, -2, -3, -4, -5
+
+
+class MinerError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        lib = _lib_or_none()
+        msg = lib.mine_strerror(code).decode() if lib is not None else str(code)
+        extra = ""
+        if code == MINE_ECUDA and lib is not None:
+            extra = f" (cudaError {lib.mine_last_cuda_error()})"
+        super().__init__(f"{what}: {msg}{extra}")
+        self.code = code
+
+
+class _Corpus(C.Structure):
+    _fields_ = [("n_docs", C.c_int64), ("n_sents", C.c_int64), ("n_tok", C.c_int64),
+                ("doc_sent_off", C.c_void_p), ("sent_tok_off", C.c_void_p), ("tok", C.c_void_p)]
+
+
+class _Dict(C.Structure):
+    _fields_ = [("v_src", C.c_int32), ("v_tgt", C.c_int32), ("n_entries", C.c_int64),
+                ("off", C.c_void_p), ("tgt", C.c_void_p)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("w", C.c_float * 4), ("b", C.c_float), ("gap", C.c_float), ("thr", C.c_float)]
+
+
+class _Out(C.Structure):
+    _fields_ = [("link_off", C.c_void_p), ("link_i", C.c_void_p), ("link_j", C.c_void_p),
+                ("link_s", C.c_void_p), ("pair_score", C.c_void_p), ("link_capacity", C.c_int64)]
+
+
+# Every exported symbol of include/miner.h with its ctypes signature.
+_SIGS = {
+    "mine_plan_create": (C.c_int, [C.POINTER(_Corpus), C.POINTER(_Corpus), C.POINTER(_Dict),
+                                   C.POINTER(C.c_void_p), C.c_void_p]),
+    "mine_plan_destroy": (None, [C.c_void_p]),
+    "mine_plan_n_pairs": (C.c_int64, [C.c_void_p]),
+    "mine_plan_n_cells": (C.c_int64, [C.c_void_p]),
+    "mine_plan_link_capacity": (C.c_int64, [C.c_void_p]),
+    "mine_plan_cell_offsets": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mine_count": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_score": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_align": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_void_p]),
+    "mine_pairs": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_Out), C.c_void_p]),
+    "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "mine_plan_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mine_strerror": (C.c_char_p, [C.c_int]),
+    "mine_last_cuda_error": (C.c_int, []),
+}
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def lib(build_if_missing: bool = False) -> C.CDLL:
+    """Load libminer.so (raises if it is absent; never falls back)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libminer.so not built ({path}); run __graft_entry__.build()")
+            _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != MINE_OK:
+        raise MinerError(code, what)
+
+
+@dataclass
+class MineParams:
+    """Classifier weights w (4) and bias b, gap penalty, acceptance threshold."""
+    w: tuple = (4.0, 4.0, -2.0, 1.0)
+    b: float = -3.0
+    gap: float = 0.3
+    thr: float = 0.5
+
+    def c(self) -> _Params:
+        p = _Params()
+        for k in range(4):
+            p.w[k] = float(self.w[k])
+        p.b, p.gap, p.thr = float(self.b), float(self.gap), float(self.thr)
+        return p
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+class DeviceBatch:
+    """Corpus pair and dictionary resident on the GPU (int64 offsets, int32 ids)."""
+
+    def __init__(self, src_doc, src_sent, src_tok, tgt_doc, tgt_sent, tgt_tok, dict_off, dict_tgt,
+                 v_src: int, v_tgt: int):
+        self.src = (src_doc, src_sent, src_tok)
+        self.tgt = (tgt_doc, tgt_sent, tgt_tok)
+        self.dict_off, self.dict_tgt = dict_off, dict_tgt
+        self.v_src, self.v_tgt = int(v_src), int(v_tgt)
+
+    @classmethod
+    def from_batch(cls, batch, device="cuda", non_blocking=False):
+        import torch
+
+        def up(a, dt):
+            t = torch.from_numpy(np.ascontiguousarray(a, dtype=dt))
+            return t.to(device, non_blocking=non_blocking)
+        return cls(up(batch.src.doc_sent_off, np.int64), up(batch.src.sent_tok_off, np.int64),
+                   up(batch.src.tok, np.int32), up(batch.tgt.doc_sent_off, np.int64),
+                   up(batch.tgt.sent_tok_off, np.int64), up(batch.tgt.tok, np.int32),
+                   up(batch.dic.off, np.int32), up(batch.dic.tgt, np.int32), batch.dic.v_src, batch.dic.v_tgt)
+
+    def c_structs(self):
+        def corpus(doc, sent, tok):
+            c = _Corpus()
+            c.n_docs = doc.numel() - 1
+            c.n_sents = sent.numel() - 1
+            c.n_tok = tok.numel()
+            c.doc_sent_off, c.sent_tok_off, c.tok = doc.data_ptr(), sent.data_ptr(), tok.data_ptr() if tok.numel() else 0
+            return c
+        d = _Dict()
+        d.v_src, d.v_tgt = self.v_src, self.v_tgt
+        d.n_entries = self.dict_tgt.numel()
+        d.off, d.tgt = self.dict_off.data_ptr(), self.dict_tgt.data_ptr() if self.dict_tgt.numel() else 0
+        return corpus(*self.src), corpus(*self.tgt), d
+
+
+class Plan:
+    """A mining plan (mine_plan_create) over a DeviceBatch."""
+
+    def __init__(self, dbatch: DeviceBatch, stream=None):
+        L = lib()
+        self.dbatch = dbatch  # keeps the inputs alive
+        self._src, self._tgt, self._dict = dbatch.c_structs()
+        h = C.c_void_p()
+        _check(L.mine_plan_create(C.byref(self._src), C.byref(self._tgt), C.byref(self._dict), C.byref(h),
+                                  _stream(stream)), "mine_plan_create")
+        self._h = h
+        self.n_pairs = L.mine_plan_n_pairs(h)
+        self.n_cells = L.mine_plan_n_cells(h)
+        self.link_capacity = L.mine_plan_link_capacity(h)
+        off = np.zeros(self.n_pairs + 1, np.int64)
+        _check(L.mine_plan_cell_offsets(h, off.ctypes.data), "mine_plan_cell_offsets")
+        self.cell_offsets = off
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mine_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    KERNEL_KINDS = ("count", "align_fill", "traceback", "link_scan", "link_copy", "score")
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().mine_plan_set_timing(self._h, int(enable)), "mine_plan_set_timing")
+
+    def kernel_times(self):
+        """{kind: (total ms, launches)} of the launches since set_timing(True)."""
+        n = len(self.KERNEL_KINDS)
+        ms = np.zeros(n, np.float32)
+        cnt = np.zeros(n, np.int64)
+        r = lib().mine_plan_kernel_times(self._h, ms.ctypes.data, cnt.ctypes.data, n)
+        if r < 0:
+            _check(r, "mine_plan_kernel_times")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    # ------------------------------------------------------------------ calls
+    def count(self, out=None, stream=None):
+        """(n_cells, 2) uint8 tensor of (ms, mt) per cell."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_cells, 2), dtype=torch.uint8, device="cuda")
+        _check(lib().mine_count(self._h, _ptr(out), _stream(stream)), "mine_count")
+        return out
+
+    def score(self, params: MineParams, counts, want_features=False, stream=None):
+        import torch
+        s = torch.empty(self.n_cells, dtype=torch.float32, device="cuda")
+        f = torch.empty((self.n_cells, 4), dtype=torch.float32, device="cuda") if want_features else None
+        p = params.c()
+        _check(lib().mine_score(self._h, C.byref(p), _ptr(counts), _ptr(s), _ptr(f), _stream(stream)), "mine_score")
+        return (s, f) if want_features else s
+
+    def new_output(self):
+        import torch
+        cap = max(self.link_capacity, 1)
+        return {
+            "link_off": torch.empty(self.n_pairs + 1, dtype=torch.int64, device="cuda"),
+            "link_i": torch.empty(cap, dtype=torch.int32, device="cuda"),
+            "link_j": torch.empty(cap, dtype=torch.int32, device="cuda"),
+            "link_s": torch.empty(cap, dtype=torch.float32, device="cuda"),
+            "pair_score": torch.empty(max(self.n_pairs, 1), dtype=torch.float32, device="cuda"),
+        }
+
+    @staticmethod
+    def _out_struct(o, cap):
+        s = _Out()
+        s.link_off = o["link_off"].data_ptr()
+        s.link_i, s.link_j, s.link_s = o["link_i"].data_ptr(), o["link_j"].data_ptr(), o["link_s"].data_ptr()
+        s.pair_score = o["pair_score"].data_ptr()
+        s.link_capacity = cap
+        return s
+
+    def align(self, params: MineParams, counts, out=None, stream=None):
+        out = out if out is not None else self.new_output()
+        s = self._out_struct(out, out["link_i"].numel())
+        p = params.c()
+        _check(lib().mine_align(self._h, C.byref(p), _ptr(counts), C.byref(s), _stream(stream)), "mine_align")
+        return out
+
+    def mine(self, params: MineParams, out=None, stream=None):
+        """The whole hot path (counts, similarity, alignment, threshold)."""
+        out = out if out is not None else self.new_output()
+        s = self._out_struct(out, out["link_i"].numel())
+        p = params.c()
+        _check(lib().mine_pairs(self._h, C.byref(p), C.byref(s), _stream(stream)), "mine_pairs")
+        return out
+
+
+def links_per_pair(out, n_pairs):
+    """Split a mining output (on any device) into per-pair lists of (i, j, s)."""
+    off = out["link_off"].cpu().numpy()
+    li, lj, ls = (out[k].cpu().numpy() for k in ("link_i", "link_j", "link_s"))
+    return [list(zip(li[off[k]:off[k + 1]].tolist(), lj[off[k]:off[k + 1]].tolist(),
+                     ls[off[k]:off[k + 1]].tolist())) for k in range(n_pairs)]

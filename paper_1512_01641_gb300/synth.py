@@ -345,13 +345,13 @@ def uneven_batch(n_pairs: int = 100_000, n_long: int = 8, long_n: int = 5000,
     sentences (every other long pair planted, target kept square)."""
     rng = np.random.Generator(np.random.PCG64(seed + 1_000_003))
     dic = make_dictionary(rng, 50_000, 50_000)
-    a = make_batch(seed, n_pairs, dic=dic)
+    a = make_batch(seed, n_pairs, dic=dic) if n_pairs else None
     if n_long == 0:
         return a
     sz = np.full(n_long, long_n)
     b = make_batch(seed + 7, n_long, dic=dic, src_sizes=sz, tgt_sizes=sz,
                    keep_square=np.ones(n_long, bool))
-    return concat_batches(a, b)
+    return b if a is None else concat_batches(a, b)
 
 
 def soft_batch(n_pairs: int = 4096, n: int = 100, seed: int = SEED_BASE + 3) -> Batch:

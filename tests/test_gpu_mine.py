@@ -1,0 +1,216 @@
+"""GPU parity of the mining path (counts, similarity, alignment, threshold)
+against the FP64 oracle, through the C ABI.  Tolerances: tests/gpu_parity.py."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1512_01641_gb300 import synth
+
+from gpu_parity import S_TOL, check_alignment, check_counts, per_pair, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+W = (4.0, 4.0, -2.0, 1.0)
+
+
+def _params(thr=0.5, gap=0.3, b=-3.0):
+    from paper_1512_01641_gb300 import miner
+    return miner.MineParams(w=W, b=b, gap=gap, thr=thr)
+
+
+def _edge_batch():
+    # sizes around the 32-row strip and 32-column block edges, single rows and
+    # columns, and very unequal documents
+    ns = [1, 1, 40, 31, 32, 33, 63, 64, 65, 5, 130, 97]
+    ms = [1, 50, 1, 33, 32, 31, 64, 65, 63, 130, 5, 96]
+    return synth.make_batch(77, len(ns), v_src=3000, v_tgt=3000, planted_frac=0.0,
+                            src_sizes=ns, tgt_sizes=ms)
+
+
+def _mixed_batch():
+    return synth.make_batch(78, 60, v_src=5000, v_tgt=5000, size_median=40, size_hi=200)
+
+
+def _long_sentence_batch():
+    # sentences of up to 255 tokens (several 32-lane chunks, 8 counter planes,
+    # the largest hash table) with a small vocabulary, so that counts are high
+    rng = np.random.default_rng(5)
+    v = 400
+    lists = [sorted(set(rng.integers(0, v, size=int(rng.integers(1, 4))).tolist())) for _ in range(v)]
+
+    def sent(n):
+        return sorted(rng.integers(0, v, size=n).tolist())
+    src = [[sent(int(rng.integers(1, 256))) for _ in range(n)] for n in (3, 35, 7)]
+    tgt = [[sent(int(rng.integers(1, 256))) for _ in range(m)] for m in (40, 4, 33)]
+    # one pair where target sentences are full translations (counts = lengths)
+    return synth.from_lists(src, tgt, lists, v_tgt=v)
+
+
+BATCHES = {"single_40x45": synth.single_pair, "edges": _edge_batch, "mixed": _mixed_batch,
+           "long_sentences": _long_sentence_batch}
+
+
+@pytest.fixture(scope="module", params=list(BATCHES))
+def case(request):
+    batch = BATCHES[request.param]()
+    p_all = _params(thr=-1.0)
+    p = _params()
+    ref_all = oracle.mine(batch, p.w, p.b, p.gap, p_all.thr, want_counts=True, want_sim=True)
+    ref = {"links": [[x for x in d if x[2] >= p.thr] for d in ref_all["diag"]]}
+    gpu_all = run_gpu(batch, p_all, want_scores=True)
+    gpu = run_gpu(batch, p, want_counts=False)
+    return request.param, batch, p, ref_all, ref, gpu_all, gpu
+
+
+def test_counts_bit_exact(case):
+    name, batch, p, ref_all, ref, gpu_all, gpu = case
+    check_counts(batch, gpu_all, ref_all)
+
+
+def test_features_and_similarity(case):
+    name, batch, p, ref_all, ref, gpu_all, gpu = case
+    off = gpu_all["plan"].cell_offsets
+    for k in range(batch.n_pairs):
+        c = ref_all["counts"][k]
+        N, M = c.shape[:2]
+        if N * M == 0:
+            continue
+        ls = np.array([len(x) for x in batch.src.doc(k)])
+        lt = np.array([len(x) for x in batch.tgt.doc(k)])
+        feat = per_pair(gpu_all["feat"], off, k, (N, M, 4))
+        s = per_pair(gpu_all["s"], off, k, (N, M))
+        for i in range(0, N, max(1, N // 13)):
+            for j in range(0, M, max(1, M // 11)):
+                f64 = oracle.features(c[i, j, 0], c[i, j, 1], ls[i], lt[j])
+                assert np.array_equal(feat[i, j], f64.astype(np.float32)), (k, i, j)
+        assert np.abs(s - ref_all["sim"][k]).max() <= S_TOL
+
+
+def test_alignment_and_threshold(case):
+    name, batch, p, ref_all, ref, gpu_all, gpu = case
+    ties = check_alignment(batch, p, gpu_all, ref_all, gpu, ref)
+    # unplanted pairs repeat the same (counts, lengths) often, so mathematically
+    # tied alignments are common; each was validated above
+    assert ties <= max(2, batch.n_pairs // 3), f"{ties} near-tie pairs of {batch.n_pairs}"
+
+
+def test_fused_equals_count_then_align(case):
+    name, batch, p, ref_all, ref, gpu_all, gpu = case
+    import torch
+    plan = gpu["plan"]
+    counts = plan.count()
+    out = plan.align(p, counts)
+    torch.cuda.synchronize()
+    for key in ("link_off", "pair_score"):
+        assert torch.equal(out[key][: plan.n_pairs + (key == "link_off")],
+                           gpu["out"][key][: plan.n_pairs + (key == "link_off")]), key
+    n = int(out["link_off"][-1])
+    for key in ("link_i", "link_j", "link_s"):
+        assert torch.equal(out[key][:n], gpu["out"][key][:n]), key
+
+
+def test_deterministic():
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = _mixed_batch()
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        a = plan.mine(_params())
+        b = plan.mine(_params())
+        torch.cuda.synchronize()
+        n = int(a["link_off"][-1])
+        assert torch.equal(a["link_off"], b["link_off"])
+        assert torch.equal(a["pair_score"], b["pair_score"])
+        for key in ("link_i", "link_j", "link_s"):
+            assert torch.equal(a[key][:n], b[key][:n])
+
+
+def test_empty_documents_and_no_pairs():
+    import torch
+    from paper_1512_01641_gb300 import miner
+    dic = [[0], [1, 2], [3]]
+    src = [[], [[0, 1]], [[1], [2, 2]], []]
+    tgt = [[[0]], [], [[1, 3], [2]], []]
+    batch = synth.from_lists(src, tgt, dic, v_tgt=4)
+    p = _params()
+    r = run_gpu(batch, p)
+    ref = oracle.mine(batch, p.w, p.b, p.gap, p.thr)
+    for k in range(4):
+        assert abs(r["score"][k] - ref["score"][k]) <= 1e-6
+        assert [(i, j) for i, j, _ in r["links"][k]] == [(i, j) for i, j, _ in ref["links"][k]]
+    empty = synth.from_lists([], [], dic, v_tgt=4)
+    with miner.Plan(miner.DeviceBatch.from_batch(empty)) as plan:
+        out = plan.mine(p)
+        torch.cuda.synchronize()
+        assert int(out["link_off"][0]) == 0
+
+
+def test_rejects_malformed_inputs():
+    import torch
+    from paper_1512_01641_gb300 import miner
+    good = synth.make_batch(3, 2, v_src=100, v_tgt=100, size_median=6)
+
+    def attempt(mut):
+        b = synth.make_batch(3, 2, v_src=100, v_tgt=100, size_median=6)
+        mut(b)
+        with pytest.raises(miner.MinerError) as e:
+            miner.Plan(miner.DeviceBatch.from_batch(b))
+        assert e.value.code == miner.MINE_EINVAL
+
+    def unsorted(b):
+        b.src.tok[0], b.src.tok[1] = 99, 0  # sentences hold >= 5 tokens
+    attempt(unsorted)
+
+    def bad_id(b):
+        b.tgt.tok[-1] = 100
+    attempt(bad_id)
+
+    def empty_sentence(b):
+        b.src.sent_tok_off[1] = 0
+    attempt(empty_sentence)
+
+    def bad_dict(b):
+        b.dic.tgt[0] = 1000
+    attempt(bad_dict)
+    # the good batch still plans
+    with miner.Plan(miner.DeviceBatch.from_batch(good)):
+        pass
+
+
+@pytest.mark.slow
+def test_wikipedia_batch_sampled_pairs():
+    """10,000 Wikipedia-shaped pairs in one launch; 150 sampled pairs (the largest
+    included) compared in full with the oracle."""
+    batch = synth.wiki_batch()
+    p_all = _params(thr=-1.0)
+    gpu = run_gpu(batch, p_all, want_counts=True)
+    sizes = batch.src.doc_sizes() * batch.tgt.doc_sizes()
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([np.argsort(sizes)[-3:], rng.choice(batch.n_pairs, 147, replace=False)]))
+    sub = batch.subset(pick)
+    ref = oracle.mine(sub, p_all.w, p_all.b, p_all.gap, p_all.thr, want_counts=True, want_sim=True)
+    off = gpu["plan"].cell_offsets
+    sel = {"counts": None, "score": gpu["score"][pick], "links": [gpu["links"][k] for k in pick]}
+    for n, k in enumerate(pick):
+        got = per_pair(gpu["counts"], off, k, ref["counts"][n].shape)
+        assert np.array_equal(got, ref["counts"][n]), k
+    ties = check_alignment(sub, p_all, sel, ref)
+    assert ties <= len(pick) // 20
+
+
+@pytest.mark.slow
+def test_long_pair_5000x5000():
+    """One 5000 x 5000 pair (the long pairs of the uneven batch): full oracle
+    comparison of the pair score and path, sampled cell counts."""
+    batch = synth.uneven_batch(n_pairs=0, n_long=1)
+    p_all = _params(thr=-1.0)
+    gpu = run_gpu(batch, p_all, want_counts=True)
+    ref = oracle.mine(batch, p_all.w, p_all.b, p_all.gap, p_all.thr, want_sim=True)
+    c = gpu["counts"].reshape(5000, 5000, 2)
+    rng = np.random.default_rng(1)
+    src, tgt = batch.src.doc(0), batch.tgt.doc(0)
+    for i, j in rng.integers(0, 5000, size=(400, 2)):
+        assert tuple(c[i, j]) == oracle.counts(src[i], tgt[j], batch.dic)
+    sel = {"score": gpu["score"], "links": gpu["links"]}
+    assert check_alignment(batch, p_all, sel, ref) <= 1
