@@ -136,13 +136,20 @@ int mine_align(mine_plan *plan, const mine_params *params, const uint8_t *counts
 int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
                miner_stream_t stream);
 
+/* Synchronise the stream and report device-side errors raised since the last
+ * check: MINE_ETIMEOUT if a bounded wait of the cooperative fill gave up (its
+ * results are then invalid), MINE_EINVAL if a count table overflowed, else
+ * MINE_OK.  Clears the recorded errors. */
+int mine_plan_check(mine_plan *plan, miner_stream_t stream);
+
 /* Per-kernel timing (profiling aid).  When enabled, every kernel launch of the
  * plan is bracketed by CUDA events on the launching stream and its duration is
  * accumulated per kernel kind.  mine_plan_kernel_times synchronises the last
  * stream used, then writes up to n totals (milliseconds) into host_ms and the
  * matching launch counts into host_launches (either may be NULL); it returns
  * the number of kernel kinds (MINE_KERNEL_KINDS).  Kinds, in order: count,
- * align-fill, traceback, link-scan, link-copy, score. */
+ * fill, walk (traceback), links (link scoring, pair sums, compaction), scan,
+ * score. */
 #define MINE_KERNEL_KINDS 6
 int mine_plan_set_timing(mine_plan *plan, int enable);
 int mine_plan_kernel_times(mine_plan *plan, float *host_ms, int64_t *host_launches, int n);

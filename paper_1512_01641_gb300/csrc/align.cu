@@ -12,73 +12,252 @@
 // ~1e-7 absolute precision however large the matrix (an absolute H of 5000
 // would only keep ~5e-4), and the comparisons that pick the path are made on
 // exactly the quantities the definition compares, shifted by a common term.
-// H(N,M) itself is the score of the chosen path, summed in FP64 during the
+// H(N,M) itself is the score of the chosen path, summed in FP64 after the
 // traceback.
 //
-// One warp owns a pair and sweeps it in strips of 32 rows (lane = row),
-// skewed by one column per lane so that lane i handles column t - i at step
-// t (the anti-diagonal wavefront of Figure 2, 32 cells wide); a(i,j) comes
-// from the lane above by a register shuffle, and the last lane's outputs
-// seed the next strip through a per-pair boundary row.
+// Fill: a warp owns 32 rows (lane = row) and sweeps columns with a skew of one
+// column per lane, so lane i handles column t - i at step t -- the
+// anti-diagonal wavefront of Figure 2, 32 cells wide.  a(i,j) comes from the
+// lane above through a register shuffle; the last lane's outputs seed the next
+// strip through a boundary row.  Similarities of a 32 x 32 block are computed
+// before its 32 DP steps, into registers in a rotated order (value for column
+// c of lane i sits at index (c + i) mod 32) so that step u reads register u
+// in every lane; the DP chain then carries only max/compare/add per step.
+// A small pair is one work item (all its strips, all columns).  A large pair
+// is cut into 32-row x cw-column tiles, each its own work item; a tile waits
+// (bounded) on the completion flags of the tile above and the tile to its
+// left, whose boundary row/column it reads from global memory.  Work items are
+// handed out by an atomic counter in the planner's order.
 #include "kernels.h"
 
 namespace gbm {
 namespace {
 
-constexpr int kAlignWarps = 4;
+constexpr int kFillWarps = 4;
+constexpr int kTailWarps = 4;
 
-__global__ void __launch_bounds__(32 * kAlignWarps)
-nw_counts_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
-                 const int32_t *__restrict__ order, int64_t n_pairs, DevParams P,
-                 const uint8_t *__restrict__ counts, uint64_t *__restrict__ tb,
-                 float *__restrict__ hrow) {
+// Bounded wait for a nonzero tile flag.
+__device__ bool wait_flag(const int32_t *f, int64_t limit) {
+    for (int64_t it = 0; it < limit; ++it) {
+        if (ld_acquire(f) != 0) return true;
+        __nanosleep(200);
+    }
+    return false;
+}
+
+struct FillCtx {
+    int lane, N, M, c0, c1, r;
+    bool rv;
+    float two_p;
+    SimRow row;
+    SimConst k;
+    const uchar2 *rowp;   // counts of row r
+    const int64_t *tsent; // target sentence offsets of the pair
+    SimCol *colv;         // shared: per-column similarity constants of the current block
+    DevParams P;
+};
+
+// One 32-column block iteration of a strip sweep.  cur receives the
+// similarities of block jb (rotated); prev holds block jb-1.  rc/rp are the
+// 64-bit traceback registers of this and the previous iteration.
+__device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, bool first_strip,
+                                           const float *__restrict__ hrow, float *__restrict__ hrow_w,
+                                           float (&cur)[32], const float (&prev)[32], uint64_t &rc,
+                                           const uint64_t &rp, float &a_down, float &b,
+                                           uint64_t *__restrict__ tb_strip) {
+    const int lane = C.lane;
+    const int col_base = C.c0 + 32 * jb;
+    const bool lane_col = col_base + lane < C.c1;
+    // UP candidates of the first row of the strip for the 32 columns of this block
+    const float hv = first_strip ? -C.two_p : (lane_col ? __ldcg(hrow + col_base + lane) : 0.0f);
+    if (jb < nb) {
+        __syncwarp();
+        C.colv[lane] = sim_col(lane_col ? (int)(C.tsent[col_base + lane + 1] - C.tsent[col_base + lane]) : 1, C.P);
+        __syncwarp();
+#pragma unroll
+        for (int x = 0; x < 32; ++x) {
+            const int c = (x - lane) & 31;
+            const int col = col_base + c;
+            float v = 0.0f;
+            if (C.rv && col < C.c1) {
+                const uchar2 q = C.rowp[col];
+                v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
+            }
+            cur[x] = v;
+        }
+    }
+    rc = 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        float a_up = __shfl_up_sync(kFull, a_down, 1);
+        const float h0 = __shfl_sync(kFull, hv, u);
+        if (lane == 0) a_up = h0;
+        const int j = col_base + u - lane;
+        const float sv = (u >= lane) ? cur[u] : prev[u];
+        if (C.rv && j >= C.c0 && j < C.c1) {
+            const float d = fmaxf(fmaxf(sv, a_up), b);
+            const uint64_t bits = (d == a_up) ? (uint64_t)kUp << (2 * u)
+                                              : ((d == b) ? (uint64_t)kLeft << (2 * u) : 0ull);
+            rc |= bits;
+            const float e = __fsub_rn(d, C.two_p);
+            const float nb2 = __fsub_rn(e, a_up);
+            a_down = __fsub_rn(e, b);
+            b = nb2;
+            if (lane == 31) __stcg(hrow_w + j, a_down);
+        }
+    }
+    // the word of block jb-1 is complete: its columns came at steps u >= lane
+    // of iteration jb-1 and u < lane of iteration jb
+    if (jb > 0) {
+        const int sh = 2 * lane;
+        const uint64_t w = (rp >> sh) | (sh ? (rc << (64 - sh)) : 0ull);
+        tb_strip[(int64_t)((C.c0 >> 5) + jb - 1) * 32 + lane] = w;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kFillWarps)
+fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
+            const FillItem *__restrict__ items, int64_t n_items, DevParams P,
+            const uint8_t *__restrict__ counts, AlignScratch S, int64_t wait_limit) {
+    __shared__ SimCol colv_all[kFillWarps][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    FillCtx C;
+    C.lane = lane;
+    C.P = P;
+    C.two_p = __fadd_rn(P.gap, P.gap);
+    C.k = sim_const(P);
+    C.colv = colv_all[warp];
+    for (;;) {
+        int64_t it = 0;
+        if (lane == 0) it = atomicAdd(S.queue, 1);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const FillItem w = items[it];
+        const PairGeom g = geom[w.pair];
+        C.N = g.n;
+        C.M = g.m;
+        if (C.N == 0 || C.M == 0) continue;
+        C.c0 = w.cj * g.cw;
+        C.c1 = min(C.M, C.c0 + g.cw);
+        const bool tiled = g.flag_off >= 0;
+        const int nblk_pair = (C.M + 31) >> 5;
+        const int nb = (C.c1 - C.c0 + 31) >> 5;
+        const int64_t sbase = src.doc[w.pair];
+        C.tsent = tgt.sent + tgt.doc[w.pair];
+        float *hrow = S.hrow + g.hrow_off;
+        for (int s = w.s0; s < w.s1; ++s) {
+            if (tiled) {
+                if (lane == 0) {
+                    bool ok = true;
+                    if (s > 0) ok &= wait_flag(S.flags + g.flag_off + (int64_t)(s - 1) * g.nchunk + w.cj, wait_limit);
+                    if (w.cj > 0) ok &= wait_flag(S.flags + g.flag_off + (int64_t)s * g.nchunk + w.cj - 1, wait_limit);
+                    if (!ok) atomicOr(S.status, kStTimeout);
+                }
+                __syncwarp();
+                if (s > 0) (void)ld_acquire(S.flags + g.flag_off + (int64_t)(s - 1) * g.nchunk + w.cj);
+                if (w.cj > 0) (void)ld_acquire(S.flags + g.flag_off + (int64_t)s * g.nchunk + w.cj - 1);
+            }
+            C.r = 32 * s + lane;
+            C.rv = C.r < C.N;
+            const int ls = C.rv ? (int)(src.sent[sbase + C.r + 1] - src.sent[sbase + C.r]) : 1;
+            C.row = sim_row(ls, P);
+            C.rowp = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)C.r * C.M;
+            float b = -C.two_p;
+            if (C.c0 > 0 && C.rv) b = __ldcg(S.vcol + g.vcol_off + C.r);
+            float a_down = 0.0f;
+            float A[32], B[32];
+#pragma unroll
+            for (int x = 0; x < 32; ++x) B[x] = 0.0f;
+            uint64_t RA = 0, RB = 0;
+            uint64_t *tb_strip = S.tb + g.tb_off + (int64_t)s * nblk_pair * 32;
+            for (int jb = 0; jb <= nb; jb += 2) {
+                fill_block(C, jb, nb, s == 0, hrow, hrow, A, B, RA, RB, a_down, b, tb_strip);
+                if (jb + 1 > nb) break;
+                fill_block(C, jb + 1, nb, s == 0, hrow, hrow, B, A, RB, RA, a_down, b, tb_strip);
+            }
+            if (tiled) {
+                if (C.c1 < C.M && C.rv) __stcg(S.vcol + g.vcol_off + C.r, b);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release(S.flags + g.flag_off + (int64_t)s * g.nchunk + w.cj, 1);
+            } else {
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// Walk back from (N,M) to (0,0), one warp per pair.  The 32 x 32 block of
+// traceback codes around the current cell sits in registers (lane l holds the
+// word of row l of the block), so a step costs a shuffle; leaving the block
+// loads the next one with one coalesced 256-byte read.  Diagonal cells are
+// written to the END of the pair's link window in ascending order.
+__global__ void __launch_bounds__(32 * kTailWarps)
+walk_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, AlignScratch S) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const float p = P.gap;
-    const float two_p = __fadd_rn(p, p);
-    for (int64_t it = warp0; it < n_pairs; it += nwarps) {
-        const int32_t k = order[it];
+    for (int64_t k = warp0; k < n_pairs; k += nwarps) {
         const PairGeom g = geom[k];
         const int N = g.n, M = g.m;
-        if (N == 0 || M == 0) continue;
         const int nblk = (M + 31) >> 5;
-        const int64_t sbase = src.doc[k], tbase = tgt.doc[k];
-        float *hb = hrow + g.hrow_off;
-        uint64_t *tbp = tb + g.tb_off;
-        const int nstrips = (N + 31) >> 5;
-        for (int s = 0; s < nstrips; ++s) {
-            const int r = 32 * s + lane;
-            const bool rv = r < N;
-            const int ls = rv ? (int)(src.sent[sbase + r + 1] - src.sent[sbase + r]) : 1;
-            const uchar2 *crow = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)r * M;
-            float b = -two_p, a_down = 0.0f;
-            uint64_t acc = 0;
-            for (int t = 0; t < M + 31; ++t) {
-                float a_up = __shfl_up_sync(kFull, a_down, 1);
-                const int j = t - lane;
-                if (lane == 0) a_up = (s == 0) ? -two_p : (t < M ? hb[t] : 0.0f);
-                if (rv && j >= 0 && j < M) {
-                    const uchar2 c = crow[j];
-                    const int lt = (int)(tgt.sent[tbase + j + 1] - tgt.sent[tbase + j]);
-                    const float sv = similarity(c.x, c.y, ls, lt, P);
-                    const float d = fmaxf(fmaxf(sv, a_up), b);
-                    const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : kDiag);
-                    const float e = __fsub_rn(d, two_p);
-                    const float nb = __fsub_rn(e, a_up);
-                    a_down = __fsub_rn(e, b);
-                    b = nb;
-                    acc |= (uint64_t)code << (2 * (j & 31));
-                    if ((j & 31) == 31 || j == M - 1) {
-                        tbp[((int64_t)s * nblk + (j >> 5)) * 32 + lane] = acc;
-                        acc = 0;
-                    }
-                    if (lane == 31) hb[j] = a_down;
-                }
+        const int cap = min(N, M);
+        const uint64_t *tbp = S.tb + g.tb_off;
+        int i = N, j = M, n = 0;
+        int bs = -1, bj = -1;  // strip and column block held in `word`
+        uint64_t word = 0;
+        while (i > 0 && j > 0) {
+            const int rr = i - 1, cc = j - 1;
+            if ((rr >> 5) != bs || (cc >> 5) != bj) {
+                bs = rr >> 5;
+                bj = cc >> 5;
+                word = tbp[((int64_t)bs * nblk + bj) * 32 + lane];
             }
-            __syncwarp();
+            const uint64_t wr = __shfl_sync(kFull, word, rr & 31);
+            const uint32_t code = (uint32_t)(wr >> (2 * (cc & 31))) & 3u;
+            if (code == kUp) {
+                --i;
+            } else if (code == kLeft) {
+                --j;
+            } else {
+                if (lane == 0) {
+                    const int64_t at = g.link_off + cap - 1 - n;
+                    S.diag_i[at] = rr;
+                    S.diag_j[at] = cc;
+                }
+                ++n;
+                --i;
+                --j;
+            }
         }
+        if (lane == 0) S.n_diag[k] = n;
     }
+}
+
+// Exclusive scan of int32 counts into int64 offsets (one block; n is at most a
+// few hundred thousand, so a strided serial pass per thread is enough).
+__global__ void __launch_bounds__(1024)
+scan_kernel(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t a = t * chunk, b = min(n, a + chunk);
+    int64_t sum = 0;
+    for (int64_t x = a; x < b; ++x) sum += in[x];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int64_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - sum;
+    for (int64_t x = a; x < b; ++x) {
+        out[x] = run;
+        run += in[x];
+    }
+    if (t == 1023) out[n] = part[1023];
 }
 
 // (ms, mt) of one cell by warp vote: lanes hold target positions (in chunks
@@ -117,119 +296,96 @@ __device__ __forceinline__ void ballot_counts(const int32_t *__restrict__ stok, 
     mt = mtc;
 }
 
-// Walk back from (N,M) to (0,0) (one warp per pair).  A DIAG step links the
-// cell; its counts are recomputed by warp vote and its similarity by the same
-// function the fill used, and the link is kept iff s >= thr.  The path score
-// (= H(N,M)) is summed in FP64.  Kept links land at the END of the pair's
-// capacity window, so that they read in ascending order.
-__global__ void __launch_bounds__(32 * kAlignWarps)
-traceback_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
-                 int64_t n_pairs, DevParams P, const uint64_t *__restrict__ tb,
-                 int32_t *__restrict__ scr_i, int32_t *__restrict__ scr_j, float *__restrict__ scr_s,
-                 int32_t *__restrict__ n_links, float *__restrict__ pair_score) {
+// Similarity of every diagonal cell of every path: one warp per cell,
+// counts by warp vote, similarity by the same helper the fill used.
+__global__ void __launch_bounds__(32 * kTailWarps)
+link_score_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
+                  int64_t n_pairs, DevParams P, AlignScratch S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = S.diag_off[n_pairs];
+    const SimConst K = sim_const(P);
+    for (int64_t f = warp0; f < total; f += nwarps) {
+        // pair owning flat diagonal f: last k with diag_off[k] <= f
+        int64_t lo = 0, hi = n_pairs - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (S.diag_off[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int64_t k = lo;
+        const PairGeom g = geom[k];
+        const int nd = S.n_diag[k];
+        const int64_t at = g.link_off + min(g.n, g.m) - nd + (f - S.diag_off[k]);
+        const int rr = S.diag_i[at], cc = S.diag_j[at];
+        const int64_t sb = src.doc[k] + rr, tbs = tgt.doc[k] + cc;
+        const int64_t s0 = src.sent[sb], s1 = src.sent[sb + 1];
+        const int64_t t0 = tgt.sent[tbs], t1 = tgt.sent[tbs + 1];
+        int ms, mt;
+        ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
+        if (lane == 0)
+            S.diag_s[at] = similarity(ms, mt, sim_row((int)(s1 - s0), P), sim_col((int)(t1 - t0), P), K);
+    }
+}
+
+// Per pair: H(N,M) = sum of the path's similarities (FP64, fixed order) minus
+// p per gap step, and the number of kept links (s >= thr).
+__global__ void __launch_bounds__(32 * kTailWarps)
+pair_sum_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, DevParams P, AlignScratch S,
+                float *__restrict__ pair_score) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t k = warp0; k < n_pairs; k += nwarps) {
         const PairGeom g = geom[k];
-        const int N = g.n, M = g.m;
-        const int nblk = (M + 31) >> 5;
-        const int cap = min(N, M);
-        const int64_t sbase = src.doc[k], tbase = tgt.doc[k];
-        const uint64_t *tbp = tb + g.tb_off;
-        int i = N, j = M, n = 0;
-        double score = 0.0;
-        int64_t cached = -1;
-        uint64_t word = 0;
-        while (i > 0 || j > 0) {
-            uint32_t code;
-            if (i == 0) {
-                code = kLeft;
-            } else if (j == 0) {
-                code = kUp;
-            } else {
-                const int rr = i - 1, cc = j - 1;
-                const int64_t widx = ((int64_t)(rr >> 5) * nblk + (cc >> 5)) * 32 + (rr & 31);
-                if (widx != cached) {
-                    word = tbp[widx];
-                    cached = widx;
-                }
-                code = (uint32_t)(word >> (2 * (cc & 31))) & 3u;
-            }
-            if (code == kDiag) {
-                const int rr = i - 1, cc = j - 1;
-                const int64_t s0 = src.sent[sbase + rr], s1 = src.sent[sbase + rr + 1];
-                const int64_t t0 = tgt.sent[tbase + cc], t1 = tgt.sent[tbase + cc + 1];
-                int ms, mt;
-                ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
-                const float sv = similarity(ms, mt, (int)(s1 - s0), (int)(t1 - t0), P);
-                score += (double)sv;
-                if (sv >= P.thr) {
-                    if (lane == 0) {
-                        const int64_t at = g.link_off + cap - 1 - n;
-                        scr_i[at] = rr;
-                        scr_j[at] = cc;
-                        scr_s[at] = sv;
-                    }
-                    ++n;
-                }
-                --i;
-                --j;
-            } else {
-                score -= (double)P.gap;
-                if (code == kUp) --i; else --j;
-            }
+        const int nd = S.n_diag[k];
+        const int64_t base = g.link_off + min(g.n, g.m) - nd;
+        double sum = 0.0;
+        int kept = 0;
+        for (int x = lane; x < nd; x += 32) {
+            const float s = S.diag_s[base + x];
+            sum += (double)s;
+            kept += s >= P.thr;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sum += __shfl_xor_sync(kFull, sum, off);
+            kept += __shfl_xor_sync(kFull, kept, off);
         }
         if (lane == 0) {
-            n_links[k] = n;
-            pair_score[k] = (float)score;
+            const int gaps = g.n + g.m - 2 * nd;
+            pair_score[k] = (float)(sum - (double)P.gap * (double)gaps);
+            S.n_links[k] = kept;
         }
     }
 }
 
-// Exclusive scan of the per-pair link counts (one block; the pair count is a
-// few hundred thousand at most, so a strided serial pass per thread is enough).
-__global__ void __launch_bounds__(1024)
-scan_kernel(const int32_t *__restrict__ n_links, int64_t n_pairs, int64_t *__restrict__ link_off) {
-    __shared__ int64_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = (n_pairs + 1023) / 1024;
-    const int64_t a = t * chunk, b = min(n_pairs, a + chunk);
-    int64_t sum = 0;
-    for (int64_t x = a; x < b; ++x) sum += n_links[x];
-    part[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int64_t v = t >= off ? part[t - off] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int64_t run = part[t] - sum;
-    for (int64_t x = a; x < b; ++x) {
-        link_off[x] = run;
-        run += n_links[x];
-    }
-    if (t == 1023) link_off[n_pairs] = part[1023];
-}
-
-__global__ void __launch_bounds__(32 * kAlignWarps)
-copy_links_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, const int32_t *__restrict__ n_links,
-                  const int32_t *__restrict__ scr_i, const int32_t *__restrict__ scr_j,
-                  const float *__restrict__ scr_s, const int64_t *__restrict__ link_off,
-                  int32_t *__restrict__ out_i, int32_t *__restrict__ out_j, float *__restrict__ out_s) {
+// Kept links of each pair, compacted in ascending order at link_off[k].
+__global__ void __launch_bounds__(32 * kTailWarps)
+copy_links_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, DevParams P, AlignScratch S,
+                  const int64_t *__restrict__ link_off, int32_t *__restrict__ out_i,
+                  int32_t *__restrict__ out_j, float *__restrict__ out_s) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t k = warp0; k < n_pairs; k += nwarps) {
         const PairGeom g = geom[k];
-        const int n = n_links[k];
-        const int cap = min(g.n, g.m);
-        const int64_t from = g.link_off + cap - n, to = link_off[k];
-        for (int x = lane; x < n; x += 32) {
-            out_i[to + x] = scr_i[from + x];
-            out_j[to + x] = scr_j[from + x];
-            out_s[to + x] = scr_s[from + x];
+        const int nd = S.n_diag[k];
+        const int64_t base = g.link_off + min(g.n, g.m) - nd;
+        int64_t to = link_off[k];
+        for (int x0 = 0; x0 < nd; x0 += 32) {
+            const int x = x0 + lane;
+            const bool in = x < nd;
+            const float s = in ? S.diag_s[base + x] : 0.0f;
+            const bool keep = in && s >= P.thr;
+            const uint32_t m = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int64_t o = to + __popc(m & ((1u << lane) - 1u));
+                out_i[o] = S.diag_i[base + x];
+                out_j[o] = S.diag_j[base + x];
+                out_s[o] = s;
+            }
+            to += __popc(m);
         }
     }
 }
@@ -242,12 +398,13 @@ score_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, De
     const PairGeom g = geom[k];
     const int64_t sbase = src.doc[k], tbase = tgt.doc[k];
     const int64_t cells = (int64_t)g.n * g.m;
+    const SimConst K = sim_const(P);
     for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) {
         const int i = (int)(c / g.m), j = (int)(c % g.m);
         const int ls = (int)(src.sent[sbase + i + 1] - src.sent[sbase + i]);
         const int lt = (int)(tgt.sent[tbase + j + 1] - tgt.sent[tbase + j]);
         const int ms = counts[2 * (g.cell_off + c)], mt = counts[2 * (g.cell_off + c) + 1];
-        s[g.cell_off + c] = similarity(ms, mt, ls, lt, P);
+        s[g.cell_off + c] = similarity(ms, mt, sim_row(ls, P), sim_col(lt, P), K);
         if (feat) {
             float f[4];
             features(ms, mt, ls, lt, f);
@@ -257,55 +414,66 @@ score_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, De
     }
 }
 
-int grid_for(int64_t warps_wanted, int warps_per_block, int n_sms, int per_sm) {
-    int64_t blocks = (warps_wanted + warps_per_block - 1) / warps_per_block;
-    int64_t cap = (int64_t)n_sms * per_sm;
+int tail_grid(int64_t warps_wanted, int n_sms) {
+    int64_t blocks = (warps_wanted + kTailWarps - 1) / kTailWarps;
+    int64_t cap = (int64_t)n_sms * 16;
     if (blocks > cap) blocks = cap;
     return (int)(blocks < 1 ? 1 : blocks);
 }
 
 }  // namespace
 
-cudaError_t launch_nw_counts(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
-                             const int32_t *order, int64_t n_pairs, const DevParams &P,
-                             const uint8_t *counts, uint64_t *tb, float *hrow, int n_sms,
-                             cudaStream_t st) {
-    if (n_pairs == 0) return cudaSuccess;
-    int grid = grid_for(n_pairs, kAlignWarps, n_sms, 16);
-    nw_counts_kernel<<<grid, 32 * kAlignWarps, 0, st>>>(src, tgt, geom, order, n_pairs, P, counts, tb, hrow);
+cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
+                        const FillItem *items, int64_t n_items, const DevParams &P,
+                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit,
+                        int n_sms, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_kernel, 32 * kFillWarps, 0);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t want = (n_items + kFillWarps - 1) / kFillWarps;
+    if (blocks > want) blocks = want;
+    e = cudaMemsetAsync(S.queue, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    fill_kernel<<<(unsigned)blocks, 32 * kFillWarps, 0, st>>>(src, tgt, geom, items, n_items, P, counts, S,
+                                                               wait_limit);
     return cudaGetLastError();
 }
 
-cudaError_t launch_traceback(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
-                             const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                             const uint64_t *tb, int32_t *scr_i, int32_t *scr_j, float *scr_s,
-                             int32_t *n_links, float *pair_score, cudaStream_t st) {
+cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
+                        cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    int dev = 0, n_sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = grid_for(n_pairs, kAlignWarps, n_sms, 16);
-    traceback_kernel<<<grid, 32 * kAlignWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, tb, scr_i, scr_j,
-                                                        scr_s, n_links, pair_score);
+    walk_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const int32_t *n_links, int64_t n_pairs, int64_t *link_off, cudaStream_t st) {
-    scan_kernel<<<1, 1024, 0, st>>>(n_links, n_pairs, link_off);
+cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t st) {
+    scan_kernel<<<1, 1024, 0, st>>>(in, n, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const int32_t *n_links,
-                              const int32_t *scr_i, const int32_t *scr_j, const float *scr_s,
-                              const int64_t *link_off, int32_t *out_i, int32_t *out_j, float *out_s,
-                              cudaStream_t st) {
+cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
+                              const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                              const AlignScratch &S, int n_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    int dev = 0, n_sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = grid_for(n_pairs, kAlignWarps, n_sms, 16);
-    copy_links_kernel<<<grid, 32 * kAlignWarps, 0, st>>>(geom, n_pairs, n_links, scr_i, scr_j, scr_s, link_off,
-                                                         out_i, out_j, out_s);
+    link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_sum(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                            const AlignScratch &S, float *pair_score, int n_sms, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    pair_sum_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, P, S, pair_score);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                              const AlignScratch &S, const int64_t *link_off, int32_t *out_i,
+                              int32_t *out_j, float *out_s, int n_sms, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    copy_links_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, P, S, link_off,
+                                                                             out_i, out_j, out_s);
     return cudaGetLastError();
 }
 

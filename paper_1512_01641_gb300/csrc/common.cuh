@@ -42,16 +42,70 @@ __device__ __forceinline__ void features(int ms, int mt, int ls, int lt, float f
 }
 
 // Similarity s = sigmoid(w . f + b) (Section 4: a linear decision value
-// squashed into [0,1]).  Every kernel that needs s calls this one function with
-// explicitly rounded operations, so all of them produce the same float.
-__device__ __forceinline__ float similarity(int ms, int mt, int ls, int lt, const DevParams &P) {
-    float f[4];
-    features(ms, mt, ls, lt, f);
-    float z = __fmaf_rn(P.w[0], f[0], P.b);
-    z = __fmaf_rn(P.w[1], f[1], z);
-    z = __fmaf_rn(P.w[2], f[2], z);
-    z = __fmaf_rn(P.w[3], f[3], z);
-    return __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-z)));
+// squashed into [0,1]), evaluated without divisions.  Since
+// |ls-lt|/max + min/max = 1, the two length features fold into
+//   w2 f2 + w3 f3 = w2 + (w3 - w2) * min(ls/lt, lt/ls),
+// and with y = -log2(e) * (w . f + b) the similarity is 1 / (1 + 2^y):
+//   y = A_i * ms + B_j * mt + C0 + C1 * min(ls / lt, lt / ls)
+// where A_i = -log2(e) w0 / ls depends on the source sentence only, B_j on the
+// target sentence only.  Every kernel that needs s goes through these
+// helpers with explicitly rounded operations, so all of them produce the same
+// float for the same cell.
+constexpr float kLog2e = 1.4426950408889634f;
+
+struct SimRow {  // per source sentence
+    float a;     // -log2(e) w0 / ls
+    float len;   // ls
+    float rlen;  // 1 / ls
+};
+struct SimCol {  // per target sentence
+    float b;     // -log2(e) w1 / lt
+    float len;   // lt
+    float rlen;  // 1 / lt
+    float pad;
+};
+struct SimConst {
+    float c0;  // -log2(e) (w2 + b)
+    float c1;  // -log2(e) (w3 - w2)
+};
+
+__device__ __forceinline__ SimConst sim_const(const DevParams &P) {
+    return {__fmul_rn(-kLog2e, __fadd_rn(P.w[2], P.b)), __fmul_rn(-kLog2e, __fsub_rn(P.w[3], P.w[2]))};
+}
+__device__ __forceinline__ SimRow sim_row(int ls, const DevParams &P) {
+    const float r = __frcp_rn((float)ls);
+    return {__fmul_rn(__fmul_rn(-kLog2e, P.w[0]), r), (float)ls, r};
+}
+__device__ __forceinline__ SimCol sim_col(int lt, const DevParams &P) {
+    const float r = __frcp_rn((float)lt);
+    return {__fmul_rn(__fmul_rn(-kLog2e, P.w[1]), r), (float)lt, r, 0.0f};
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float similarity(int ms, int mt, const SimRow &r, const SimCol &c, const SimConst &k) {
+    const float q = fminf(__fmul_rn(r.len, c.rlen), __fmul_rn(c.len, r.rlen));
+    float y = __fmaf_rn(k.c1, q, k.c0);
+    y = __fmaf_rn(c.b, (float)mt, y);
+    y = __fmaf_rn(r.a, (float)ms, y);
+    return rcp_approx(__fadd_rn(1.0f, ex2_approx(y)));
+}
+
+// PTX acquire/release accesses for the tile flags of the cooperative fill.
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Multiplicative hash of a token id into a table of 2^log_slots slots.

@@ -1,4 +1,5 @@
-// Launch wrappers shared between the kernel translation units and the plan.
+// Launch wrappers and device-side layouts shared between the kernel
+// translation units and the plan.
 #pragma once
 
 #include <cstdint>
@@ -29,9 +30,35 @@ struct CountItem {
 struct PairGeom {
     int64_t cell_off;  // first cell of the pair in per-cell buffers
     int64_t tb_off;    // first uint64 traceback word of the pair
-    int64_t link_off;  // first link slot (capacity min(N,M) per pair)
-    int64_t hrow_off;  // first float of the pair's boundary row buffer (M floats)
+    int64_t link_off;  // first slot of the pair's window of min(N,M) link slots
+    int64_t hrow_off;  // first float of the pair's boundary row (M floats)
+    int64_t vcol_off;  // first float of the pair's boundary column (N floats)
+    int64_t flag_off;  // first tile flag (nstrips * nchunk ints), -1 if one warp does the pair
     int32_t n, m;      // sentence counts
+    int32_t cw;        // fill column chunk width (multiple of 32)
+    int32_t nchunk;    // number of column chunks
+};
+
+// One fill work item: strips [s0, s1) of column chunk cj of a pair.
+struct FillItem {
+    int32_t pair;
+    int32_t s0, s1;
+    int32_t cj;
+};
+
+// Plan-owned scratch of the alignment kernels.
+struct AlignScratch {
+    uint64_t *tb;      // traceback words: [strip][column block][row in strip], 2 bits per cell
+    float *hrow;       // boundary row per pair (UP candidates of the next strip)
+    float *vcol;       // boundary column per pair (LEFT candidates of the next chunk)
+    int32_t *flags;    // tile completion flags
+    int32_t *queue;    // dynamic work counter of the fill
+    uint32_t *status;  // error bits
+    int32_t *diag_i, *diag_j;  // diagonal cells of each path, in the pair's link window
+    float *diag_s;
+    int32_t *n_diag;
+    int64_t *diag_off;  // exclusive scan of n_diag (n_pairs+1)
+    int32_t *n_links;
 };
 
 cudaError_t launch_validate_corpus(const DevCorpus &c, int64_t n_sents, int64_t n_tok, int32_t vocab,
@@ -48,24 +75,28 @@ cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairG
                          int64_t n_pairs, const DevParams &P, const uint8_t *counts, float *s,
                          float *feat, cudaStream_t st);
 
-cudaError_t launch_nw_counts(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
-                             const int32_t *order, int64_t n_pairs, const DevParams &P,
-                             const uint8_t *counts, uint64_t *tb, float *hrow, int n_sms,
-                             cudaStream_t st);
+cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
+                        const FillItem *items, int64_t n_items, const DevParams &P,
+                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit,
+                        int n_sms, cudaStream_t st);
 
-cudaError_t launch_traceback(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
-                             const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                             const uint64_t *tb, int32_t *scr_i, int32_t *scr_j, float *scr_s,
-                             int32_t *n_links, float *pair_score, cudaStream_t st);
+cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
+                        cudaStream_t st);
 
-cudaError_t launch_scan(const int32_t *n_links, int64_t n_pairs, int64_t *link_off, cudaStream_t st);
+cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t st);
 
-cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const int32_t *n_links,
-                              const int32_t *scr_i, const int32_t *scr_j, const float *scr_s,
-                              const int64_t *link_off, int32_t *out_i, int32_t *out_j, float *out_s,
-                              cudaStream_t st);
+cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
+                              const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                              const AlignScratch &S, int n_sms, cudaStream_t st);
+
+cudaError_t launch_pair_sum(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                            const AlignScratch &S, float *pair_score, int n_sms, cudaStream_t st);
+
+cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
+                              const AlignScratch &S, const int64_t *link_off, int32_t *out_i,
+                              int32_t *out_j, float *out_s, int n_sms, cudaStream_t st);
 
 // Kernel kinds of the per-kernel timing hook (order of MINE_KERNEL_KINDS).
-enum KernelKind { kKCount = 0, kKFill, kKTraceback, kKScan, kKCopy, kKScore, kKinds };
+enum KernelKind { kKCount = 0, kKFill, kKWalk, kKLinks, kKScan, kKScore, kKinds };
 
 }  // namespace gbm

@@ -102,21 +102,26 @@ cudaError_t launch_block_tokens(const DevCorpus &tgt, const PairGeom *geom, int6
 
 using namespace gbm;
 
+// Planner knobs (defaults; the tuner may override them per plan).
+struct PlanKnobs {
+    int64_t tile_min_cells = 1 << 18;  // pairs with at least this many cells are tiled
+    int tile_min_rows = 64;            // ... and at least this many rows
+    int tile_cols = 128;               // column chunk width of a tile (multiple of 32)
+    int64_t wait_limit = 1 << 24;      // bounded spin iterations of a tile wait (~200 ns each)
+};
+
 struct mine_plan {
     DevCorpus src{}, tgt{};
     DevDict dict{};
-    int64_t n_pairs = 0, n_cells = 0, link_cap = 0, n_items = 0;
+    int64_t n_pairs = 0, n_cells = 0, link_cap = 0, n_count_items = 0, n_fill_items = 0, n_flags = 0;
     std::vector<int64_t> cell_off_h;
+    std::vector<PairGeom> geom_h;
+    PlanKnobs knobs;
     PairGeom *geom = nullptr;
-    int32_t *order = nullptr;
-    CountItem *items = nullptr;
+    CountItem *count_items = nullptr;
+    FillItem *fill_items = nullptr;
     uint8_t *counts = nullptr;
-    uint64_t *tb = nullptr;
-    float *hrow = nullptr;
-    int32_t *scr_i = nullptr, *scr_j = nullptr;
-    float *scr_s = nullptr;
-    int32_t *n_links = nullptr;
-    uint32_t *status = nullptr;
+    AlignScratch S{};
     int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens]
     int log_slots = 11, planes = 5, n_sms = 1, device = 0;
     // per-kernel timing hook
@@ -162,26 +167,133 @@ static void drain_pending(mine_plan *p) {
     p->pending.clear();
 }
 
-#define MINE_CK(x)                                   \
-    do {                                             \
-        cudaError_t e_ = (x);                        \
-        if (e_ != cudaSuccess) {                     \
-            g_last_cuda = (int)e_;                   \
-            return MINE_ECUDA;                       \
-        }                                            \
+#define MINE_CK(x)                   \
+    do {                             \
+        cudaError_t e_ = (x);        \
+        if (e_ != cudaSuccess) {     \
+            g_last_cuda = (int)e_;   \
+            return MINE_ECUDA;       \
+        }                            \
     } while (0)
 
 static void plan_free(mine_plan *p) {
     if (!p) return;
     drain_pending(p);
-    void *bufs[] = {p->geom, p->order, p->items, p->counts, p->tb, p->hrow, p->scr_i,
-                    p->scr_j, p->scr_s, p->n_links, p->status, p->stats};
+    void *bufs[] = {p->geom, p->count_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
+                    p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
+                    p->S.diag_off, p->S.n_links, p->stats};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete p;
 }
 
-static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st);
+static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st) {
+    int64_t blocks = std::min<int64_t>((d->v_src + 255) / 256, 4096);
+    gbm::validate_dict_kernel<<<(unsigned)blocks, 256, 0, st>>>(DevDict{d->off, d->tgt}, d->v_src, d->v_tgt,
+                                                                d->n_entries, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_last_cuda = (int)e;
+        return MINE_ECUDA;
+    }
+    return MINE_OK;
+}
+
+// Geometry, tiling and work order.  Tiled pairs are cut into 32-row x
+// tile_cols tiles listed in anti-diagonal order (every tile after the tile
+// above it and the tile to its left); whole small pairs (largest first) are
+// interleaved between the diagonals so that warps find ready work while the
+// wavefronts of the large pairs advance.
+static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const std::vector<int64_t> &td,
+                           std::vector<CountItem> &citems, std::vector<FillItem> &fitems, int64_t &tbw,
+                           int64_t &hrow, int64_t &vcol) {
+    const int64_t n = p->n_pairs;
+    const PlanKnobs &K = p->knobs;
+    p->geom_h.assign(n, PairGeom{});
+    p->cell_off_h.assign(n + 1, 0);
+    int64_t cell = 0, link = 0, flags = 0;
+    tbw = hrow = vcol = 0;
+    std::vector<int32_t> small, tiled;
+    for (int64_t k = 0; k < n; ++k) {
+        PairGeom &g = p->geom_h[k];
+        g.n = (int32_t)(sd[k + 1] - sd[k]);
+        g.m = (int32_t)(td[k + 1] - td[k]);
+        g.cell_off = cell;
+        g.tb_off = tbw;
+        g.link_off = link;
+        g.hrow_off = hrow;
+        g.vcol_off = vcol;
+        p->cell_off_h[k] = cell;
+        const int64_t ns = (g.n + 31) / 32, nb = (g.m + 31) / 32;
+        const int64_t cells = (int64_t)g.n * g.m;
+        const bool tile = cells >= K.tile_min_cells && g.n >= K.tile_min_rows && g.m > K.tile_cols;
+        if (tile) {
+            g.cw = K.tile_cols;
+            g.nchunk = (g.m + g.cw - 1) / g.cw;
+            g.flag_off = flags;
+            flags += ns * g.nchunk;
+            tiled.push_back((int32_t)k);
+        } else {
+            g.cw = (int32_t)std::max<int64_t>(32, nb * 32);
+            g.nchunk = 1;
+            g.flag_off = -1;
+            if (cells > 0) small.push_back((int32_t)k);
+        }
+        cell += cells;
+        tbw += ns * nb * 32;
+        link += std::min(g.n, g.m);
+        hrow += g.m;
+        vcol += g.n;
+    }
+    p->cell_off_h[n] = cell;
+    p->n_cells = cell;
+    p->link_cap = link;
+    p->n_flags = flags;
+
+    auto cells_of = [&](int32_t k) { return (int64_t)p->geom_h[k].n * p->geom_h[k].m; };
+    std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
+    std::stable_sort(tiled.begin(), tiled.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
+
+    // count items: 32 x 32 blocks, large pairs first
+    citems.clear();
+    std::vector<int32_t> all(tiled);
+    all.insert(all.end(), small.begin(), small.end());
+    for (int32_t k : all) {
+        const int ns = (p->geom_h[k].n + 31) / 32, nb = (p->geom_h[k].m + 31) / 32;
+        for (int s = 0; s < ns; ++s)
+            for (int b = 0; b < nb; ++b) citems.push_back({k, (s << 16) | b});
+    }
+
+    // fill items
+    fitems.clear();
+    int64_t max_diag = 0;
+    for (int32_t k : tiled) {
+        const PairGeom &g = p->geom_h[k];
+        max_diag = std::max<int64_t>(max_diag, (g.n + 31) / 32 + g.nchunk - 1);
+    }
+    const int64_t per_diag = max_diag > 0 ? ((int64_t)small.size() + max_diag - 1) / max_diag : 0;
+    size_t next_small = 0;
+    for (int64_t d = 0; d < max_diag; ++d) {
+        for (int32_t k : tiled) {
+            const PairGeom &g = p->geom_h[k];
+            const int ns = (g.n + 31) / 32;
+            for (int s = 0; s < ns; ++s) {
+                const int64_t cj = d - s;
+                if (cj >= 0 && cj < g.nchunk) fitems.push_back({k, s, s + 1, (int32_t)cj});
+            }
+        }
+        for (int64_t q = 0; q < per_diag && next_small < small.size(); ++q, ++next_small) {
+            const int32_t k = small[next_small];
+            fitems.push_back({k, 0, (p->geom_h[k].n + 31) / 32, 0});
+        }
+    }
+    for (; next_small < small.size(); ++next_small) {
+        const int32_t k = small[next_small];
+        fitems.push_back({k, 0, (p->geom_h[k].n + 31) / 32, 0});
+    }
+    p->n_count_items = (int64_t)citems.size();
+    p->n_fill_items = (int64_t)fitems.size();
+}
 
 extern "C" {
 
@@ -192,6 +304,9 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     if (src->n_docs != tgt->n_docs || src->n_docs < 0 || src->n_sents < 0 || tgt->n_sents < 0 ||
         src->n_tok < 0 || tgt->n_tok < 0 || dict->v_src <= 0 || dict->v_tgt <= 0 || dict->n_entries < 0)
         return MINE_EINVAL;
+    if (!src->doc_sent_off || !src->sent_tok_off || !tgt->doc_sent_off || !tgt->sent_tok_off || !dict->off ||
+        (src->n_tok > 0 && !src->tok) || (tgt->n_tok > 0 && !tgt->tok) || (dict->n_entries > 0 && !dict->tgt))
+        return MINE_EINVAL;
     if (src->n_docs > INT32_MAX) return MINE_ENOTSUP;
     cudaStream_t st = (cudaStream_t)stream;
     mine_plan *p = new (std::nothrow) mine_plan();
@@ -201,13 +316,13 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         return code;
     };
     cudaError_t e;
-#define PLAN_CK(x)                       \
-    do {                                 \
-        e = (x);                         \
-        if (e != cudaSuccess) {          \
-            g_last_cuda = (int)e;        \
+#define PLAN_CK(x)                                                                  \
+    do {                                                                            \
+        e = (x);                                                                    \
+        if (e != cudaSuccess) {                                                     \
+            g_last_cuda = (int)e;                                                   \
             return fail(e == cudaErrorMemoryAllocation ? MINE_ENOMEM : MINE_ECUDA); \
-        }                                \
+        }                                                                           \
     } while (0)
     PLAN_CK(cudaGetDevice(&p->device));
     PLAN_CK(cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -224,83 +339,52 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     PLAN_CK(cudaStreamSynchronize(st));
     if (sd[0] != 0 || td[0] != 0 || sd[n] != src->n_sents || td[n] != tgt->n_sents) return fail(MINE_EINVAL);
     for (int64_t k = 0; k < n; ++k)
-        if (sd[k + 1] < sd[k] || td[k + 1] < td[k] || sd[k + 1] - sd[k] > INT32_MAX / 2 ||
-            td[k + 1] - td[k] > INT32_MAX / 2)
+        if (sd[k + 1] < sd[k] || td[k + 1] < td[k] || sd[k + 1] - sd[k] > (1 << 21) || td[k + 1] - td[k] > (1 << 21))
             return fail(MINE_EINVAL);
 
     // validation kernels
-    PLAN_CK(dalloc(&p->status, 4));
+    PLAN_CK(dalloc(&p->S.status, 4));
     PLAN_CK(dalloc(&p->stats, 4));
-    PLAN_CK(cudaMemsetAsync(p->status, 0, 4 * sizeof(uint32_t), st));
+    PLAN_CK(cudaMemsetAsync(p->S.status, 0, 4 * sizeof(uint32_t), st));
     PLAN_CK(cudaMemsetAsync(p->stats, 0, 4 * sizeof(int32_t), st));
     if (src->n_sents > 0)
-        PLAN_CK(launch_validate_corpus(p->src, src->n_sents, src->n_tok, dict->v_src, p->status, p->stats + 0, st));
+        PLAN_CK(launch_validate_corpus(p->src, src->n_sents, src->n_tok, dict->v_src, p->S.status, p->stats + 0, st));
     if (tgt->n_sents > 0)
-        PLAN_CK(launch_validate_corpus(p->tgt, tgt->n_sents, tgt->n_tok, dict->v_tgt, p->status, p->stats + 1, st));
+        PLAN_CK(launch_validate_corpus(p->tgt, tgt->n_sents, tgt->n_tok, dict->v_tgt, p->S.status, p->stats + 1, st));
     {
-        int r = validate_dict(dict, p->status, st);
+        int r = validate_dict(dict, p->S.status, st);
         if (r != MINE_OK) return fail(r);
     }
 
-    // geometry
-    std::vector<PairGeom> geom(n);
-    p->cell_off_h.assign(n + 1, 0);
-    int64_t cell = 0, tbw = 0, link = 0, hrow = 0, items = 0;
-    for (int64_t k = 0; k < n; ++k) {
-        PairGeom &g = geom[k];
-        g.n = (int32_t)(sd[k + 1] - sd[k]);
-        g.m = (int32_t)(td[k + 1] - td[k]);
-        g.cell_off = cell;
-        g.tb_off = tbw;
-        g.link_off = link;
-        g.hrow_off = hrow;
-        p->cell_off_h[k] = cell;
-        const int64_t ns = (g.n + 31) / 32, nb = (g.m + 31) / 32;
-        cell += (int64_t)g.n * g.m;
-        tbw += ns * nb * 32;
-        link += std::min(g.n, g.m);
-        hrow += g.m;
-        items += ns * nb;
-        if (ns > 0xFFFF || nb > 0xFFFF) return fail(MINE_ENOTSUP);
-    }
-    p->cell_off_h[n] = cell;
-    p->n_cells = cell;
-    p->link_cap = link;
-    p->n_items = items;
+    std::vector<CountItem> citems;
+    std::vector<FillItem> fitems;
+    int64_t tbw = 0, hrow = 0, vcol = 0;
+    build_geometry(p, sd, td, citems, fitems, tbw, hrow, vcol);
     PLAN_CK(dalloc(&p->geom, n));
-    PLAN_CK(cudaMemcpyAsync(p->geom, geom.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
-
-    // work order: largest pairs first
-    std::vector<int32_t> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return (int64_t)geom[a].n * geom[a].m > (int64_t)geom[b].n * geom[b].m;
-    });
-    PLAN_CK(dalloc(&p->order, n));
-    PLAN_CK(cudaMemcpyAsync(p->order, order.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    std::vector<CountItem> it;
-    it.reserve(items);
-    for (int32_t k : order) {
-        const int ns = (geom[k].n + 31) / 32, nb = (geom[k].m + 31) / 32;
-        for (int s = 0; s < ns; ++s)
-            for (int b = 0; b < nb; ++b) it.push_back({k, (s << 16) | b});
-    }
-    PLAN_CK(dalloc(&p->items, items));
-    PLAN_CK(cudaMemcpyAsync(p->items, it.data(), items * sizeof(CountItem), cudaMemcpyHostToDevice, st));
+    PLAN_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
+    PLAN_CK(dalloc(&p->count_items, citems.size()));
+    PLAN_CK(cudaMemcpyAsync(p->count_items, citems.data(), citems.size() * sizeof(CountItem), cudaMemcpyHostToDevice, st));
+    PLAN_CK(dalloc(&p->fill_items, fitems.size()));
+    PLAN_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice, st));
 
     // scratch
-    PLAN_CK(dalloc(&p->counts, 2 * cell));
-    PLAN_CK(dalloc(&p->tb, tbw));
-    PLAN_CK(dalloc(&p->hrow, hrow));
-    PLAN_CK(dalloc(&p->scr_i, link));
-    PLAN_CK(dalloc(&p->scr_j, link));
-    PLAN_CK(dalloc(&p->scr_s, link));
-    PLAN_CK(dalloc(&p->n_links, n));
+    PLAN_CK(dalloc(&p->counts, 2 * p->n_cells));
+    PLAN_CK(dalloc(&p->S.tb, tbw));
+    PLAN_CK(dalloc(&p->S.hrow, hrow));
+    PLAN_CK(dalloc(&p->S.vcol, vcol));
+    PLAN_CK(dalloc(&p->S.flags, p->n_flags));
+    PLAN_CK(dalloc(&p->S.queue, 1));
+    PLAN_CK(dalloc(&p->S.diag_i, p->link_cap));
+    PLAN_CK(dalloc(&p->S.diag_j, p->link_cap));
+    PLAN_CK(dalloc(&p->S.diag_s, p->link_cap));
+    PLAN_CK(dalloc(&p->S.n_diag, n));
+    PLAN_CK(dalloc(&p->S.diag_off, n + 1));
+    PLAN_CK(dalloc(&p->S.n_links, n));
     PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
 
     uint32_t status[4];
     int32_t stats[4];
-    PLAN_CK(cudaMemcpyAsync(status, p->status, sizeof status, cudaMemcpyDeviceToHost, st));
+    PLAN_CK(cudaMemcpyAsync(status, p->S.status, sizeof status, cudaMemcpyDeviceToHost, st));
     PLAN_CK(cudaMemcpyAsync(stats, p->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
     PLAN_CK(cudaStreamSynchronize(st));
     if (status[0] != 0) return fail(MINE_EINVAL);
@@ -329,11 +413,11 @@ int mine_plan_cell_offsets(const mine_plan *p, int64_t *host_out) {
 
 int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
-    if (p->n_items == 0) return MINE_OK;
+    if (p->n_count_items == 0) return MINE_OK;
     cudaStream_t st = (cudaStream_t)stream;
     MINE_CK(timed(p, kKCount, st, [&] {
-        return launch_count(p->src, p->tgt, p->dict, p->geom, p->items, p->n_items, p->log_slots, p->planes,
-                            counts, p->status, p->n_sms, st);
+        return launch_count(p->src, p->tgt, p->dict, p->geom, p->count_items, p->n_count_items, p->log_slots,
+                            p->planes, counts, p->S.status, p->n_sms, st);
     }));
     return MINE_OK;
 }
@@ -350,24 +434,28 @@ int mine_score(mine_plan *p, const mine_params *params, const uint8_t *counts, f
 
 int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, mine_out *out,
                miner_stream_t stream) {
-    if (!p || !params || !out || !out->link_off || !out->pair_score) return MINE_EINVAL;
+    if (!p || !params || !out || !out->link_off || (!out->pair_score && p->n_pairs > 0)) return MINE_EINVAL;
     if (out->link_capacity < p->link_cap) return MINE_EINVAL;
     if (p->link_cap > 0 && (!out->link_i || !out->link_j || !out->link_s)) return MINE_EINVAL;
     if (p->n_cells > 0 && !counts) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const DevParams P = to_dev(*params);
+    const AlignScratch &S = p->S;
+    const int64_t n = p->n_pairs;
+    if (p->n_flags > 0) MINE_CK(cudaMemsetAsync(S.flags, 0, p->n_flags * sizeof(int32_t), st));
     MINE_CK(timed(p, kKFill, st, [&] {
-        return launch_nw_counts(p->src, p->tgt, p->geom, p->order, p->n_pairs, P, counts, p->tb, p->hrow, p->n_sms,
-                                st);
+        return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, S,
+                           p->knobs.wait_limit, p->n_sms, st);
     }));
-    MINE_CK(timed(p, kKTraceback, st, [&] {
-        return launch_traceback(p->src, p->tgt, p->dict, p->geom, p->n_pairs, P, p->tb, p->scr_i, p->scr_j,
-                                p->scr_s, p->n_links, out->pair_score, st);
+    MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, n, S, p->n_sms, st); }));
+    MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_diag, n, S.diag_off, st); }));
+    MINE_CK(timed(p, kKLinks, st, [&] {
+        return launch_link_score(p->src, p->tgt, p->dict, p->geom, n, P, S, p->n_sms, st);
     }));
-    MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(p->n_links, p->n_pairs, out->link_off, st); }));
-    MINE_CK(timed(p, kKCopy, st, [&] {
-        return launch_copy_links(p->geom, p->n_pairs, p->n_links, p->scr_i, p->scr_j, p->scr_s, out->link_off,
-                                 out->link_i, out->link_j, out->link_s, st);
+    MINE_CK(timed(p, kKLinks, st, [&] { return launch_pair_sum(p->geom, n, P, S, out->pair_score, p->n_sms, st); }));
+    MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_links, n, out->link_off, st); }));
+    MINE_CK(timed(p, kKLinks, st, [&] {
+        return launch_copy_links(p->geom, n, P, S, out->link_off, out->link_i, out->link_j, out->link_s, p->n_sms, st);
     }));
     return MINE_OK;
 }
@@ -377,6 +465,18 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
     int r = mine_count(p, p->counts, stream);
     if (r != MINE_OK) return r;
     return mine_align(p, params, p->counts, out, stream);
+}
+
+int mine_plan_check(mine_plan *p, miner_stream_t stream) {
+    if (!p) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t status = 0;
+    MINE_CK(cudaMemcpyAsync(&status, p->S.status, sizeof status, cudaMemcpyDeviceToHost, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    MINE_CK(cudaMemsetAsync(p->S.status, 0, sizeof status, st));
+    if (status & kStTimeout) return MINE_ETIMEOUT;
+    if (status) return MINE_EINVAL;
+    return MINE_OK;
 }
 
 int mine_plan_set_timing(mine_plan *p, int enable) {
@@ -415,16 +515,3 @@ const char *mine_strerror(int code) {
 int mine_last_cuda_error(void) { return g_last_cuda; }
 
 }  // extern "C"
-
-static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st) {
-    if (d->v_src <= 0) return MINE_EINVAL;
-    int64_t blocks = std::min<int64_t>((d->v_src + 255) / 256, 4096);
-    gbm::validate_dict_kernel<<<(unsigned)blocks, 256, 0, st>>>(DevDict{d->off, d->tgt}, d->v_src, d->v_tgt,
-                                                                d->n_entries, status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        g_last_cuda = (int)e;
-        return MINE_ECUDA;
-    }
-    return MINE_OK;
-}

@@ -61,6 +61,7 @@ _SIGS = {
     "mine_score": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mine_align": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_void_p]),
     "mine_pairs": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_Out), C.c_void_p]),
+    "mine_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mine_plan_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mine_strerror": (C.c_char_p, [C.c_int]),
@@ -199,7 +200,11 @@ class Plan:
     def __exit__(self, *a):
         self.close()
 
-    KERNEL_KINDS = ("count", "align_fill", "traceback", "link_scan", "link_copy", "score")
+    KERNEL_KINDS = ("count", "fill", "walk", "links", "scan", "score")
+
+    def check(self, stream=None):
+        """Synchronise and raise if a device-side wait timed out (mine_plan_check)."""
+        _check(lib().mine_plan_check(self._h, _stream(stream)), "mine_plan_check")
 
     def set_timing(self, enable: bool = True):
         _check(lib().mine_plan_set_timing(self._h, int(enable)), "mine_plan_set_timing")
