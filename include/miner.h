@@ -136,6 +136,19 @@ int mine_align(mine_plan *plan, const mine_params *params, const uint8_t *counts
 int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
                miner_stream_t stream);
 
+/* Plan options: the tuning knobs of the planner (defaults in parentheses).
+ * Setting a tiling option rebuilds the plan's work lists synchronously; do
+ * not call it while work on the plan is in flight. */
+#define MINE_OPT_TILE_COLS 1      /* fill tile width in columns, multiple of 32 (128) */
+#define MINE_OPT_TILE_MIN_CELLS 2 /* a pair with at least this many cells ... (262144) */
+#define MINE_OPT_TILE_MIN_ROWS 3  /* ... and this many rows is filled as tiles (64) */
+#define MINE_OPT_WAIT_LIMIT 4     /* spin iterations before a tile wait gives up (2^24) */
+#define MINE_OPT_LINK_RECOUNT 5   /* 1: recount the overlaps of aligned pairs by warp
+                                     vote instead of reading the cached counts (0) */
+int mine_plan_set_option(mine_plan *plan, int option, int64_t value);
+/* Current value of an option, or MINE_EINVAL for an unknown option. */
+int64_t mine_plan_get_option(const mine_plan *plan, int option);
+
 /* Synchronise the stream and report device-side errors raised since the last
  * check: MINE_ETIMEOUT if a bounded wait of the cooperative fill gave up (its
  * results are then invalid), MINE_EINVAL if a count table overflowed, else

@@ -296,11 +296,12 @@ __device__ __forceinline__ void ballot_counts(const int32_t *__restrict__ stok, 
     mt = mtc;
 }
 
-// Similarity of every diagonal cell of every path: one warp per cell,
-// counts by warp vote, similarity by the same helper the fill used.
+// Similarity of every diagonal cell of every path, one warp per cell, by the
+// same helper the fill used.  The counts come from the cached per-cell counts
+// when given, else they are recounted by warp vote from the tokens.
 __global__ void __launch_bounds__(32 * kTailWarps)
 link_score_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
-                  int64_t n_pairs, DevParams P, AlignScratch S) {
+                  int64_t n_pairs, DevParams P, AlignScratch S, const uint8_t *__restrict__ counts) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -322,7 +323,13 @@ link_score_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__
         const int64_t s0 = src.sent[sb], s1 = src.sent[sb + 1];
         const int64_t t0 = tgt.sent[tbs], t1 = tgt.sent[tbs + 1];
         int ms, mt;
-        ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
+        if (counts) {
+            const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)rr * g.m + cc];
+            ms = q.x;
+            mt = q.y;
+        } else {
+            ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
+        }
         if (lane == 0)
             S.diag_s[at] = similarity(ms, mt, sim_row((int)(s1 - s0), P), sim_col((int)(t1 - t0), P), K);
     }
@@ -455,9 +462,9 @@ cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                              const AlignScratch &S, int n_sms, cudaStream_t st) {
+                              const AlignScratch &S, const uint8_t *counts, int n_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S);
+    link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S, counts);
     return cudaGetLastError();
 }
 

@@ -130,6 +130,24 @@ struct BitCounter {
             x = c;
         }
     }
+    // Add four 0/1 words with a carry-save tree: two full adders into plane 0,
+    // one into plane 1, then a ripple of the weight-4 carry (Harley-Seal).
+    __device__ __forceinline__ void add4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+        const uint32_t s1 = p[0] ^ a ^ b;
+        const uint32_t c1 = (p[0] & a) | (p[0] & b) | (a & b);
+        const uint32_t s2 = s1 ^ c ^ d;
+        const uint32_t c2 = (s1 & c) | (s1 & d) | (c & d);
+        p[0] = s2;
+        const uint32_t t = p[1] ^ c1 ^ c2;
+        uint32_t x = (p[1] & c1) | (p[1] & c2) | (c1 & c2);
+        p[1] = t;
+#pragma unroll
+        for (int k = 2; k < K; ++k) {
+            const uint32_t y = p[k] & x;
+            p[k] ^= x;
+            x = y;
+        }
+    }
     // Counter for bit position 4m+r lands in byte r of out[m].
     __device__ __forceinline__ void to_bytes(uint32_t out[8]) const {
 #pragma unroll

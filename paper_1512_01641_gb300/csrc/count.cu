@@ -151,6 +151,182 @@ count_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Strip kernel: one warp owns 32 source rows (a strip) and sweeps all column
+// blocks of the pair.  The row table is built once per strip:
+//   RT[t] = 32-bit mask of the strip's rows i with t in T_i (T_i = dictionary
+//           translations of source sentence i),
+// and every row keeps, in shared memory, the list of RT slots of its
+// translations in position order (last translation of a position flagged).
+// Per 32-column block:
+//   column pass: lane j looks up each token of target sentence j in RT; a hit
+//     adds RT[t] into the mt counters (mt for 32 rows) and sets bit j of the
+//     slot's column mask;
+//   row pass: lane i walks its slot list; the column masks of a position's
+//     translations OR into h (bit j: the position is matched in column j), and
+//     h is added into the ms counters (ms for 32 columns).
+// No dictionary or hash work is left in the row pass, and the table build is
+// paid once per strip instead of once per block.
+template <int LOG_SLOTS, int LCAP>
+struct StripSmem {
+    static constexpr int S = 1 << LOG_SLOTS;
+    int32_t key[S];
+    uint32_t rowmask[S];
+    uint32_t colmask[S];  // also holds the two 32 x 36 byte transpose tiles after the row pass
+    uint16_t list[32][LCAP];
+};
+static_assert(sizeof(uint32_t) * 1024 >= 2 * 32 * kPad, "transpose tiles alias the column masks");
+
+constexpr uint16_t kEndPos = 0x8000u;
+// Per-row slot-list capacity: an odd number of 32-bit words per row keeps the
+// lanes' list reads on distinct banks.
+static_assert((kStripListCap / 2) % 2 == 1, "row lists need an odd word stride");
+
+template <int LOG_SLOTS, int K, int LCAP>
+__global__ void __launch_bounds__(32 * kCountWarps)
+count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
+                   const CountStripItem *__restrict__ items, int64_t n_items, uint8_t *__restrict__ counts,
+                   uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using Smem = StripSmem<LOG_SLOTS, LCAP>;
+    constexpr int S = Smem::S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Smem &sm = reinterpret_cast<Smem *>(smem_raw)[warp];
+    uint8_t(*ms_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(sm.colmask);
+    uint8_t(*mt_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(reinterpret_cast<uint8_t *>(sm.colmask) + 32 * kPad);
+
+    for (int64_t it = (int64_t)blockIdx.x * kCountWarps + warp; it < n_items;
+         it += (int64_t)gridDim.x * kCountWarps) {
+        const CountStripItem item = items[it];
+        const PairGeom g = geom[item.pair];
+        const int r0 = item.strip * 32;
+        const bool rv = lane >= item.r_lo && lane < item.r_hi && r0 + lane < g.n;
+        const int nr = min(item.r_hi, g.n - r0);  // rows [r_lo, nr) of the strip are written
+        for (int x = lane; x < S; x += 32) {
+            sm.key[x] = kEmpty;
+            sm.rowmask[x] = 0u;
+        }
+        __syncwarp();
+
+        // row table + slot lists
+        int n_list = 0;
+        if (rv) {
+            const int64_t ssent = src.doc[item.pair] + r0 + lane;
+            const int64_t p0 = src.sent[ssent], p1 = src.sent[ssent + 1];
+            for (int64_t p = p0; p < p1; ++p) {
+                const int32_t v = src.tok[p];
+                const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int h = table_insert<LOG_SLOTS>(sm.key, dict.tgt[e]);
+                    if (h < 0 || n_list >= LCAP) {
+                        atomicOr(status, kStTableFull);
+                        break;
+                    }
+                    atomicOr(&sm.rowmask[h], 1u << lane);
+                    sm.list[lane][n_list++] = (uint16_t)h | (e + 1 == e1 ? kEndPos : 0u);
+                }
+            }
+        }
+        __syncwarp();
+
+        const int nblk = (g.m + 31) >> 5;
+        const int64_t tdoc = tgt.doc[item.pair];
+        uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m);
+        for (int jb = 0; jb < nblk; ++jb) {
+            const int c0 = jb * 32;
+            const int nc = min(32, g.m - c0);
+            for (int x = lane; x < S; x += 32) sm.colmask[x] = 0u;
+            __syncwarp();
+            // column pass: mt for 32 rows of column c0 + lane
+            BitCounter<K> mt;
+            mt.clear();
+            if (lane < nc) {
+                const int64_t q0 = tgt.sent[tdoc + c0 + lane], q1 = tgt.sent[tdoc + c0 + lane + 1];
+                uint32_t b0 = 0, b1 = 0, b2 = 0;
+                int nbuf = 0;
+                for (int64_t q = q0; q < q1; ++q) {
+                    const int slot = table_find<LOG_SLOTS>(sm.key, tgt.tok[q]);
+                    if (slot < 0) continue;
+                    const uint32_t rm = sm.rowmask[slot];
+                    atomicOr(&sm.colmask[slot], 1u << lane);
+                    if (nbuf == 3) {
+                        mt.add4(b0, b1, b2, rm);
+                        nbuf = 0;
+                    } else {
+                        b2 = b1;
+                        b1 = b0;
+                        b0 = rm;
+                        ++nbuf;
+                    }
+                }
+                if (nbuf > 0) mt.add4(b0, nbuf > 1 ? b1 : 0u, nbuf > 2 ? b2 : 0u, 0u);
+            }
+            __syncwarp();
+            // row pass: ms for 32 columns of row r0 + lane
+            BitCounter<K> ms;
+            ms.clear();
+            if (rv) {
+                uint32_t b0 = 0, b1 = 0, b2 = 0, h = 0;
+                int nbuf = 0;
+                for (int x = 0; x < n_list; ++x) {
+                    const uint16_t ent = sm.list[lane][x];
+                    h |= sm.colmask[ent & 0x7FFF];
+                    if (ent & kEndPos) {
+                        if (nbuf == 3) {
+                            ms.add4(b0, b1, b2, h);
+                            nbuf = 0;
+                        } else {
+                            b2 = b1;
+                            b1 = b0;
+                            b0 = h;
+                            ++nbuf;
+                        }
+                        h = 0;
+                    }
+                }
+                if (nbuf > 0) ms.add4(b0, nbuf > 1 ? b1 : 0u, nbuf > 2 ? b2 : 0u, 0u);
+            }
+            __syncwarp();
+            // expand, transpose (tiles alias the column masks), write
+            uint32_t w[8];
+            ms.to_bytes(w);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&ms_t[lane][4 * m]) = w[m];
+            mt.to_bytes(w);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&mt_t[lane][4 * m]) = w[m];
+            __syncwarp();
+            if (lane < nc) {
+                for (int i = item.r_lo; i < nr; ++i) {
+                    const uchar2 v = make_uchar2(ms_t[i][lane], mt_t[lane][i]);
+                    reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[lane] = v;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <int LOG_SLOTS, int K>
+cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
+                           const PairGeom *geom, const CountStripItem *items, int64_t n_items,
+                           uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st) {
+    constexpr int LCAP = kStripListCap;
+    const size_t smem = sizeof(StripSmem<LOG_SLOTS, LCAP>) * kCountWarps;
+    auto kern = count_strip_kernel<LOG_SLOTS, K, LCAP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kCountWarps, smem);
+    if (e != cudaSuccess) return e;
+    int64_t want = (n_items + kCountWarps - 1) / kCountWarps;
+    int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
+    int grid = (int)(want < cap ? want : cap);
+    if (grid < 1) return cudaSuccess;
+    kern<<<grid, 32 * kCountWarps, smem, st>>>(src, tgt, dict, geom, items, n_items, counts, status);
+    return cudaGetLastError();
+}
+
 template <int LOG_SLOTS, int K>
 cudaError_t launch_count_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                            const PairGeom *geom, const CountItem *items, int64_t n_items,
@@ -170,7 +346,55 @@ cudaError_t launch_count_t(const DevCorpus &src, const DevCorpus &tgt, const Dev
     return cudaGetLastError();
 }
 
+// Translation totals of every 32-row strip (sizes the row tables) and the
+// largest per-sentence total (sizes the slot lists).
+__global__ void strip_translations_kernel(DevCorpus src, DevDict dict, const PairGeom *__restrict__ geom,
+                                          const int64_t *__restrict__ strip_off, int64_t n_pairs,
+                                          int32_t *__restrict__ strip_tr, int32_t *__restrict__ max_row) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride) {
+        const int N = geom[k].n;
+        const int64_t base = src.doc[k];
+        int best = 0;
+        for (int s = 0; s * 32 < N; ++s) {
+            int64_t tot = 0;
+            for (int r = s * 32; r < min(N, s * 32 + 32); ++r) {
+                int row = 0;
+                for (int64_t p = src.sent[base + r]; p < src.sent[base + r + 1]; ++p) {
+                    const int32_t v = src.tok[p];
+                    row += dict.off[v + 1] - dict.off[v];
+                }
+                best = max(best, row);
+                tot += row;
+            }
+            strip_tr[strip_off[k] + s] = (int32_t)(tot < 0x7fffffffLL ? tot : 0x7fffffffLL);
+        }
+        atomicMax(max_row, best);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict, const PairGeom *geom,
+                                      const int64_t *strip_off, int64_t n_pairs, int32_t *strip_tr,
+                                      int32_t *max_row, cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    const int64_t blocks = (n_pairs + 127) / 128;
+    strip_translations_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 128, 0, st>>>(
+        src, dict, geom, strip_off, n_pairs, strip_tr, max_row);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
+                                const PairGeom *geom, const CountStripItem *items, int64_t n_items,
+                                int log_slots, int planes, uint8_t *counts, uint32_t *status, int n_sms,
+                                cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    if (log_slots == 11)
+        return planes <= 5 ? launch_strip_t<11, 5>(src, tgt, dict, geom, items, n_items, counts, status, n_sms, st)
+                           : launch_strip_t<11, 8>(src, tgt, dict, geom, items, n_items, counts, status, n_sms, st);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_count(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                          const PairGeom *geom, const CountItem *items, int64_t n_items,

@@ -26,6 +26,14 @@ struct CountItem {
     int32_t strip_block;  // (row strip << 16) | column block
 };
 
+// One count work item of the strip kernel: rows [r_lo, r_hi) of a 32-row
+// strip of one pair, all column blocks.
+struct CountStripItem {
+    int32_t pair;
+    int32_t strip;
+    int32_t r_lo, r_hi;
+};
+
 // Per-pair geometry the plan precomputes (device copy).
 struct PairGeom {
     int64_t cell_off;  // first cell of the pair in per-cell buffers
@@ -71,6 +79,18 @@ cudaError_t launch_count(const DevCorpus &src, const DevCorpus &tgt, const DevDi
                          int log_slots, int planes, uint8_t *counts, uint32_t *status,
                          int n_sms, cudaStream_t st);
 
+cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
+                                const PairGeom *geom, const CountStripItem *items, int64_t n_items,
+                                int log_slots, int planes, uint8_t *counts, uint32_t *status, int n_sms,
+                                cudaStream_t st);
+
+constexpr int kStripListCap = 98;   // slot-list entries per row of the strip count kernel
+constexpr int kStripLogSlots = 11;  // row-table slots of the strip count kernel (2^11)
+
+cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict, const PairGeom *geom,
+                                      const int64_t *strip_off, int64_t n_pairs, int32_t *strip_tr,
+                                      int32_t *max_row, cudaStream_t st);
+
 cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                          int64_t n_pairs, const DevParams &P, const uint8_t *counts, float *s,
                          float *feat, cudaStream_t st);
@@ -87,7 +107,7 @@ cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                              const AlignScratch &S, int n_sms, cudaStream_t st);
+                              const AlignScratch &S, const uint8_t *counts, int n_sms, cudaStream_t st);
 
 cudaError_t launch_pair_sum(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
                             const AlignScratch &S, float *pair_score, int n_sms, cudaStream_t st);

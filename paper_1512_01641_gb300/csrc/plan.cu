@@ -108,6 +108,7 @@ struct PlanKnobs {
     int tile_min_rows = 64;            // ... and at least this many rows
     int tile_cols = 128;               // column chunk width of a tile (multiple of 32)
     int64_t wait_limit = 1 << 24;      // bounded spin iterations of a tile wait (~200 ns each)
+    int link_recount = 0;              // 1: recount link overlaps by warp vote
 };
 
 struct mine_plan {
@@ -119,10 +120,13 @@ struct mine_plan {
     PlanKnobs knobs;
     PairGeom *geom = nullptr;
     CountItem *count_items = nullptr;
+    CountStripItem *strip_items = nullptr;
+    int64_t n_strip_items = 0;
+    bool use_strips = false;  // strip count kernel (else the per-block kernel)
     FillItem *fill_items = nullptr;
     uint8_t *counts = nullptr;
     AlignScratch S{};
-    int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens]
+    int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens, max row translations]
     int log_slots = 11, planes = 5, n_sms = 1, device = 0;
     // per-kernel timing hook
     bool timing = false;
@@ -179,7 +183,7 @@ static void drain_pending(mine_plan *p) {
 static void plan_free(mine_plan *p) {
     if (!p) return;
     drain_pending(p);
-    void *bufs[] = {p->geom, p->count_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
+    void *bufs[] = {p->geom, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
                     p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
                     p->S.diag_off, p->S.n_links, p->stats};
     for (void *b : bufs)
@@ -388,6 +392,59 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     PLAN_CK(cudaMemcpyAsync(stats, p->stats, sizeof stats, cudaMemcpyDeviceToHost, st));
     PLAN_CK(cudaStreamSynchronize(st));
     if (status[0] != 0) return fail(MINE_EINVAL);
+
+    // strip count kernel: translation totals per strip decide row-table splits
+    {
+        std::vector<int64_t> strip_off(n + 1, 0);
+        for (int64_t k = 0; k < n; ++k) strip_off[k + 1] = strip_off[k] + (p->geom_h[k].n + 31) / 32;
+        const int64_t n_strips = strip_off[n];
+        int64_t *d_off = nullptr;
+        int32_t *d_tr = nullptr;
+        PLAN_CK(dalloc(&d_off, n + 1));
+        e = dalloc(&d_tr, n_strips);
+        if (e != cudaSuccess) cudaFree(d_off);
+        PLAN_CK(e);
+        std::vector<int32_t> tr(n_strips > 0 ? n_strips : 1);
+        e = cudaMemcpyAsync(d_off, strip_off.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = launch_strip_translations(p->src, p->dict, p->geom, d_off, n, d_tr, p->stats + 3, st);
+        if (e == cudaSuccess && n_strips > 0)
+            e = cudaMemcpyAsync(tr.data(), d_tr, n_strips * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stats, p->stats, sizeof stats, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(d_off);
+        cudaFree(d_tr);
+        PLAN_CK(e);
+        const int maxlen0 = std::max(stats[0], stats[1]);
+        p->use_strips = maxlen0 <= 31 && stats[3] <= kStripListCap;
+        if (p->use_strips) {
+            // a strip whose translations would fill the row table past ~70% is
+            // split into 2, 4, ... row groups
+            const int64_t limit = (int64_t)(0.7 * (1 << kStripLogSlots));
+            std::vector<int32_t> order(n);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+                return (int64_t)p->geom_h[a].n * p->geom_h[a].m > (int64_t)p->geom_h[b].n * p->geom_h[b].m;
+            });
+            std::vector<CountStripItem> sitems;
+            for (int32_t k : order) {
+                if (p->geom_h[k].m == 0) continue;
+                const int ns = (p->geom_h[k].n + 31) / 32;
+                for (int sidx = 0; sidx < ns; ++sidx) {
+                    const int64_t t = tr[strip_off[k] + sidx];
+                    int parts = 1;
+                    while (parts < 32 && t > limit * parts) parts *= 2;
+                    const int rows = 32 / parts;
+                    for (int q = 0; q < parts; ++q) sitems.push_back({k, sidx, q * rows, (q + 1) * rows});
+                }
+            }
+            p->n_strip_items = (int64_t)sitems.size();
+            PLAN_CK(dalloc(&p->strip_items, sitems.size()));
+            PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
+                                    cudaMemcpyHostToDevice, st));
+            PLAN_CK(cudaStreamSynchronize(st));
+        }
+    }
     const int maxlen = std::max(stats[0], stats[1]);
     p->planes = maxlen <= 31 ? 5 : 8;
     const int btok = std::max(stats[2], 1);
@@ -415,10 +472,17 @@ int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
     if (p->n_count_items == 0) return MINE_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    MINE_CK(timed(p, kKCount, st, [&] {
-        return launch_count(p->src, p->tgt, p->dict, p->geom, p->count_items, p->n_count_items, p->log_slots,
-                            p->planes, counts, p->S.status, p->n_sms, st);
-    }));
+    if (p->use_strips) {
+        MINE_CK(timed(p, kKCount, st, [&] {
+            return launch_count_strips(p->src, p->tgt, p->dict, p->geom, p->strip_items, p->n_strip_items,
+                                       kStripLogSlots, p->planes, counts, p->S.status, p->n_sms, st);
+        }));
+    } else {
+        MINE_CK(timed(p, kKCount, st, [&] {
+            return launch_count(p->src, p->tgt, p->dict, p->geom, p->count_items, p->n_count_items, p->log_slots,
+                                p->planes, counts, p->S.status, p->n_sms, st);
+        }));
+    }
     return MINE_OK;
 }
 
@@ -450,7 +514,8 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
     MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, n, S, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_diag, n, S.diag_off, st); }));
     MINE_CK(timed(p, kKLinks, st, [&] {
-        return launch_link_score(p->src, p->tgt, p->dict, p->geom, n, P, S, p->n_sms, st);
+        return launch_link_score(p->src, p->tgt, p->dict, p->geom, n, P, S, p->knobs.link_recount ? nullptr : counts,
+                                 p->n_sms, st);
     }));
     MINE_CK(timed(p, kKLinks, st, [&] { return launch_pair_sum(p->geom, n, P, S, out->pair_score, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_links, n, out->link_off, st); }));
@@ -477,6 +542,67 @@ int mine_plan_check(mine_plan *p, miner_stream_t stream) {
     if (status & kStTimeout) return MINE_ETIMEOUT;
     if (status) return MINE_EINVAL;
     return MINE_OK;
+}
+
+int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
+    if (!p) return MINE_EINVAL;
+    PlanKnobs k = p->knobs;
+    switch (option) {
+        case MINE_OPT_TILE_COLS:
+            if (value < 32 || value % 32 || value > (1 << 20)) return MINE_EINVAL;
+            k.tile_cols = (int)value;
+            break;
+        case MINE_OPT_TILE_MIN_CELLS:
+            if (value < 1) return MINE_EINVAL;
+            k.tile_min_cells = value;
+            break;
+        case MINE_OPT_TILE_MIN_ROWS:
+            if (value < 1) return MINE_EINVAL;
+            k.tile_min_rows = (int)std::min<int64_t>(value, 1 << 30);
+            break;
+        case MINE_OPT_WAIT_LIMIT:
+            if (value < 1) return MINE_EINVAL;
+            p->knobs.wait_limit = value;
+            return MINE_OK;
+        case MINE_OPT_LINK_RECOUNT:
+            p->knobs.link_recount = value != 0;
+            return MINE_OK;
+        default:
+            return MINE_EINVAL;
+    }
+    // tiling changed: rebuild the work lists and the tile flags (synchronous)
+    std::vector<int64_t> sd(p->n_pairs + 1, 0), td(p->n_pairs + 1, 0);
+    for (int64_t x = 0; x < p->n_pairs; ++x) {
+        sd[x + 1] = sd[x] + p->geom_h[x].n;
+        td[x + 1] = td[x] + p->geom_h[x].m;
+    }
+    p->knobs = k;
+    std::vector<CountItem> citems;
+    std::vector<FillItem> fitems;
+    int64_t tbw, hrow, vcol;
+    build_geometry(p, sd, td, citems, fitems, tbw, hrow, vcol);
+    cudaFree(p->fill_items);
+    cudaFree(p->S.flags);
+    p->fill_items = nullptr;
+    p->S.flags = nullptr;
+    MINE_CK(cudaDeviceSynchronize());
+    MINE_CK(dalloc(&p->fill_items, fitems.size()));
+    MINE_CK(dalloc(&p->S.flags, p->n_flags));
+    MINE_CK(cudaMemcpy(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice));
+    MINE_CK(cudaMemcpy(p->geom, p->geom_h.data(), p->n_pairs * sizeof(PairGeom), cudaMemcpyHostToDevice));
+    return MINE_OK;
+}
+
+int64_t mine_plan_get_option(const mine_plan *p, int option) {
+    if (!p) return MINE_EINVAL;
+    switch (option) {
+        case MINE_OPT_TILE_COLS: return p->knobs.tile_cols;
+        case MINE_OPT_TILE_MIN_CELLS: return p->knobs.tile_min_cells;
+        case MINE_OPT_TILE_MIN_ROWS: return p->knobs.tile_min_rows;
+        case MINE_OPT_WAIT_LIMIT: return p->knobs.wait_limit;
+        case MINE_OPT_LINK_RECOUNT: return p->knobs.link_recount;
+        default: return MINE_EINVAL;
+    }
 }
 
 int mine_plan_set_timing(mine_plan *p, int enable) {

@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 MINE_OK, MINE_EINVAL, MINE_ENOMEM, MINE_ECUDA, MINE_ETIMEOUT, MINE_ENOTSUP = 0, -1, -2, -3, -4, -5
+OPTIONS = {"tile_cols": 1, "tile_min_cells": 2, "tile_min_rows": 3, "wait_limit": 4, "link_recount": 5}
 
 
 class MinerError(RuntimeError):
@@ -62,6 +63,8 @@ _SIGS = {
     "mine_align": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_void_p]),
     "mine_pairs": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_Out), C.c_void_p]),
     "mine_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mine_plan_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
+    "mine_plan_get_option": (C.c_int64, [C.c_void_p, C.c_int]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mine_plan_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mine_strerror": (C.c_char_p, [C.c_int]),
@@ -201,6 +204,12 @@ class Plan:
         self.close()
 
     KERNEL_KINDS = ("count", "fill", "walk", "links", "scan", "score")
+
+    def set_option(self, name: str, value: int):
+        _check(lib().mine_plan_set_option(self._h, OPTIONS[name], int(value)), f"mine_plan_set_option({name})")
+
+    def get_option(self, name: str) -> int:
+        return int(lib().mine_plan_get_option(self._h, OPTIONS[name]))
 
     def check(self, stream=None):
         """Synchronise and raise if a device-side wait timed out (mine_plan_check)."""

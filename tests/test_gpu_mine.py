@@ -48,8 +48,16 @@ def _long_sentence_batch():
     return synth.from_lists(src, tgt, lists, v_tgt=v)
 
 
+def _dense_translation_batch():
+    # every source id has 3 translations: strips carry ~1700 translations, so
+    # the planner splits their row tables into row groups
+    rng = np.random.Generator(np.random.PCG64(9))
+    dic = synth.make_dictionary(rng, 3000, 3000, kmin=3, kmax=3)
+    return synth.make_batch(79, 8, dic=dic, size_median=70, size_hi=160)
+
+
 BATCHES = {"single_40x45": synth.single_pair, "edges": _edge_batch, "mixed": _mixed_batch,
-           "long_sentences": _long_sentence_batch}
+           "long_sentences": _long_sentence_batch, "dense_translations": _dense_translation_batch}
 
 
 @pytest.fixture(scope="module", params=list(BATCHES))
@@ -214,3 +222,56 @@ def test_long_pair_5000x5000():
         assert tuple(c[i, j]) == oracle.counts(src[i], tgt[j], batch.dic)
     sel = {"score": gpu["score"], "links": gpu["links"]}
     assert check_alignment(batch, p_all, sel, ref) <= 1
+
+
+def _outputs_equal(a, b, n_pairs):
+    import torch
+    n = int(a["link_off"][-1])
+    assert torch.equal(a["link_off"][: n_pairs + 1], b["link_off"][: n_pairs + 1])
+    assert torch.equal(a["pair_score"][:n_pairs], b["pair_score"][:n_pairs])
+    for key in ("link_i", "link_j", "link_s"):
+        assert torch.equal(a[key][:n], b[key][:n]), key
+
+
+@pytest.mark.parametrize("tile_cols", [32, 96, 128, 256])
+def test_tiled_fill_equals_single_warp_fill(tile_cols):
+    """The cooperative tiled fill (tile waits, boundary rows/columns) gives
+    bit-identical results to one warp per pair, for tile widths that do and do
+    not divide the pair widths."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    ns = [300, 97, 64, 257, 40]
+    ms = [410, 300, 97, 64, 700]
+    batch = synth.make_batch(81, len(ns), v_src=4000, v_tgt=4000, planted_frac=0.0, src_sizes=ns, tgt_sizes=ms)
+    p = _params(thr=-1.0)
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        plan.set_option("tile_min_cells", 1 << 40)  # one warp per pair
+        ref = plan.mine(p)
+        torch.cuda.synchronize()
+        ref = {k: v.clone() for k, v in ref.items()}
+        plan.set_option("tile_min_cells", 1)
+        plan.set_option("tile_min_rows", 33)
+        plan.set_option("tile_cols", tile_cols)
+        got = plan.mine(p)
+        plan.check()
+        _outputs_equal(ref, got, batch.n_pairs)
+    ora = oracle.mine(batch, p.w, p.b, p.gap, p.thr, want_sim=True)
+    sel = {"score": got["pair_score"].cpu().numpy(), "links": miner.links_per_pair(got, batch.n_pairs)}
+    check_alignment(batch, p, sel, ora)
+
+
+def test_link_recount_by_warp_vote_matches_cached_counts():
+    """Recounting the overlaps of the aligned pairs by warp vote gives exactly
+    the similarities computed from the cached bit-sliced counts."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = _mixed_batch()
+    p = _params(thr=-1.0)
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        a = plan.mine(p)
+        torch.cuda.synchronize()
+        a = {k: v.clone() for k, v in a.items()}
+        plan.set_option("link_recount", 1)
+        b = plan.mine(p)
+        plan.check()
+        _outputs_equal(a, b, batch.n_pairs)
