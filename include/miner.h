@@ -167,6 +167,37 @@ int mine_plan_check(mine_plan *plan, miner_stream_t stream);
 int mine_plan_set_timing(mine_plan *plan, int enable);
 int mine_plan_kernel_times(mine_plan *plan, float *host_ms, int64_t *host_launches, int n);
 
+/* Allocation-free alignment of ONE document pair (the paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they call -- a serving loop with a fixed memory budget,
+ * a library embedded in a host framework that owns every device allocation,
+ * or code that cannot afford cudaMalloc's implicit synchronisation).
+ *
+ * Same result as mine_align on a plan holding just this pair (bit-identical
+ * links and score), from the pair's precomputed counts; no plan, no
+ * allocation: the scratch (traceback codes, one boundary row, the path
+ * cells) is one fixed device array of about 1.1 MB inside the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   src_sent_off: n+1 sentence token offsets of the source document (device;
+ *                 only their differences, the sentence lengths, are used)
+ *   tgt_sent_off: m+1 likewise for the target document
+ *   counts:       n*m*2 bytes, (ms, mt) per cell, row-major (as mine_count)
+ *   link_i/j/s:   capacity min(n, m); the kept links, ascending
+ *   n_links, pair_score: one int32 / one float (device)
+ * n and m may be 0; each must be at most MINE_NOALLOC_MAX_SIDE, otherwise the
+ * call returns MINE_EINVAL without launching anything.  Asynchronous on the
+ * stream.  The first call on a device looks up the scratch array's device
+ * address (once per device, with that device current): make that first call
+ * before any stream capture.  Every call uses the same array, so calls whose
+ * kernels overlap on the GPU (other streams, other threads) race and corrupt
+ * each other's results; serialise them.  Nothing needs to be zero beforehand:
+ * each call overwrites every scratch word it reads. */
+#define MINE_NOALLOC_MAX_SIDE 2048
+int mine_align_pair_noalloc(const int64_t *src_sent_off, const int64_t *tgt_sent_off, int32_t n, int32_t m,
+                            const uint8_t *counts, const mine_params *params, int32_t *link_i,
+                            int32_t *link_j, float *link_s, int32_t *n_links, float *pair_score,
+                            miner_stream_t stream);
+
 const char *mine_strerror(int code);
 /* The cudaError_t value behind the last MINE_ECUDA of this thread. */
 int mine_last_cuda_error(void);

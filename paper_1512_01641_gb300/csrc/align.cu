@@ -28,6 +28,7 @@
 // (bounded) on the completion flags of the tile above and the tile to its
 // left, whose boundary row/column it reads from global memory.  Work items are
 // handed out by an atomic counter in the planner's order.
+#include "fill.cuh"
 #include "kernels.h"
 
 namespace gbm {
@@ -43,76 +44,6 @@ __device__ bool wait_flag(const int32_t *f, int64_t limit) {
         __nanosleep(200);
     }
     return false;
-}
-
-struct FillCtx {
-    int lane, N, M, c0, c1, r;
-    bool rv;
-    float two_p;
-    SimRow row;
-    SimConst k;
-    const uchar2 *rowp;   // counts of row r
-    const int64_t *tsent; // target sentence offsets of the pair
-    SimCol *colv;         // shared: per-column similarity constants of the current block
-    DevParams P;
-};
-
-// One 32-column block iteration of a strip sweep.  cur receives the
-// similarities of block jb (rotated); prev holds block jb-1.  rc/rp are the
-// 64-bit traceback registers of this and the previous iteration.
-__device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, bool first_strip,
-                                           const float *__restrict__ hrow, float *__restrict__ hrow_w,
-                                           float (&cur)[32], const float (&prev)[32], uint64_t &rc,
-                                           const uint64_t &rp, float &a_down, float &b,
-                                           uint64_t *__restrict__ tb_strip) {
-    const int lane = C.lane;
-    const int col_base = C.c0 + 32 * jb;
-    const bool lane_col = col_base + lane < C.c1;
-    // UP candidates of the first row of the strip for the 32 columns of this block
-    const float hv = first_strip ? -C.two_p : (lane_col ? __ldcg(hrow + col_base + lane) : 0.0f);
-    if (jb < nb) {
-        __syncwarp();
-        C.colv[lane] = sim_col(lane_col ? (int)(C.tsent[col_base + lane + 1] - C.tsent[col_base + lane]) : 1, C.P);
-        __syncwarp();
-#pragma unroll
-        for (int x = 0; x < 32; ++x) {
-            const int c = (x - lane) & 31;
-            const int col = col_base + c;
-            float v = 0.0f;
-            if (C.rv && col < C.c1) {
-                const uchar2 q = C.rowp[col];
-                v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
-            }
-            cur[x] = v;
-        }
-    }
-    rc = 0;
-#pragma unroll
-    for (int u = 0; u < 32; ++u) {
-        float a_up = __shfl_up_sync(kFull, a_down, 1);
-        const float h0 = __shfl_sync(kFull, hv, u);
-        if (lane == 0) a_up = h0;
-        const int j = col_base + u - lane;
-        const float sv = (u >= lane) ? cur[u] : prev[u];
-        if (C.rv && j >= C.c0 && j < C.c1) {
-            const float d = fmaxf(fmaxf(sv, a_up), b);
-            const uint64_t bits = (d == a_up) ? (uint64_t)kUp << (2 * u)
-                                              : ((d == b) ? (uint64_t)kLeft << (2 * u) : 0ull);
-            rc |= bits;
-            const float e = __fsub_rn(d, C.two_p);
-            const float nb2 = __fsub_rn(e, a_up);
-            a_down = __fsub_rn(e, b);
-            b = nb2;
-            if (lane == 31) __stcg(hrow_w + j, a_down);
-        }
-    }
-    // the word of block jb-1 is complete: its columns came at steps u >= lane
-    // of iteration jb-1 and u < lane of iteration jb
-    if (jb > 0) {
-        const int sh = 2 * lane;
-        const uint64_t w = (rp >> sh) | (sh ? (rc << (64 - sh)) : 0ull);
-        tb_strip[(int64_t)((C.c0 >> 5) + jb - 1) * 32 + lane] = w;
-    }
 }
 
 __global__ void __launch_bounds__(32 * kFillWarps)
@@ -141,7 +72,6 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
         C.c1 = min(C.M, C.c0 + g.cw);
         const bool tiled = g.flag_off >= 0;
         const int nblk_pair = (C.M + 31) >> 5;
-        const int nb = (C.c1 - C.c0 + 31) >> 5;
         const int64_t sbase = src.doc[w.pair];
         C.tsent = tgt.sent + tgt.doc[w.pair];
         float *hrow = S.hrow + g.hrow_off;
@@ -157,24 +87,9 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
                 if (s > 0) (void)ld_acquire(S.flags + g.flag_off + (int64_t)(s - 1) * g.nchunk + w.cj);
                 if (w.cj > 0) (void)ld_acquire(S.flags + g.flag_off + (int64_t)s * g.nchunk + w.cj - 1);
             }
-            C.r = 32 * s + lane;
-            C.rv = C.r < C.N;
-            const int ls = C.rv ? (int)(src.sent[sbase + C.r + 1] - src.sent[sbase + C.r]) : 1;
-            C.row = sim_row(ls, P);
-            C.rowp = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)C.r * C.M;
             float b = -C.two_p;
-            if (C.c0 > 0 && C.rv) b = __ldcg(S.vcol + g.vcol_off + C.r);
-            float a_down = 0.0f;
-            float A[32], B[32];
-#pragma unroll
-            for (int x = 0; x < 32; ++x) B[x] = 0.0f;
-            uint64_t RA = 0, RB = 0;
-            uint64_t *tb_strip = S.tb + g.tb_off + (int64_t)s * nblk_pair * 32;
-            for (int jb = 0; jb <= nb; jb += 2) {
-                fill_block(C, jb, nb, s == 0, hrow, hrow, A, B, RA, RB, a_down, b, tb_strip);
-                if (jb + 1 > nb) break;
-                fill_block(C, jb + 1, nb, s == 0, hrow, hrow, B, A, RB, RA, a_down, b, tb_strip);
-            }
+            if (C.c0 > 0 && 32 * s + lane < C.N) b = __ldcg(S.vcol + g.vcol_off + 32 * s + lane);
+            b = fill_strip(C, s, src.sent + sbase, counts, g.cell_off, hrow, S.tb + g.tb_off, nblk_pair, b);
             if (tiled) {
                 if (C.c1 < C.M && C.rv) __stcg(S.vcol + g.vcol_off + C.r, b);
                 __threadfence();
@@ -200,36 +115,9 @@ walk_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, AlignScratch S) 
     for (int64_t k = warp0; k < n_pairs; k += nwarps) {
         const PairGeom g = geom[k];
         const int N = g.n, M = g.m;
-        const int nblk = (M + 31) >> 5;
         const int cap = min(N, M);
-        const uint64_t *tbp = S.tb + g.tb_off;
-        int i = N, j = M, n = 0;
-        int bs = -1, bj = -1;  // strip and column block held in `word`
-        uint64_t word = 0;
-        while (i > 0 && j > 0) {
-            const int rr = i - 1, cc = j - 1;
-            if ((rr >> 5) != bs || (cc >> 5) != bj) {
-                bs = rr >> 5;
-                bj = cc >> 5;
-                word = tbp[((int64_t)bs * nblk + bj) * 32 + lane];
-            }
-            const uint64_t wr = __shfl_sync(kFull, word, rr & 31);
-            const uint32_t code = (uint32_t)(wr >> (2 * (cc & 31))) & 3u;
-            if (code == kUp) {
-                --i;
-            } else if (code == kLeft) {
-                --j;
-            } else {
-                if (lane == 0) {
-                    const int64_t at = g.link_off + cap - 1 - n;
-                    S.diag_i[at] = rr;
-                    S.diag_j[at] = cc;
-                }
-                ++n;
-                --i;
-                --j;
-            }
-        }
+        const int n = walk_pair(S.tb + g.tb_off, N, M, lane, S.diag_i + g.link_off + cap,
+                                S.diag_j + g.link_off + cap);
         if (lane == 0) S.n_diag[k] = n;
     }
 }
@@ -347,18 +235,9 @@ pair_sum_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, DevParams P,
         const PairGeom g = geom[k];
         const int nd = S.n_diag[k];
         const int64_t base = g.link_off + min(g.n, g.m) - nd;
-        double sum = 0.0;
-        int kept = 0;
-        for (int x = lane; x < nd; x += 32) {
-            const float s = S.diag_s[base + x];
-            sum += (double)s;
-            kept += s >= P.thr;
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sum += __shfl_xor_sync(kFull, sum, off);
-            kept += __shfl_xor_sync(kFull, kept, off);
-        }
+        double sum;
+        int kept;
+        pair_sum_warp(S.diag_s + base, nd, P.thr, lane, sum, kept);
         if (lane == 0) {
             const int gaps = g.n + g.m - 2 * nd;
             pair_score[k] = (float)(sum - (double)P.gap * (double)gaps);
@@ -379,21 +258,8 @@ copy_links_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, DevParams 
         const PairGeom g = geom[k];
         const int nd = S.n_diag[k];
         const int64_t base = g.link_off + min(g.n, g.m) - nd;
-        int64_t to = link_off[k];
-        for (int x0 = 0; x0 < nd; x0 += 32) {
-            const int x = x0 + lane;
-            const bool in = x < nd;
-            const float s = in ? S.diag_s[base + x] : 0.0f;
-            const bool keep = in && s >= P.thr;
-            const uint32_t m = __ballot_sync(kFull, keep);
-            if (keep) {
-                const int64_t o = to + __popc(m & ((1u << lane) - 1u));
-                out_i[o] = S.diag_i[base + x];
-                out_j[o] = S.diag_j[base + x];
-                out_s[o] = s;
-            }
-            to += __popc(m);
-        }
+        copy_kept_warp(S.diag_i + base, S.diag_j + base, S.diag_s + base, nd, P.thr, lane, out_i + link_off[k],
+                       out_j + link_off[k], out_s + link_off[k]);
     }
 }
 

@@ -1,0 +1,189 @@
+// Device building blocks of the Needleman-Wunsch fill and traceback, shared
+// by the batched kernels (align.cu) and the allocation-free single-pair
+// variant (noalloc.cu), so that both run the same arithmetic.
+#pragma once
+
+#include "common.cuh"
+
+namespace gbm {
+
+struct FillCtx {
+    int lane, N, M, c0, c1, r;
+    bool rv;
+    float two_p;
+    SimRow row;
+    SimConst k;
+    const uchar2 *rowp;   // counts of row r
+    const int64_t *tsent; // target sentence offsets of the pair
+    SimCol *colv;         // shared: per-column similarity constants of the current block
+    DevParams P;
+};
+
+// One 32-column block iteration of a strip sweep.  cur receives the
+// similarities of block jb (rotated); prev holds block jb-1.  rc/rp are the
+// 64-bit traceback registers of this and the previous iteration.
+__device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, bool first_strip,
+                                           const float *__restrict__ hrow, float *__restrict__ hrow_w,
+                                           float (&cur)[32], const float (&prev)[32], uint64_t &rc,
+                                           const uint64_t &rp, float &a_down, float &b,
+                                           uint64_t *__restrict__ tb_strip) {
+    const int lane = C.lane;
+    const int col_base = C.c0 + 32 * jb;
+    const bool lane_col = col_base + lane < C.c1;
+    // UP candidates of the first row of the strip for the 32 columns of this block
+    const float hv = first_strip ? -C.two_p : (lane_col ? __ldcg(hrow + col_base + lane) : 0.0f);
+    if (jb < nb) {
+        __syncwarp();
+        C.colv[lane] = sim_col(lane_col ? (int)(C.tsent[col_base + lane + 1] - C.tsent[col_base + lane]) : 1, C.P);
+        __syncwarp();
+#pragma unroll
+        for (int x = 0; x < 32; ++x) {
+            const int c = (x - lane) & 31;
+            const int col = col_base + c;
+            float v = 0.0f;
+            if (C.rv && col < C.c1) {
+                const uchar2 q = C.rowp[col];
+                v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
+            }
+            cur[x] = v;
+        }
+    }
+    rc = 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+        float a_up = __shfl_up_sync(kFull, a_down, 1);
+        const float h0 = __shfl_sync(kFull, hv, u);
+        if (lane == 0) a_up = h0;
+        const int j = col_base + u - lane;
+        const float sv = (u >= lane) ? cur[u] : prev[u];
+        if (C.rv && j >= C.c0 && j < C.c1) {
+            const float d = fmaxf(fmaxf(sv, a_up), b);
+            const uint64_t bits = (d == a_up) ? (uint64_t)kUp << (2 * u)
+                                              : ((d == b) ? (uint64_t)kLeft << (2 * u) : 0ull);
+            rc |= bits;
+            const float e = __fsub_rn(d, C.two_p);
+            const float nb2 = __fsub_rn(e, a_up);
+            a_down = __fsub_rn(e, b);
+            b = nb2;
+            if (lane == 31) __stcg(hrow_w + j, a_down);
+        }
+    }
+    // the word of block jb-1 is complete: its columns came at steps u >= lane
+    // of iteration jb-1 and u < lane of iteration jb
+    if (jb > 0) {
+        const int sh = 2 * lane;
+        const uint64_t w = (rp >> sh) | (sh ? (rc << (64 - sh)) : 0ull);
+        tb_strip[(int64_t)((C.c0 >> 5) + jb - 1) * 32 + lane] = w;
+    }
+}
+
+
+// Sweep strip s (rows 32s..32s+31) over columns [C.c0, C.c1).  b0 holds the
+// LEFT candidates of column c0 (-2p at the left border); returns each lane's
+// LEFT candidate after the last column.  hrow holds the UP candidates of the
+// row above the strip and receives those of the strip's last row.
+__device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__restrict__ ssent,
+                                            const uint8_t *__restrict__ counts, int64_t cell_off,
+                                            float *__restrict__ hrow, uint64_t *__restrict__ tb_pair,
+                                            int nblk_pair, float b0) {
+    const int lane = C.lane;
+    C.r = 32 * s + lane;
+    C.rv = C.r < C.N;
+    const int ls = C.rv ? (int)(ssent[C.r + 1] - ssent[C.r]) : 1;
+    C.row = sim_row(ls, C.P);
+    C.rowp = reinterpret_cast<const uchar2 *>(counts) + cell_off + (int64_t)C.r * C.M;
+    const int nb = (C.c1 - C.c0 + 31) >> 5;
+    float b = b0, a_down = 0.0f;
+    float A[32], B[32];
+#pragma unroll
+    for (int x = 0; x < 32; ++x) B[x] = 0.0f;
+    uint64_t RA = 0, RB = 0;
+    uint64_t *tb_strip = tb_pair + (int64_t)s * nblk_pair * 32;
+    for (int jb = 0; jb <= nb; jb += 2) {
+        fill_block(C, jb, nb, s == 0, hrow, hrow, A, B, RA, RB, a_down, b, tb_strip);
+        if (jb + 1 > nb) break;
+        fill_block(C, jb + 1, nb, s == 0, hrow, hrow, B, A, RB, RA, a_down, b, tb_strip);
+    }
+    return b;
+}
+
+// Walk back from (N,M) to (0,0) for one pair (whole warp, same path in every
+// lane).  The 32 x 32 block of traceback codes around the current cell sits
+// in registers (lane l holds the word of row l of the block), so a step costs
+// a shuffle; leaving the block loads the next one with one coalesced 256-byte
+// read.  The t-th diagonal cell found (from the end) is written at index
+// -1-t of diag_i_end / diag_j_end, so the cells end up ascending.  Returns the
+// number of diagonal cells.
+__device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N, int M, int lane,
+                                         int32_t *diag_i_end, int32_t *diag_j_end) {
+    const int nblk = (M + 31) >> 5;
+    int i = N, j = M, n = 0;
+    int bs = -1, bj = -1;
+    uint64_t word = 0;
+    while (i > 0 && j > 0) {
+        const int rr = i - 1, cc = j - 1;
+        if ((rr >> 5) != bs || (cc >> 5) != bj) {
+            bs = rr >> 5;
+            bj = cc >> 5;
+            word = tbp[((int64_t)bs * nblk + bj) * 32 + lane];
+        }
+        const uint64_t wr = __shfl_sync(kFull, word, rr & 31);
+        const uint32_t code = (uint32_t)(wr >> (2 * (cc & 31))) & 3u;
+        if (code == kUp) {
+            --i;
+        } else if (code == kLeft) {
+            --j;
+        } else {
+            if (lane == 0) {
+                diag_i_end[-1 - n] = rr;
+                diag_j_end[-1 - n] = cc;
+            }
+            ++n;
+            --i;
+            --j;
+        }
+    }
+    return n;
+}
+
+// Sum (FP64, fixed order: lane-strided partial sums, then a butterfly) of nd
+// similarities, and the number of them >= thr; every lane gets the totals.
+__device__ __forceinline__ void pair_sum_warp(const float *__restrict__ s, int nd, float thr, int lane,
+                                              double &sum, int &kept) {
+    sum = 0.0;
+    kept = 0;
+    for (int x = lane; x < nd; x += 32) {
+        const float v = s[x];
+        sum += (double)v;
+        kept += v >= thr;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sum += __shfl_xor_sync(kFull, sum, off);
+        kept += __shfl_xor_sync(kFull, kept, off);
+    }
+}
+
+// Copy the cells with s >= thr, in order, to out_*[0..).
+__device__ __forceinline__ void copy_kept_warp(const int32_t *__restrict__ di, const int32_t *__restrict__ dj,
+                                               const float *__restrict__ ds, int nd, float thr, int lane,
+                                               int32_t *__restrict__ out_i, int32_t *__restrict__ out_j,
+                                               float *__restrict__ out_s) {
+    int64_t to = 0;
+    for (int x0 = 0; x0 < nd; x0 += 32) {
+        const int x = x0 + lane;
+        const bool in = x < nd;
+        const float s = in ? ds[x] : 0.0f;
+        const bool keep = in && s >= thr;
+        const uint32_t m = __ballot_sync(kFull, keep);
+        if (keep) {
+            const int64_t o = to + __popc(m & ((1u << lane) - 1u));
+            out_i[o] = di[x];
+            out_j[o] = dj[x];
+            out_s[o] = s;
+        }
+        to += __popc(m);
+    }
+}
+
+}  // namespace gbm

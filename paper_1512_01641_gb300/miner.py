@@ -67,6 +67,9 @@ _SIGS = {
     "mine_plan_get_option": (C.c_int64, [C.c_void_p, C.c_int]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mine_plan_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mine_align_pair_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                         C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]),
     "mine_strerror": (C.c_char_p, [C.c_int]),
     "mine_last_cuda_error": (C.c_int, []),
 }
