@@ -162,10 +162,47 @@ int mine_plan_check(mine_plan *plan, miner_stream_t stream);
  * matching launch counts into host_launches (either may be NULL); it returns
  * the number of kernel kinds (MINE_KERNEL_KINDS).  Kinds, in order: count,
  * fill, walk (traceback), links (link scoring, pair sums, compaction), scan,
- * score. */
-#define MINE_KERNEL_KINDS 6
+ * score, soft forward, soft backward. */
+#define MINE_KERNEL_KINDS 8
 int mine_plan_set_timing(mine_plan *plan, int enable);
 int mine_plan_kernel_times(mine_plan *plan, float *host_ms, int64_t *host_launches, int n);
+
+/* ---------------------------------------------------------------------------
+ * Soft (differentiable) alignment for tuning w, b, gap and thr.
+ *
+ * The paper tunes the threshold and the gap penalty by random search against
+ * human alignments (Section 5.2).  This library replaces the search by
+ * gradients of a smoothed alignment: every max of the Needleman-Wunsch fill
+ * (Section 5.1, Eq. 1) becomes gamma * log-sum-exp(. / gamma), giving the
+ * soft value V and the expected alignment E = dV(N,M)/ds (the probability
+ * that the alignment pairs source sentence i with target sentence j).  With
+ * gold links g (0/1 per cell) the loss is
+ *   P = clamp(E * sigmoid((s - thr) / tau), eps, 1 - eps)
+ *   L = mean over all cells of all pairs of -(g log P + (1-g) log(1-P)).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    float gamma; /* smoothing temperature (> 0); -> hard NW as gamma -> 0 */
+    float tau;   /* gate temperature of the acceptance threshold (> 0) */
+    float eps;   /* clamp of P (0 < eps < 0.5) */
+} softnw_opts;
+
+/* Bytes of the caller-provided workspace of softnw_fwd / softnw_bwd. */
+int64_t softnw_workspace_size(const mine_plan *plan);
+
+/* Loss L (one float at *loss, device) from cached counts (as mine_count) and
+ * gold (one byte per cell, 0 or 1).  Optional outputs (NULL to skip): value
+ * (n_pairs floats, soft V(N,M) per pair) and expected (n_cells floats, E).
+ * Keeps E in the workspace for softnw_bwd. */
+int softnw_fwd(mine_plan *plan, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
+               const uint8_t *gold, void *ws, float *loss, float *value, float *expected,
+               miner_stream_t stream);
+
+/* dloss * dL/d(w0, w1, w2, w3, b, gap, thr) into grad (7 floats, device).
+ * hvp (optional, n_cells floats): the Hessian-vector product H u of V with
+ * u = dL/dE, i.e. the derivative of E along u (dL/ds through E).
+ * Must follow softnw_fwd with the same plan, arguments and workspace. */
+int softnw_bwd(mine_plan *plan, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
+               const uint8_t *gold, void *ws, float dloss, float *grad, float *hvp, miner_stream_t stream);
 
 /* Allocation-free alignment of ONE document pair (the paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -84,10 +84,29 @@ def loss_and_grad(pairs, theta, gamma, tau, eps=1e-7):
     th = torch.as_tensor(np.asarray(theta, np.float64), dtype=T).clone().requires_grad_(True)
     L = loss(pairs, th, gamma, tau, eps)
     (g,) = torch.autograd.grad(L, th)
-    return float(L), g.numpy()
+    return float(L.detach()), g.numpy()
 
 
 def loss_value(pairs, theta, gamma, tau, eps=1e-7) -> float:
     """Loss only (still differentiates V once, to get E)."""
     th = torch.as_tensor(np.asarray(theta, np.float64), dtype=T)
     return float(loss(pairs, th, gamma, tau, eps, create_graph=False))
+
+
+def hvp_cells(ms, mt, ls, lt, gold, theta, gamma, tau, n_cells_total, eps=1e-7):
+    """For one pair: (E, u, H u) with u = dL/dE at fixed s (loss normalised by
+    n_cells_total), H the Hessian of V in s; all float64 numpy arrays."""
+    th = torch.as_tensor(np.asarray(theta, np.float64), dtype=T)
+    w, b, gap, thr = th[:4], th[4], th[5], th[6]
+    f = features(ms, mt, ls, lt)
+    s = torch.sigmoid(f @ w + b).detach().requires_grad_(True)
+    V = soft_value(s, gap, gamma)
+    (E,) = torch.autograd.grad(V, s, create_graph=True)
+    Ed = E.detach().requires_grad_(True)
+    G = torch.sigmoid((s.detach() - thr) / tau)
+    P = torch.clamp(Ed * G, eps, 1.0 - eps)
+    g = torch.as_tensor(np.asarray(gold), dtype=T)
+    L = -(g * torch.log(P) + (1 - g) * torch.log(1 - P)).sum() / n_cells_total
+    (u,) = torch.autograd.grad(L, Ed)
+    (hu,) = torch.autograd.grad(E, s, grad_outputs=u)
+    return E.detach().numpy(), u.numpy(), hu.numpy()

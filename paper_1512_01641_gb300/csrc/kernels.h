@@ -43,6 +43,7 @@ struct PairGeom {
     int64_t vcol_off;  // first float of the pair's boundary column (N floats)
     int64_t flag_off;  // first tile flag (nstrips * nchunk ints), -1 if one warp does the pair
     int32_t n, m;      // sentence counts
+    int64_t soft_off;  // first float of the pair's soft-alignment checkpoint rows (nstrips * M)
     int32_t cw;        // fill column chunk width (multiple of 32)
     int32_t nchunk;    // number of column chunks
 };
@@ -116,7 +117,33 @@ cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const DevPa
                               const AlignScratch &S, const int64_t *link_off, int32_t *out_i,
                               int32_t *out_j, float *out_s, int n_sms, cudaStream_t st);
 
+// Soft alignment: scalar arguments and the caller's workspace, carved up.
+struct SoftArgs {
+    float gamma, tau, eps, inv_cells;
+};
+struct SoftScratch {
+    double *partial;      // n_pairs x 9: loss, V, seven gradients
+    int32_t *queue;       // work counter
+    float *E;             // expected alignment per cell
+    float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
+    float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
+    float *sbuf;          // per-warp strip buffers
+    int64_t sbuf_stride;  // floats per warp
+};
+
+int64_t soft_warps(int n_sms);
+
+cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
+                                const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
+                                const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float *loss,
+                                float *value, int n_sms, cudaStream_t st);
+
+cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
+                                 const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
+                                 const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float dloss,
+                                 float *grad, float *hvp, int n_sms, cudaStream_t st);
+
 // Kernel kinds of the per-kernel timing hook (order of MINE_KERNEL_KINDS).
-enum KernelKind { kKCount = 0, kKFill, kKWalk, kKLinks, kKScan, kKScore, kKinds };
+enum KernelKind { kKCount = 0, kKFill, kKWalk, kKLinks, kKScan, kKScore, kKSoftFwd, kKSoftBwd, kKinds };
 
 }  // namespace gbm

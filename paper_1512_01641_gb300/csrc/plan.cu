@@ -117,6 +117,10 @@ struct mine_plan {
     int64_t n_pairs = 0, n_cells = 0, link_cap = 0, n_count_items = 0, n_fill_items = 0, n_flags = 0;
     std::vector<int64_t> cell_off_h;
     std::vector<PairGeom> geom_h;
+    std::vector<int32_t> pair_order_h;  // pairs by decreasing size
+    int32_t *pair_order = nullptr;
+    int64_t soft_rows = 0;              // sum over pairs of nstrips * M
+    int32_t max_m = 0;
     PlanKnobs knobs;
     PairGeom *geom = nullptr;
     CountItem *count_items = nullptr;
@@ -183,7 +187,7 @@ static void drain_pending(mine_plan *p) {
 static void plan_free(mine_plan *p) {
     if (!p) return;
     drain_pending(p);
-    void *bufs[] = {p->geom, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
+    void *bufs[] = {p->geom, p->pair_order, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
                     p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
                     p->S.diag_off, p->S.n_links, p->stats};
     for (void *b : bufs)
@@ -215,6 +219,8 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     const PlanKnobs &K = p->knobs;
     p->geom_h.assign(n, PairGeom{});
     p->cell_off_h.assign(n + 1, 0);
+    p->soft_rows = 0;
+    p->max_m = 0;
     int64_t cell = 0, link = 0, flags = 0;
     tbw = hrow = vcol = 0;
     std::vector<int32_t> small, tiled;
@@ -227,6 +233,9 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
         g.link_off = link;
         g.hrow_off = hrow;
         g.vcol_off = vcol;
+        g.soft_off = p->soft_rows;
+        p->soft_rows += ((g.n + 31) / 32) * (int64_t)g.m;
+        p->max_m = std::max(p->max_m, g.m);
         p->cell_off_h[k] = cell;
         const int64_t ns = (g.n + 31) / 32, nb = (g.m + 31) / 32;
         const int64_t cells = (int64_t)g.n * g.m;
@@ -257,6 +266,10 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     auto cells_of = [&](int32_t k) { return (int64_t)p->geom_h[k].n * p->geom_h[k].m; };
     std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
     std::stable_sort(tiled.begin(), tiled.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
+    p->pair_order_h.resize(n);
+    std::iota(p->pair_order_h.begin(), p->pair_order_h.end(), 0);
+    std::stable_sort(p->pair_order_h.begin(), p->pair_order_h.end(),
+                     [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
 
     // count items: 32 x 32 blocks, large pairs first
     citems.clear();
@@ -368,6 +381,8 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     PLAN_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->count_items, citems.size()));
     PLAN_CK(cudaMemcpyAsync(p->count_items, citems.data(), citems.size() * sizeof(CountItem), cudaMemcpyHostToDevice, st));
+    PLAN_CK(dalloc(&p->pair_order, n));
+    PLAN_CK(cudaMemcpyAsync(p->pair_order, p->pair_order_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->fill_items, fitems.size()));
     PLAN_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice, st));
 
@@ -530,6 +545,98 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
     int r = mine_count(p, p->counts, stream);
     if (r != MINE_OK) return r;
     return mine_align(p, params, p->counts, out, stream);
+}
+
+// ------------------------------------------------------------- soft alignment
+static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct SoftLayout {
+    int64_t partial, queue, E, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
+};
+
+static SoftLayout soft_layout(const mine_plan *p) {
+    SoftLayout L;
+    int64_t o = 0;
+    L.partial = o;
+    o = align_up(o + std::max<int64_t>(p->n_pairs, 1) * 9 * (int64_t)sizeof(double), 256);
+    L.queue = o;
+    o = align_up(o + 4, 256);
+    L.E = o;
+    o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
+    const int64_t rows = std::max<int64_t>(p->soft_rows, 1) * 4;
+    L.ckv = o;
+    o = align_up(o + rows, 256);
+    L.ckt = o;
+    o = align_up(o + rows, 256);
+    L.qrow = o;
+    o = align_up(o + rows, 256);
+    L.qtrow = o;
+    o = align_up(o + rows, 256);
+    L.sbuf_stride = 6 * (int64_t)(p->max_m + 31) * 32;
+    L.sbuf = o;
+    o = align_up(o + soft_warps(p->n_sms) * L.sbuf_stride * 4, 256);
+    L.total = o;
+    return L;
+}
+
+static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
+    const SoftLayout L = soft_layout(p);
+    char *b = static_cast<char *>(ws);
+    SoftScratch W;
+    W.partial = reinterpret_cast<double *>(b + L.partial);
+    W.queue = reinterpret_cast<int32_t *>(b + L.queue);
+    W.E = reinterpret_cast<float *>(b + L.E);
+    W.ckv = reinterpret_cast<float *>(b + L.ckv);
+    W.ckt = reinterpret_cast<float *>(b + L.ckt);
+    W.qrow = reinterpret_cast<float *>(b + L.qrow);
+    W.qtrow = reinterpret_cast<float *>(b + L.qtrow);
+    W.sbuf = reinterpret_cast<float *>(b + L.sbuf);
+    W.sbuf_stride = L.sbuf_stride;
+    return W;
+}
+
+static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A) {
+    if (!o || !(o->gamma > 0.0f) || !(o->tau > 0.0f) || !(o->eps > 0.0f) || !(o->eps < 0.5f)) return false;
+    A.gamma = o->gamma;
+    A.tau = o->tau;
+    A.eps = o->eps;
+    A.inv_cells = p->n_cells > 0 ? (float)(1.0 / (double)p->n_cells) : 0.0f;
+    return true;
+}
+
+int64_t softnw_workspace_size(const mine_plan *p) { return p ? soft_layout(p).total : MINE_EINVAL; }
+
+int softnw_fwd(mine_plan *p, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
+               const uint8_t *gold, void *ws, float *loss, float *value, float *expected, miner_stream_t stream) {
+    SoftArgs A;
+    if (!p || !params || !ws || !loss || !soft_args(p, opts, A)) return MINE_EINVAL;
+    if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
+    if (p->max_m > (1 << 20)) return MINE_ENOTSUP;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SoftScratch W = soft_scratch(p, ws);
+    const DevParams P = to_dev(*params);
+    MINE_CK(timed(p, kKSoftFwd, st, [&] {
+        return launch_soft_forward(p->src, p->tgt, p->geom, p->pair_order, p->n_pairs, P, A, counts, gold, W, loss,
+                                   value, p->n_sms, st);
+    }));
+    if (expected && p->n_cells > 0)
+        MINE_CK(cudaMemcpyAsync(expected, W.E, p->n_cells * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return MINE_OK;
+}
+
+int softnw_bwd(mine_plan *p, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
+               const uint8_t *gold, void *ws, float dloss, float *grad, float *hvp, miner_stream_t stream) {
+    SoftArgs A;
+    if (!p || !params || !ws || !grad || !soft_args(p, opts, A)) return MINE_EINVAL;
+    if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const SoftScratch W = soft_scratch(p, ws);
+    const DevParams P = to_dev(*params);
+    MINE_CK(timed(p, kKSoftBwd, st, [&] {
+        return launch_soft_backward(p->src, p->tgt, p->geom, p->pair_order, p->n_pairs, P, A, counts, gold, W, dloss,
+                                    grad, hvp, p->n_sms, st);
+    }));
+    return MINE_OK;
 }
 
 int mine_plan_check(mine_plan *p, miner_stream_t stream) {

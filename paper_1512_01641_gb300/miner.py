@@ -44,6 +44,10 @@ class _Params(C.Structure):
     _fields_ = [("w", C.c_float * 4), ("b", C.c_float), ("gap", C.c_float), ("thr", C.c_float)]
 
 
+class _SoftOpts(C.Structure):
+    _fields_ = [("gamma", C.c_float), ("tau", C.c_float), ("eps", C.c_float)]
+
+
 class _Out(C.Structure):
     _fields_ = [("link_off", C.c_void_p), ("link_i", C.c_void_p), ("link_j", C.c_void_p),
                 ("link_s", C.c_void_p), ("pair_score", C.c_void_p), ("link_capacity", C.c_int64)]
@@ -67,6 +71,11 @@ _SIGS = {
     "mine_plan_get_option": (C.c_int64, [C.c_void_p, C.c_int]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "mine_plan_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "softnw_workspace_size": (C.c_int64, [C.c_void_p]),
+    "softnw_fwd": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_SoftOpts), C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "softnw_bwd": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_SoftOpts), C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mine_align_pair_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                          C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
@@ -206,7 +215,7 @@ class Plan:
     def __exit__(self, *a):
         self.close()
 
-    KERNEL_KINDS = ("count", "fill", "walk", "links", "scan", "score")
+    KERNEL_KINDS = ("count", "fill", "walk", "links", "scan", "score", "soft_fwd", "soft_bwd")
 
     def set_option(self, name: str, value: int):
         _check(lib().mine_plan_set_option(self._h, OPTIONS[name], int(value)), f"mine_plan_set_option({name})")
@@ -290,3 +299,93 @@ def links_per_pair(out, n_pairs):
     li, lj, ls = (out[k].cpu().numpy() for k in ("link_i", "link_j", "link_s"))
     return [list(zip(li[off[k]:off[k + 1]].tolist(), lj[off[k]:off[k + 1]].tolist(),
                      ls[off[k]:off[k + 1]].tolist())) for k in range(n_pairs)]
+
+
+# ---------------------------------------------------------------------------
+# soft alignment (softnw_fwd / softnw_bwd) and its autograd wrapper
+# ---------------------------------------------------------------------------
+THETA_NAMES = ("w0", "w1", "w2", "w3", "b", "gap", "thr")
+
+
+def params_from_theta(theta) -> MineParams:
+    t = [float(x) for x in theta]
+    return MineParams(w=tuple(t[:4]), b=t[4], gap=t[5], thr=t[6])
+
+
+class SoftAligner:
+    """Soft alignment loss over a plan's pairs, from cached counts and gold
+    links (one 0/1 byte per cell, row-major per pair like the counts)."""
+
+    def __init__(self, plan: Plan, counts, gold, gamma: float, tau: float = 0.05, eps: float = 1e-7):
+        import torch
+        self.plan, self.counts, self.gold = plan, counts, gold
+        self.opts = _SoftOpts(float(gamma), float(tau), float(eps))
+        n = lib().softnw_workspace_size(plan.handle)
+        if n < 0:
+            _check(int(n), "softnw_workspace_size")
+        self.ws = torch.empty(max(int(n), 1), dtype=torch.uint8, device="cuda")
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.grad = torch.zeros(7, dtype=torch.float32, device="cuda")
+
+    def forward(self, params: MineParams, want_value=False, want_expected=False, stream=None):
+        import torch
+        value = torch.empty(max(self.plan.n_pairs, 1), dtype=torch.float32, device="cuda") if want_value else None
+        exp = torch.empty(max(self.plan.n_cells, 1), dtype=torch.float32, device="cuda") if want_expected else None
+        p = params.c()
+        _check(lib().softnw_fwd(self.plan.handle, C.byref(p), C.byref(self.opts), _ptr(self.counts), _ptr(self.gold),
+                                _ptr(self.ws), _ptr(self.loss), _ptr(value), _ptr(exp), _stream(stream)), "softnw_fwd")
+        return self.loss, value, exp
+
+    def backward(self, params: MineParams, dloss: float = 1.0, want_hvp=False, stream=None):
+        import torch
+        hvp = torch.empty(max(self.plan.n_cells, 1), dtype=torch.float32, device="cuda") if want_hvp else None
+        p = params.c()
+        _check(lib().softnw_bwd(self.plan.handle, C.byref(p), C.byref(self.opts), _ptr(self.counts), _ptr(self.gold),
+                                _ptr(self.ws), C.c_float(dloss), _ptr(self.grad), _ptr(hvp), _stream(stream)),
+               "softnw_bwd")
+        return (self.grad, hvp) if want_hvp else self.grad
+
+
+def _soft_fn():
+    import torch
+
+    class SoftNWLoss(torch.autograd.Function):
+        """loss = SoftNWLoss.apply(theta, aligner), theta = [w0..w3, b, gap, thr].
+
+        Forward and backward run in the library's kernels (softnw_fwd /
+        softnw_bwd); theta is read back to the host for the kernel arguments."""
+
+        @staticmethod
+        def forward(ctx, theta, aligner):
+            params = params_from_theta(theta.detach().cpu().tolist())
+            loss, _, _ = aligner.forward(params)
+            ctx.aligner, ctx.params = aligner, params
+            return loss[0].clone()
+
+        @staticmethod
+        def backward(ctx, dloss):
+            g = ctx.aligner.backward(ctx.params, float(dloss))
+            return g.clone().to(dloss.dtype), None
+
+    return SoftNWLoss
+
+
+_SOFT_FN = None
+
+
+def soft_nw_loss(theta, aligner: SoftAligner):
+    """Differentiable soft-alignment loss (autograd through the CUDA kernels)."""
+    global _SOFT_FN
+    if _SOFT_FN is None:
+        _SOFT_FN = _soft_fn()
+    return _SOFT_FN.apply(theta, aligner)
+
+
+def gold_cells(batch, plan: Plan):
+    """One 0/1 byte per cell from the batch's planted gold links (host array)."""
+    g = np.zeros(max(plan.n_cells, 1), np.uint8)
+    M = batch.tgt.doc_sizes()
+    for k, links in enumerate(batch.gold):
+        if len(links):
+            g[plan.cell_offsets[k] + links[:, 0].astype(np.int64) * M[k] + links[:, 1]] = 1
+    return g
