@@ -42,6 +42,27 @@ OPS_SIM = 11   # 4 quotients, 4 multiply-adds, exp, add, reciprocal
 OPS_DP = 8     # 3 candidates, 2 max, 2 compare/select, 1 pack
 
 
+# DRAM bytes per cell of the dominant kernels, from one ncu capture
+# (profiles/), valid only while the kernel's source is unchanged.
+TRAFFIC = {
+    "count": {"file": "paper_1512_01641_gb300/csrc/count.cu", "sha1": None, "bytes_per_cell": None},
+}
+
+
+def traffic_per_launch(kind, cells):
+    import hashlib
+    t = TRAFFIC.get(kind)
+    if not t or not t["sha1"] or t["bytes_per_cell"] is None:
+        return None
+    try:
+        with open(os.path.join(HERE, t["file"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes_per_cell"] * cells
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -55,6 +76,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-pairs", type=int, default=8000, help="pairs in the oracle's timed sample")
+    ap.add_argument("--no-tune", action="store_true", help="skip the tuning comparison")
+    ap.add_argument("--tune-pairs", type=int, default=50_000)
+    ap.add_argument("--tune-eval", type=int, default=10_000)
+    ap.add_argument("--tune-steps", type=int, default=200)
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -187,6 +213,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tune(args):
+    """Soft-NW gradient tuning (Adam) vs the 7^3 grid search, same GPU,
+    evaluated by hard-NW micro-F1 on held-out planted pairs."""
+    from paper_1512_01641_gb300 import tune
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
+    dic = synth.make_dictionary(rng, 50_000, 50_000)
+    tr = synth.tune_batch(args.tune_pairs, seed=synth.SEED_BASE + 4, dic=dic)
+    ev = synth.tune_batch(args.tune_eval, seed=synth.SEED_BASE + 5, dic=dic)
+    r = tune.compare(tr, ev, steps=args.tune_steps)
+    r["train_cells"] = tr.cells()
+    return r
+
+
 def e2e_run(batch, params, steps):
     """Public API from pinned host buffers: upload, plan, mine, download."""
     import torch
@@ -233,6 +272,11 @@ def main():
     db = miner.DeviceBatch.from_batch(batch)
     plan = miner.Plan(db)
     out = plan.new_output()
+    tuned = None
+    if not args.no_autotune:
+        from paper_1512_01641_gb300 import autotune
+        tuned = autotune.autotune(plan, batch, params, cache_path=None)
+        tuned = {"best": tuned["best"], "fill_ms": tuned["fill_ms"], "candidates": len(tuned["trials"])}
     for _ in range(args.warmup):
         plan.mine(params, out)
     torch.cuda.synchronize()
@@ -241,10 +285,10 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    plan.set_timing(True)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(lrank) as clk:
+        # timed region: K graph launches of the whole batch
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -253,9 +297,21 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    secs = ev0.elapsed_time(ev1) / 1000.0
-    kt = plan.kernel_times()
+        secs = ev0.elapsed_time(ev1) / 1000.0
+        # per-kernel pass: the same K steps launched directly, each kernel
+        # bracketed by CUDA events on its launching stream
+        plan.set_timing(True)
+        ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev2.record(stream)
+        for _ in range(args.steps):
+            plan.mine(params, out)
+        ev3.record(stream)
+        torch.cuda.synchronize()
+        secs_direct = ev2.elapsed_time(ev3) / 1000.0
+        kt = plan.kernel_times()
+        plan.set_timing(False)
     clocks = clk.summary()
+    plan.check()
     if world > 1:
         t = torch.tensor([secs], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -277,9 +333,9 @@ def main():
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak = N_SMS * LANES_PER_SM * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic_per_launch(dom, n_cells),
                 "ops_per_launch": ops, "ms_per_launch": dom_ms,
-                "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lane-ops/clk x {sm_max:.0f} MHz"}
+                "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lane-ops/clk x {sm_max:.0f} MHz (max SM clock)"}
 
     e2e = None
     if not args.no_e2e:
@@ -294,13 +350,23 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(batch, args.cpu_pairs)
 
+    tune_rec = None
+    if rank == 0 and not args.no_tune:
+        try:
+            tune_rec = run_tune(args)
+        except Exception as exc:  # the tuning comparison must not lose the bench line
+            tune_rec = {"error": f"{type(exc).__name__}: {exc}"}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded, Wikipedia-shaped)", "config": desc,
                 "pairs_per_s": pairs_s, "gpu_launches": launches,
-                "kernel_ms": {k: v[0] / max(args.steps, 1) for k, v in kt.items()},
+                "kernel_ms": {k: v[0] / max(args.steps, 1) for k, v in kt.items() if v[1]},
+                "direct_launch_ms_per_step": 1000 * secs_direct / args.steps,
+                "graph": {"captures": plan.get_option("graph_captures")},
+                "autotune": tuned, "tune": tune_rec,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()

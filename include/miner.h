@@ -131,10 +131,21 @@ int mine_align(mine_plan *plan, const mine_params *params, const uint8_t *counts
                mine_out *out, miner_stream_t stream);
 
 /* The whole hot path: overlap counts, similarity, alignment, threshold
- * filter, for every document pair of the plan.  Uses plan-owned scratch; no
- * allocation after plan creation. */
+ * filter, for every document pair of the plan, as one CUDA graph launch
+ * (MINE_OPT_USE_GRAPH).  Uses plan-owned scratch; no allocation after plan
+ * creation.  The first call, and any call whose output buffers or parameters
+ * differ from the previous one, captures the graph (on a plan-owned stream)
+ * before launching it on `stream`. */
 int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
                miner_stream_t stream);
+
+/* Link quality against gold links (gold: one 0/1 byte per cell, per-cell
+ * layout as the counts): counts3[0] = links that are gold, counts3[1] =
+ * links, counts3[2] = gold cells (device, 3 x uint64).  Micro precision =
+ * [0]/[1], recall = [0]/[2]; the tuning evaluation of Section 5.2's
+ * threshold/penalty search uses them. */
+int mine_link_gold_counts(mine_plan *plan, const mine_out *out, const uint8_t *gold, uint64_t *counts3,
+                          miner_stream_t stream);
 
 /* Plan options: the tuning knobs of the planner (defaults in parentheses).
  * Setting a tiling option rebuilds the plan's work lists synchronously; do
@@ -145,6 +156,17 @@ int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
 #define MINE_OPT_WAIT_LIMIT 4     /* spin iterations before a tile wait gives up (2^24) */
 #define MINE_OPT_LINK_RECOUNT 5   /* 1: recount the overlaps of aligned pairs by warp
                                      vote instead of reading the cached counts (0) */
+#define MINE_OPT_USE_GRAPH 6      /* 1: mine_pairs captures its launches once into a
+                                     CUDA graph and replays it (1); the graph is
+                                     re-captured when the output buffers or the
+                                     parameters change, and bypassed while per-kernel
+                                     timing is on */
+#define MINE_OPT_GRAPH_CAPTURES 7 /* read-only: graph captures made so far */
+#define MINE_OPT_FAULT_SKIP_FLAG 8 /* fault injection for tests: the completion flag with
+                                      this index is never published, so the tiles that
+                                      wait on it give up after MINE_OPT_WAIT_LIMIT spins
+                                      and mine_plan_check reports MINE_ETIMEOUT (-1: off) */
+#define MINE_OPT_N_TILE_FLAGS 9   /* read-only: tile flags of the plan (tiled pairs) */
 int mine_plan_set_option(mine_plan *plan, int option, int64_t value);
 /* Current value of an option, or MINE_EINVAL for an unknown option. */
 int64_t mine_plan_get_option(const mine_plan *plan, int option);
@@ -181,9 +203,13 @@ int mine_plan_kernel_times(mine_plan *plan, float *host_ms, int64_t *host_launch
  *   L = mean over all cells of all pairs of -(g log P + (1-g) log(1-P)).
  * ------------------------------------------------------------------------- */
 typedef struct {
-    float gamma; /* smoothing temperature (> 0); -> hard NW as gamma -> 0 */
-    float tau;   /* gate temperature of the acceptance threshold (> 0) */
-    float eps;   /* clamp of P (0 < eps < 0.5) */
+    float gamma;           /* smoothing temperature (> 0); -> hard NW as gamma -> 0 */
+    float tau;             /* gate temperature of the acceptance threshold (> 0) */
+    float eps;             /* clamp of P (0 < eps < 0.5) */
+    const int32_t *pairs;  /* device: the pairs to include (a minibatch), or NULL for all */
+    int64_t n_pairs;       /* number of entries of pairs (ignored when pairs is NULL) */
+    int64_t n_cells;       /* cells of the listed pairs: the loss is their mean
+                              (ignored when pairs is NULL) */
 } softnw_opts;
 
 /* Bytes of the caller-provided workspace of softnw_fwd / softnw_bwd. */
@@ -192,7 +218,8 @@ int64_t softnw_workspace_size(const mine_plan *plan);
 /* Loss L (one float at *loss, device) from cached counts (as mine_count) and
  * gold (one byte per cell, 0 or 1).  Optional outputs (NULL to skip): value
  * (n_pairs floats, soft V(N,M) per pair) and expected (n_cells floats, E).
- * Keeps E in the workspace for softnw_bwd. */
+ * Keeps E in the workspace for softnw_bwd.  With opts->pairs set, only the
+ * listed pairs are swept (E and value of the others are left untouched). */
 int softnw_fwd(mine_plan *plan, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
                const uint8_t *gold, void *ws, float *loss, float *value, float *expected,
                miner_stream_t stream);

@@ -49,7 +49,7 @@ __device__ bool wait_flag(const int32_t *f, int64_t limit) {
 __global__ void __launch_bounds__(32 * kFillWarps)
 fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             const FillItem *__restrict__ items, int64_t n_items, DevParams P,
-            const uint8_t *__restrict__ counts, AlignScratch S, int64_t wait_limit) {
+            const uint8_t *__restrict__ counts, AlignScratch S, int64_t wait_limit, int64_t skip_flag) {
     __shared__ SimCol colv_all[kFillWarps][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     FillCtx C;
@@ -94,7 +94,8 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
                 if (C.c1 < C.M && C.rv) __stcg(S.vcol + g.vcol_off + C.r, b);
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) st_release(S.flags + g.flag_off + (int64_t)s * g.nchunk + w.cj, 1);
+                const int64_t fi = g.flag_off + (int64_t)s * g.nchunk + w.cj;
+                if (lane == 0 && fi != skip_flag) st_release(S.flags + fi, 1);
             } else {
                 __syncwarp();
             }
@@ -184,25 +185,46 @@ __device__ __forceinline__ void ballot_counts(const int32_t *__restrict__ stok, 
     mt = mtc;
 }
 
-// Similarity of every diagonal cell of every path, one warp per cell, by the
-// same helper the fill used.  The counts come from the cached per-cell counts
-// when given, else they are recounted by warp vote from the tokens.
+// Similarity of every diagonal cell of every path, by the same helper the fill
+// used.  From the cached per-cell counts one thread handles a cell; without
+// them (link recount) one warp per cell recounts the overlaps by warp vote.
+__device__ __forceinline__ int64_t owner_pair(const int64_t *__restrict__ diag_off, int64_t n_pairs, int64_t f) {
+    int64_t lo = 0, hi = n_pairs - 1;  // last k with diag_off[k] <= f
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (diag_off[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(32 * kTailWarps)
+link_score_cached_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, int64_t n_pairs,
+                         DevParams P, AlignScratch S, const uint8_t *__restrict__ counts) {
+    const int64_t total = S.diag_off[n_pairs];
+    const SimConst K = sim_const(P);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += stride) {
+        const int64_t k = owner_pair(S.diag_off, n_pairs, f);
+        const PairGeom g = geom[k];
+        const int64_t at = g.link_off + min(g.n, g.m) - S.n_diag[k] + (f - S.diag_off[k]);
+        const int rr = S.diag_i[at], cc = S.diag_j[at];
+        const int64_t sb = src.doc[k] + rr, tbs = tgt.doc[k] + cc;
+        const int ls = (int)(src.sent[sb + 1] - src.sent[sb]), lt = (int)(tgt.sent[tbs + 1] - tgt.sent[tbs]);
+        const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)rr * g.m + cc];
+        S.diag_s[at] = similarity(q.x, q.y, sim_row(ls, P), sim_col(lt, P), K);
+    }
+}
+
 __global__ void __launch_bounds__(32 * kTailWarps)
 link_score_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
-                  int64_t n_pairs, DevParams P, AlignScratch S, const uint8_t *__restrict__ counts) {
+                  int64_t n_pairs, DevParams P, AlignScratch S) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = S.diag_off[n_pairs];
     const SimConst K = sim_const(P);
     for (int64_t f = warp0; f < total; f += nwarps) {
-        // pair owning flat diagonal f: last k with diag_off[k] <= f
-        int64_t lo = 0, hi = n_pairs - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (S.diag_off[mid] <= f) lo = mid; else hi = mid - 1;
-        }
-        const int64_t k = lo;
+        const int64_t k = owner_pair(S.diag_off, n_pairs, f);
         const PairGeom g = geom[k];
         const int nd = S.n_diag[k];
         const int64_t at = g.link_off + min(g.n, g.m) - nd + (f - S.diag_off[k]);
@@ -211,13 +233,7 @@ link_score_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__
         const int64_t s0 = src.sent[sb], s1 = src.sent[sb + 1];
         const int64_t t0 = tgt.sent[tbs], t1 = tgt.sent[tbs + 1];
         int ms, mt;
-        if (counts) {
-            const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)rr * g.m + cc];
-            ms = q.x;
-            mt = q.y;
-        } else {
-            ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
-        }
+        ballot_counts(src.tok + s0, (int)(s1 - s0), tgt.tok + t0, (int)(t1 - t0), dict, lane, ms, mt);
         if (lane == 0)
             S.diag_s[at] = similarity(ms, mt, sim_row((int)(s1 - s0), P), sim_col((int)(t1 - t0), P), K);
     }
@@ -263,6 +279,39 @@ copy_links_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, DevParams 
     }
 }
 
+// Link quality against gold links (one 0/1 byte per cell): per pair, the
+// number of links that are gold; plus the number of links and of gold cells.
+// One warp per pair, integer sums (exact).
+__global__ void __launch_bounds__(32 * kTailWarps)
+link_gold_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, const int64_t *__restrict__ link_off,
+                 const int32_t *__restrict__ li, const int32_t *__restrict__ lj, const uint8_t *__restrict__ gold,
+                 unsigned long long *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long tp = 0, ng = 0, nl = 0;
+    for (int64_t k = warp0; k < n_pairs; k += nwarps) {
+        const PairGeom g = geom[k];
+        for (int64_t x = link_off[k] + lane; x < link_off[k + 1]; x += 32) {
+            tp += gold[g.cell_off + (int64_t)li[x] * g.m + lj[x]];
+            ++nl;
+        }
+        const int64_t cells = (int64_t)g.n * g.m;
+        for (int64_t c = lane; c < cells; c += 32) ng += gold[g.cell_off + c];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        tp += __shfl_xor_sync(kFull, tp, off);
+        ng += __shfl_xor_sync(kFull, ng, off);
+        nl += __shfl_xor_sync(kFull, nl, off);
+    }
+    if (lane == 0) {
+        atomicAdd(out + 0, tp);
+        atomicAdd(out + 1, nl);
+        atomicAdd(out + 2, ng);
+    }
+}
+
 // Unfused similarity of every cell from counts (one block per pair).
 __global__ void __launch_bounds__(256)
 score_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, DevParams P,
@@ -298,7 +347,7 @@ int tail_grid(int64_t warps_wanted, int n_sms) {
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit,
+                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit, int64_t skip_flag,
                         int n_sms, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     int per_sm = 0;
@@ -310,7 +359,7 @@ cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGe
     e = cudaMemsetAsync(S.queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     fill_kernel<<<(unsigned)blocks, 32 * kFillWarps, 0, st>>>(src, tgt, geom, items, n_items, P, counts, S,
-                                                               wait_limit);
+                                                               wait_limit, skip_flag);
     return cudaGetLastError();
 }
 
@@ -330,7 +379,10 @@ cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const 
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,
                               const AlignScratch &S, const uint8_t *counts, int n_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S, counts);
+    if (counts)
+        link_score_cached_kernel<<<n_sms * 8, 32 * kTailWarps, 0, st>>>(src, tgt, geom, n_pairs, P, S, counts);
+    else
+        link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S);
     return cudaGetLastError();
 }
 
@@ -347,6 +399,16 @@ cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const DevPa
     if (n_pairs == 0) return cudaSuccess;
     copy_links_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, P, S, link_off,
                                                                              out_i, out_j, out_s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_link_gold(const PairGeom *geom, int64_t n_pairs, const int64_t *link_off, const int32_t *li,
+                             const int32_t *lj, const uint8_t *gold, unsigned long long *out, int n_sms,
+                             cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess || n_pairs == 0) return e;
+    link_gold_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, link_off, li, lj, gold,
+                                                                            out);
     return cudaGetLastError();
 }
 

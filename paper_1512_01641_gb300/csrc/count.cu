@@ -152,79 +152,148 @@ count_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restr
 }
 
 // ---------------------------------------------------------------------------
-// Strip kernel: one warp owns 32 source rows (a strip) and sweeps all column
-// blocks of the pair.  The row table is built once per strip:
-//   RT[t] = 32-bit mask of the strip's rows i with t in T_i (T_i = dictionary
-//           translations of source sentence i),
-// and every row keeps, in shared memory, the list of RT slots of its
-// translations in position order (last translation of a position flagged).
-// Per 32-column block:
-//   column pass: lane j looks up each token of target sentence j in RT; a hit
-//     adds RT[t] into the mt counters (mt for 32 rows) and sets bit j of the
-//     slot's column mask;
-//   row pass: lane i walks its slot list; the column masks of a position's
-//     translations OR into h (bit j: the position is matched in column j), and
-//     h is added into the ms counters (ms for 32 columns).
-// No dictionary or hash work is left in the row pass, and the table build is
-// paid once per strip instead of once per block.
-template <int LOG_SLOTS, int LCAP>
+// Strip kernel: one warp owns the rows of a 32-row strip (or a row group of
+// it) and sweeps all 32-column blocks of the pair.  Once per strip a
+// shared-memory hash table is built over the dictionary translations of the
+// strip's source positions:  RT[t] = mask of the rows i with t in T_i.  Every
+// source position keeps the table slots of its translations.  Per block:
+//   column pass: every target token of the block looks itself up in RT; a hit
+//     records RT[t] (which rows' translation sets contain it) and sets the
+//     token's column bit in the slot's column mask;
+//   mt: lane j adds the recorded row masks of column j's tokens into
+//     bit-sliced counters (mt of 32 rows at once);
+//   row pass: every source position ORs the column masks of its translations
+//     (bit j: the position has a translation in target sentence j);
+//   ms: lane i adds the masks of row i's positions into bit-sliced counters
+//     (ms of 32 columns at once).
+// The table build, the column pass and the row pass are spread over the 32
+// lanes token by token (position by position), so no lane waits for the
+// longest sentence; only the two accumulations run one row (column) per lane.
+// Counters are carry-save (four words per step), bytes are expanded by
+// multiply-spread and transposed through shared memory for coalesced writes.
+constexpr int kEntCap = 1440;  // translation entries per strip item (planner limit 0.7 * 2^11)
+constexpr int kPosCap = 992;   // source positions per strip item (32 rows x 31 tokens)
+constexpr int kTokCap = 992;   // target tokens per column block (32 sentences x 31 tokens)
+
+template <int LOG_SLOTS>
 struct StripSmem {
     static constexpr int S = 1 << LOG_SLOTS;
     int32_t key[S];
     uint32_t rowmask[S];
-    uint32_t colmask[S];  // also holds the two 32 x 36 byte transpose tiles after the row pass
-    uint16_t list[32][LCAP];
+    uint32_t colmask[S];
+    uint32_t gh[kTokCap];  // row masks of the block's tokens, then the positions' column masks, then byte tiles
+    uint16_t ent[kEntCap];
+    uint16_t pos_off[kPosCap + 2];
+    uint16_t tslot[kTokCap];
+    uint8_t colid[kTokCap];
+    uint8_t rowid[kPosCap];
 };
-static_assert(sizeof(uint32_t) * 1024 >= 2 * 32 * kPad, "transpose tiles alias the column masks");
+static_assert(kTokCap >= kPosCap && kTokCap * 4 >= 2 * 32 * kPad, "shared buffer sizes");
 
-constexpr uint16_t kEndPos = 0x8000u;
-// Per-row slot-list capacity: an odd number of 32-bit words per row keeps the
-// lanes' list reads on distinct banks.
-static_assert((kStripListCap / 2) % 2 == 1, "row lists need an odd word stride");
+constexpr uint16_t kNoSlot = 0xFFFFu;
 
-template <int LOG_SLOTS, int K, int LCAP>
+// Carry-save accumulation of 0/1 words into bit-sliced counters, four at a time.
+template <int K>
+struct Acc4 {
+    BitCounter<K> c;
+    uint32_t b0 = 0, b1 = 0, b2 = 0;
+    int n = 0;
+    __device__ __forceinline__ void add(uint32_t x) {
+        if (n == 3) {
+            c.add4(b0, b1, b2, x);
+            n = 0;
+        } else {
+            b2 = b1;
+            b1 = b0;
+            b0 = x;
+            ++n;
+        }
+    }
+    __device__ __forceinline__ void finish() {
+        if (n > 0) c.add4(b0, n > 1 ? b1 : 0u, n > 2 ? b2 : 0u, 0u);
+        n = 0;
+    }
+};
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, off);
+        if (lane >= off) x += y;
+    }
+    total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+template <int LOG_SLOTS, int K>
 __global__ void __launch_bounds__(32 * kCountWarps)
 count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
                    const CountStripItem *__restrict__ items, int64_t n_items, uint8_t *__restrict__ counts,
                    uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using Smem = StripSmem<LOG_SLOTS, LCAP>;
+    using Smem = StripSmem<LOG_SLOTS>;
     constexpr int S = Smem::S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem &sm = reinterpret_cast<Smem *>(smem_raw)[warp];
-    uint8_t(*ms_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(sm.colmask);
-    uint8_t(*mt_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(reinterpret_cast<uint8_t *>(sm.colmask) + 32 * kPad);
+    uint8_t(*ms_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(sm.gh);
+    uint8_t(*mt_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(reinterpret_cast<uint8_t *>(sm.gh) + 32 * kPad);
 
     for (int64_t it = (int64_t)blockIdx.x * kCountWarps + warp; it < n_items;
          it += (int64_t)gridDim.x * kCountWarps) {
         const CountStripItem item = items[it];
         const PairGeom g = geom[item.pair];
         const int r0 = item.strip * 32;
-        const bool rv = lane >= item.r_lo && lane < item.r_hi && r0 + lane < g.n;
-        const int nr = min(item.r_hi, g.n - r0);  // rows [r_lo, nr) of the strip are written
+        const int rhi = min(item.r_hi, g.n - r0);
+        const bool rv = lane >= item.r_lo && lane < rhi;
+        // source positions of the item's rows, flattened (rows are consecutive
+        // sentences, so their tokens are contiguous)
+        const int64_t ssent0 = src.doc[item.pair] + r0;
+        const int my_len = rv ? (int)(src.sent[ssent0 + lane + 1] - src.sent[ssent0 + lane]) : 0;
+        int n_pos;
+        const int prow = warp_excl_scan(my_len, lane, n_pos);
+        const int64_t ptok0 = src.sent[ssent0 + item.r_lo];
         for (int x = lane; x < S; x += 32) {
             sm.key[x] = kEmpty;
             sm.rowmask[x] = 0u;
+            sm.colmask[x] = 0u;
+        }
+        for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
+        // translation entry offsets of the positions
+        int carry = 0;
+        for (int base = 0; base < n_pos; base += 32) {
+            const int p = base + lane;
+            int f = 0;
+            if (p < n_pos) {
+                const int32_t v = src.tok[ptok0 + p];
+                f = dict.off[v + 1] - dict.off[v];
+            }
+            int tot;
+            const int ex = warp_excl_scan(f, lane, tot);
+            if (p < n_pos) sm.pos_off[p] = (uint16_t)min(carry + ex, 0xFFFF);
+            carry += tot;
+        }
+        if (lane == 0) sm.pos_off[n_pos] = (uint16_t)min(carry, 0xFFFF);
+        if (carry > kEntCap) {
+            if (lane == 0) atomicOr(status, kStTableFull);
+            continue;
         }
         __syncwarp();
-
-        // row table + slot lists
-        int n_list = 0;
-        if (rv) {
-            const int64_t ssent = src.doc[item.pair] + r0 + lane;
-            const int64_t p0 = src.sent[ssent], p1 = src.sent[ssent + 1];
-            for (int64_t p = p0; p < p1; ++p) {
-                const int32_t v = src.tok[p];
-                const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
-                for (int32_t e = e0; e < e1; ++e) {
-                    const int h = table_insert<LOG_SLOTS>(sm.key, dict.tgt[e]);
-                    if (h < 0 || n_list >= LCAP) {
-                        atomicOr(status, kStTableFull);
-                        break;
-                    }
-                    atomicOr(&sm.rowmask[h], 1u << lane);
-                    sm.list[lane][n_list++] = (uint16_t)h | (e + 1 == e1 ? kEndPos : 0u);
+        // row table
+        for (int p = lane; p < n_pos; p += 32) {
+            const int32_t v = src.tok[ptok0 + p];
+            const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
+            const uint32_t rbit = 1u << sm.rowid[p];
+            const int o = sm.pos_off[p];
+            for (int32_t e = e0; e < e1; ++e) {
+                const int h = table_insert<LOG_SLOTS>(sm.key, dict.tgt[e]);
+                if (h < 0) {
+                    atomicOr(status, kStTableFull);
+                    sm.ent[o + (e - e0)] = 0;
+                    continue;
                 }
+                atomicOr(&sm.rowmask[h], rbit);
+                sm.ent[o + (e - e0)] = (uint16_t)h;
             }
         }
         __syncwarp();
@@ -235,69 +304,58 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
         for (int jb = 0; jb < nblk; ++jb) {
             const int c0 = jb * 32;
             const int nc = min(32, g.m - c0);
-            for (int x = lane; x < S; x += 32) sm.colmask[x] = 0u;
+            const int64_t ts = tdoc + c0;
+            const int my_lt = lane < nc ? (int)(tgt.sent[ts + lane + 1] - tgt.sent[ts + lane]) : 0;
+            int n_tok;
+            const int tpre = warp_excl_scan(my_lt, lane, n_tok);
+            const int64_t ttok0 = tgt.sent[ts];
+            for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
             __syncwarp();
-            // column pass: mt for 32 rows of column c0 + lane
-            BitCounter<K> mt;
-            mt.clear();
-            if (lane < nc) {
-                const int64_t q0 = tgt.sent[tdoc + c0 + lane], q1 = tgt.sent[tdoc + c0 + lane + 1];
-                uint32_t b0 = 0, b1 = 0, b2 = 0;
-                int nbuf = 0;
-                for (int64_t q = q0; q < q1; ++q) {
-                    const int slot = table_find<LOG_SLOTS>(sm.key, tgt.tok[q]);
-                    if (slot < 0) continue;
-                    const uint32_t rm = sm.rowmask[slot];
-                    atomicOr(&sm.colmask[slot], 1u << lane);
-                    if (nbuf == 3) {
-                        mt.add4(b0, b1, b2, rm);
-                        nbuf = 0;
-                    } else {
-                        b2 = b1;
-                        b1 = b0;
-                        b0 = rm;
-                        ++nbuf;
-                    }
+            // column pass
+            for (int x = lane; x < n_tok; x += 32) {
+                const int slot = table_find<LOG_SLOTS>(sm.key, tgt.tok[ttok0 + x]);
+                uint32_t rm = 0u;
+                if (slot >= 0) {
+                    rm = sm.rowmask[slot];
+                    atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
                 }
-                if (nbuf > 0) mt.add4(b0, nbuf > 1 ? b1 : 0u, nbuf > 2 ? b2 : 0u, 0u);
+                sm.tslot[x] = slot >= 0 ? (uint16_t)slot : kNoSlot;
+                sm.gh[x] = rm;
             }
             __syncwarp();
-            // row pass: ms for 32 columns of row r0 + lane
-            BitCounter<K> ms;
-            ms.clear();
-            if (rv) {
-                uint32_t b0 = 0, b1 = 0, b2 = 0, h = 0;
-                int nbuf = 0;
-                for (int x = 0; x < n_list; ++x) {
-                    const uint16_t ent = sm.list[lane][x];
-                    h |= sm.colmask[ent & 0x7FFF];
-                    if (ent & kEndPos) {
-                        if (nbuf == 3) {
-                            ms.add4(b0, b1, b2, h);
-                            nbuf = 0;
-                        } else {
-                            b2 = b1;
-                            b1 = b0;
-                            b0 = h;
-                            ++nbuf;
-                        }
-                        h = 0;
-                    }
-                }
-                if (nbuf > 0) ms.add4(b0, nbuf > 1 ? b1 : 0u, nbuf > 2 ? b2 : 0u, 0u);
+            Acc4<K> mt;
+            mt.c.clear();
+            for (int t = 0; t < my_lt; ++t) mt.add(sm.gh[tpre + t]);
+            mt.finish();
+            __syncwarp();
+            // row pass
+            for (int p = lane; p < n_pos; p += 32) {
+                uint32_t h = 0u;
+                const int e1 = sm.pos_off[p + 1];
+                for (int e = sm.pos_off[p]; e < e1; ++e) h |= sm.colmask[sm.ent[e]];
+                sm.gh[p] = h;
             }
             __syncwarp();
-            // expand, transpose (tiles alias the column masks), write
+            Acc4<K> ms;
+            ms.c.clear();
+            for (int t = 0; t < my_len; ++t) ms.add(sm.gh[prow + t]);
+            ms.finish();
+            __syncwarp();
+            for (int x = lane; x < n_tok; x += 32) {
+                const uint16_t sl = sm.tslot[x];
+                if (sl != kNoSlot) sm.colmask[sl] = 0u;
+            }
+            // expand, transpose, write
             uint32_t w[8];
-            ms.to_bytes(w);
+            ms.c.to_bytes(w);
 #pragma unroll
             for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&ms_t[lane][4 * m]) = w[m];
-            mt.to_bytes(w);
+            mt.c.to_bytes(w);
 #pragma unroll
             for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&mt_t[lane][4 * m]) = w[m];
             __syncwarp();
             if (lane < nc) {
-                for (int i = item.r_lo; i < nr; ++i) {
+                for (int i = item.r_lo; i < rhi; ++i) {
                     const uchar2 v = make_uchar2(ms_t[i][lane], mt_t[lane][i]);
                     reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[lane] = v;
                 }
@@ -311,9 +369,8 @@ template <int LOG_SLOTS, int K>
 cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                            const PairGeom *geom, const CountStripItem *items, int64_t n_items,
                            uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st) {
-    constexpr int LCAP = kStripListCap;
-    const size_t smem = sizeof(StripSmem<LOG_SLOTS, LCAP>) * kCountWarps;
-    auto kern = count_strip_kernel<LOG_SLOTS, K, LCAP>;
+    const size_t smem = sizeof(StripSmem<LOG_SLOTS>) * kCountWarps;
+    auto kern = count_strip_kernel<LOG_SLOTS, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -345,6 +402,7 @@ cudaError_t launch_count_t(const DevCorpus &src, const DevCorpus &tgt, const Dev
     kern<<<grid, 32 * kCountWarps, smem, st>>>(src, tgt, dict, geom, items, n_items, counts, status);
     return cudaGetLastError();
 }
+
 
 // Translation totals of every 32-row strip (sizes the row tables) and the
 // largest per-sentence total (sizes the slot lists).

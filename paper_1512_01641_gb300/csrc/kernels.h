@@ -85,7 +85,7 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
                                 int log_slots, int planes, uint8_t *counts, uint32_t *status, int n_sms,
                                 cudaStream_t st);
 
-constexpr int kStripListCap = 98;   // slot-list entries per row of the strip count kernel
+constexpr int kStripEntCap = 1440;  // translation entries per item of the strip count kernel
 constexpr int kStripLogSlots = 11;  // row-table slots of the strip count kernel (2^11)
 
 cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict, const PairGeom *geom,
@@ -98,7 +98,7 @@ cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairG
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit,
+                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit, int64_t skip_flag,
                         int n_sms, cudaStream_t st);
 
 cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
@@ -116,6 +116,10 @@ cudaError_t launch_pair_sum(const PairGeom *geom, int64_t n_pairs, const DevPara
 cudaError_t launch_copy_links(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
                               const AlignScratch &S, const int64_t *link_off, int32_t *out_i,
                               int32_t *out_j, float *out_s, int n_sms, cudaStream_t st);
+
+cudaError_t launch_link_gold(const PairGeom *geom, int64_t n_pairs, const int64_t *link_off, const int32_t *li,
+                             const int32_t *lj, const uint8_t *gold, unsigned long long *out, int n_sms,
+                             cudaStream_t st);
 
 // Soft alignment: scalar arguments and the caller's workspace, carved up.
 struct SoftArgs {

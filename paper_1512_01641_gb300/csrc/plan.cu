@@ -109,6 +109,8 @@ struct PlanKnobs {
     int tile_cols = 128;               // column chunk width of a tile (multiple of 32)
     int64_t wait_limit = 1 << 24;      // bounded spin iterations of a tile wait (~200 ns each)
     int link_recount = 0;              // 1: recount link overlaps by warp vote
+    int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
+    int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
 };
 
 struct mine_plan {
@@ -141,6 +143,13 @@ struct mine_plan {
     std::vector<Pending> pending;
     double total_ms[kKinds] = {};
     int64_t launches[kKinds] = {};
+    // whole-batch CUDA graph of mine_pairs, keyed by the output buffers and
+    // the parameters baked into its kernel arguments
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    mine_out graph_out{};
+    mine_params graph_params{};
+    int64_t graph_captures = 0;
 };
 
 // Launch f() on stream st; with timing enabled, bracket it by two events.
@@ -184,9 +193,16 @@ static void drain_pending(mine_plan *p) {
         }                            \
     } while (0)
 
+static void drop_graph(mine_plan *p) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+}
+
 static void plan_free(mine_plan *p) {
     if (!p) return;
     drain_pending(p);
+    drop_graph(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     void *bufs[] = {p->geom, p->pair_order, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
                     p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
                     p->S.diag_off, p->S.n_links, p->stats};
@@ -431,11 +447,11 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         cudaFree(d_tr);
         PLAN_CK(e);
         const int maxlen0 = std::max(stats[0], stats[1]);
-        p->use_strips = maxlen0 <= 31 && stats[3] <= kStripListCap;
+        p->use_strips = maxlen0 <= 31 && stats[3] <= kStripEntCap;
         if (p->use_strips) {
             // a strip whose translations would fill the row table past ~70% is
             // split into 2, 4, ... row groups
-            const int64_t limit = (int64_t)(0.7 * (1 << kStripLogSlots));
+            const int64_t limit = std::min<int64_t>((int64_t)(0.7 * (1 << kStripLogSlots)), kStripEntCap);
             std::vector<int32_t> order(n);
             std::iota(order.begin(), order.end(), 0);
             std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
@@ -524,7 +540,7 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
     if (p->n_flags > 0) MINE_CK(cudaMemsetAsync(S.flags, 0, p->n_flags * sizeof(int32_t), st));
     MINE_CK(timed(p, kKFill, st, [&] {
         return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, S,
-                           p->knobs.wait_limit, p->n_sms, st);
+                           p->knobs.wait_limit, p->knobs.skip_flag, p->n_sms, st);
     }));
     MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, n, S, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_diag, n, S.diag_off, st); }));
@@ -540,11 +556,54 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
     return MINE_OK;
 }
 
-int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_stream_t stream) {
-    if (!p) return MINE_EINVAL;
-    int r = mine_count(p, p->counts, stream);
+static int enqueue_pairs(mine_plan *p, const mine_params *params, mine_out *out, cudaStream_t st) {
+    int r = mine_count(p, p->counts, (miner_stream_t)st);
     if (r != MINE_OK) return r;
-    return mine_align(p, params, p->counts, out, stream);
+    return mine_align(p, params, p->counts, out, (miner_stream_t)st);
+}
+
+int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_stream_t stream) {
+    if (!p || !params || !out) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->timing || !p->knobs.use_graph) return enqueue_pairs(p, params, out, st);
+    // capture once on a plan-owned stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured), replay on the caller's
+    const bool same = p->graph && std::memcmp(&p->graph_out, out, sizeof *out) == 0 &&
+                      std::memcmp(&p->graph_params, params, sizeof *params) == 0;
+    if (!same) {
+        if (!p->cap_stream) MINE_CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+        MINE_CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int r = enqueue_pairs(p, params, out, p->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (r != MINE_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) g_last_cuda = (int)e;
+            return r != MINE_OK ? r : MINE_ECUDA;
+        }
+        if (p->graph) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(p->graph, g, &info) != cudaSuccess) {
+                (void)cudaGetLastError();
+                drop_graph(p);
+            }
+        }
+        if (!p->graph) {
+            const cudaError_t ei = cudaGraphInstantiate(&p->graph, g, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(g);
+                p->graph = nullptr;
+                g_last_cuda = (int)ei;
+                return MINE_ECUDA;
+            }
+        }
+        cudaGraphDestroy(g);
+        p->graph_out = *out;
+        p->graph_params = *params;
+        ++p->graph_captures;
+    }
+    MINE_CK(cudaGraphLaunch(p->graph, st));
+    return MINE_OK;
 }
 
 // ------------------------------------------------------------- soft alignment
@@ -595,12 +654,21 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     return W;
 }
 
-static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A) {
+static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, const int32_t *&order, int64_t &n) {
     if (!o || !(o->gamma > 0.0f) || !(o->tau > 0.0f) || !(o->eps > 0.0f) || !(o->eps < 0.5f)) return false;
     A.gamma = o->gamma;
     A.tau = o->tau;
     A.eps = o->eps;
-    A.inv_cells = p->n_cells > 0 ? (float)(1.0 / (double)p->n_cells) : 0.0f;
+    int64_t cells = p->n_cells;
+    order = p->pair_order;
+    n = p->n_pairs;
+    if (o->pairs) {
+        if (o->n_pairs < 0 || o->n_pairs > p->n_pairs || o->n_cells < 0 || o->n_cells > p->n_cells) return false;
+        order = o->pairs;
+        n = o->n_pairs;
+        cells = o->n_cells;
+    }
+    A.inv_cells = cells > 0 ? (float)(1.0 / (double)cells) : 0.0f;
     return true;
 }
 
@@ -609,15 +677,17 @@ int64_t softnw_workspace_size(const mine_plan *p) { return p ? soft_layout(p).to
 int softnw_fwd(mine_plan *p, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
                const uint8_t *gold, void *ws, float *loss, float *value, float *expected, miner_stream_t stream) {
     SoftArgs A;
-    if (!p || !params || !ws || !loss || !soft_args(p, opts, A)) return MINE_EINVAL;
+    const int32_t *order = nullptr;
+    int64_t n = 0;
+    if (!p || !params || !ws || !loss || !soft_args(p, opts, A, order, n)) return MINE_EINVAL;
     if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
     if (p->max_m > (1 << 20)) return MINE_ENOTSUP;
     cudaStream_t st = (cudaStream_t)stream;
     const SoftScratch W = soft_scratch(p, ws);
     const DevParams P = to_dev(*params);
     MINE_CK(timed(p, kKSoftFwd, st, [&] {
-        return launch_soft_forward(p->src, p->tgt, p->geom, p->pair_order, p->n_pairs, P, A, counts, gold, W, loss,
-                                   value, p->n_sms, st);
+        return launch_soft_forward(p->src, p->tgt, p->geom, order, n, P, A, counts, gold, W, loss, value, p->n_sms,
+                                   st);
     }));
     if (expected && p->n_cells > 0)
         MINE_CK(cudaMemcpyAsync(expected, W.E, p->n_cells * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -627,15 +697,25 @@ int softnw_fwd(mine_plan *p, const mine_params *params, const softnw_opts *opts,
 int softnw_bwd(mine_plan *p, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
                const uint8_t *gold, void *ws, float dloss, float *grad, float *hvp, miner_stream_t stream) {
     SoftArgs A;
-    if (!p || !params || !ws || !grad || !soft_args(p, opts, A)) return MINE_EINVAL;
+    const int32_t *order = nullptr;
+    int64_t n = 0;
+    if (!p || !params || !ws || !grad || !soft_args(p, opts, A, order, n)) return MINE_EINVAL;
     if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const SoftScratch W = soft_scratch(p, ws);
     const DevParams P = to_dev(*params);
     MINE_CK(timed(p, kKSoftBwd, st, [&] {
-        return launch_soft_backward(p->src, p->tgt, p->geom, p->pair_order, p->n_pairs, P, A, counts, gold, W, dloss,
-                                    grad, hvp, p->n_sms, st);
+        return launch_soft_backward(p->src, p->tgt, p->geom, order, n, P, A, counts, gold, W, dloss, grad, hvp,
+                                    p->n_sms, st);
     }));
+    return MINE_OK;
+}
+
+int mine_link_gold_counts(mine_plan *p, const mine_out *out, const uint8_t *gold, uint64_t *counts3,
+                          miner_stream_t stream) {
+    if (!p || !out || !out->link_off || !counts3 || (p->n_cells > 0 && !gold)) return MINE_EINVAL;
+    MINE_CK(launch_link_gold(p->geom, p->n_pairs, out->link_off, out->link_i, out->link_j, gold,
+                             reinterpret_cast<unsigned long long *>(counts3), p->n_sms, (cudaStream_t)stream));
     return MINE_OK;
 }
 
@@ -670,13 +750,23 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
         case MINE_OPT_WAIT_LIMIT:
             if (value < 1) return MINE_EINVAL;
             p->knobs.wait_limit = value;
+            drop_graph(p);
             return MINE_OK;
         case MINE_OPT_LINK_RECOUNT:
             p->knobs.link_recount = value != 0;
+            drop_graph(p);
+            return MINE_OK;
+        case MINE_OPT_USE_GRAPH:
+            p->knobs.use_graph = value != 0;
+            return MINE_OK;
+        case MINE_OPT_FAULT_SKIP_FLAG:
+            p->knobs.skip_flag = value < 0 ? -1 : value;
+            drop_graph(p);
             return MINE_OK;
         default:
             return MINE_EINVAL;
     }
+    drop_graph(p);
     // tiling changed: rebuild the work lists and the tile flags (synchronous)
     std::vector<int64_t> sd(p->n_pairs + 1, 0), td(p->n_pairs + 1, 0);
     for (int64_t x = 0; x < p->n_pairs; ++x) {
@@ -688,11 +778,11 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
     std::vector<FillItem> fitems;
     int64_t tbw, hrow, vcol;
     build_geometry(p, sd, td, citems, fitems, tbw, hrow, vcol);
+    MINE_CK(cudaDeviceSynchronize());
     cudaFree(p->fill_items);
     cudaFree(p->S.flags);
     p->fill_items = nullptr;
     p->S.flags = nullptr;
-    MINE_CK(cudaDeviceSynchronize());
     MINE_CK(dalloc(&p->fill_items, fitems.size()));
     MINE_CK(dalloc(&p->S.flags, p->n_flags));
     MINE_CK(cudaMemcpy(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice));
@@ -708,6 +798,10 @@ int64_t mine_plan_get_option(const mine_plan *p, int option) {
         case MINE_OPT_TILE_MIN_ROWS: return p->knobs.tile_min_rows;
         case MINE_OPT_WAIT_LIMIT: return p->knobs.wait_limit;
         case MINE_OPT_LINK_RECOUNT: return p->knobs.link_recount;
+        case MINE_OPT_USE_GRAPH: return p->knobs.use_graph;
+        case MINE_OPT_GRAPH_CAPTURES: return p->graph_captures;
+        case MINE_OPT_FAULT_SKIP_FLAG: return p->knobs.skip_flag;
+        case MINE_OPT_N_TILE_FLAGS: return p->n_flags;
         default: return MINE_EINVAL;
     }
 }

@@ -167,7 +167,8 @@ __device__ __forceinline__ void soft_fwd_strip(const SoftCtx &C, int s, const fl
     __syncwarp();
 }
 
-// Per-pair partial results: [loss sum, V, dL/dw0..w3, dL/db, dL/dgap, dL/dthr]
+// Per-pair partial results, at the pair's position in the work order:
+// [loss sum, V, dL/dw0..w3, dL/db, dL/dgap, dL/dthr]
 constexpr int kSoftSlots = 9;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -274,7 +275,7 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
         vsum = warp_sum(vsum);
         loss = warp_sum(loss);
         if (lane == 0) {
-            double *o = W.partial + (int64_t)k * kSoftSlots;
+            double *o = W.partial + it * kSoftSlots;
             o[0] = loss;
             o[1] = (C.N > 0 && C.M > 0) ? vsum - (double)P.gap * (double)C.N : -(double)P.gap * (double)(C.N + C.M);
         }
@@ -384,7 +385,7 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
 #pragma unroll
         for (int q7 = 0; q7 < 7; ++q7) gr[q7] = warp_sum(gr[q7]);
         if (lane == 0) {
-            double *o = W.partial + (int64_t)k * kSoftSlots;
+            double *o = W.partial + it * kSoftSlots;
 #pragma unroll
             for (int q7 = 0; q7 < 7; ++q7) o[2 + q7] = gr[q7];
         }
@@ -410,10 +411,11 @@ soft_reduce_kernel(const double *__restrict__ partial, int64_t n_pairs, int firs
     }
 }
 
-__global__ void copy_values_kernel(const double *__restrict__ partial, int64_t n_pairs, float *__restrict__ value) {
+__global__ void copy_values_kernel(const double *__restrict__ partial, const int32_t *__restrict__ order,
+                                   int64_t n_pairs, float *__restrict__ value) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride)
-        value[k] = (float)partial[k * kSoftSlots + 1];
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_pairs; x += stride)
+        value[order[x]] = (float)partial[x * kSoftSlots + 1];
 }
 
 int soft_grid(int n_sms) { return n_sms * 8; }
@@ -434,7 +436,8 @@ cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, cons
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, n_pairs, 0, 1, A.inv_cells, loss);
-    if (value && n_pairs > 0) copy_values_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(W.partial, n_pairs, value);
+    if (value && n_pairs > 0)
+        copy_values_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(W.partial, order, n_pairs, value);
     return cudaGetLastError();
 }
 

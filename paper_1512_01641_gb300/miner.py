@@ -16,7 +16,8 @@ import numpy as np
 from . import build as _build
 
 MINE_OK, MINE_EINVAL, MINE_ENOMEM, MINE_ECUDA, MINE_ETIMEOUT, MINE_ENOTSUP = 0, -1, -2, -3, -4, -5
-OPTIONS = {"tile_cols": 1, "tile_min_cells": 2, "tile_min_rows": 3, "wait_limit": 4, "link_recount": 5}
+OPTIONS = {"tile_cols": 1, "tile_min_cells": 2, "tile_min_rows": 3, "wait_limit": 4, "link_recount": 5,
+           "use_graph": 6, "graph_captures": 7, "fault_skip_flag": 8, "n_tile_flags": 9}
 
 
 class MinerError(RuntimeError):
@@ -45,7 +46,8 @@ class _Params(C.Structure):
 
 
 class _SoftOpts(C.Structure):
-    _fields_ = [("gamma", C.c_float), ("tau", C.c_float), ("eps", C.c_float)]
+    _fields_ = [("gamma", C.c_float), ("tau", C.c_float), ("eps", C.c_float), ("pairs", C.c_void_p),
+                ("n_pairs", C.c_int64), ("n_cells", C.c_int64)]
 
 
 class _Out(C.Structure):
@@ -67,6 +69,7 @@ _SIGS = {
     "mine_align": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.POINTER(_Out), C.c_void_p]),
     "mine_pairs": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_Out), C.c_void_p]),
     "mine_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mine_link_gold_counts": (C.c_int, [C.c_void_p, C.POINTER(_Out), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mine_plan_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "mine_plan_get_option": (C.c_int64, [C.c_void_p, C.c_int]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -284,6 +287,15 @@ class Plan:
         _check(lib().mine_align(self._h, C.byref(p), _ptr(counts), C.byref(s), _stream(stream)), "mine_align")
         return out
 
+    def link_gold_counts(self, out, gold, stream=None):
+        """(links that are gold, links, gold cells) of an alignment output."""
+        import torch
+        res = torch.zeros(3, dtype=torch.int64, device="cuda")
+        s = self._out_struct(out, out["link_i"].numel())
+        _check(lib().mine_link_gold_counts(self._h, C.byref(s), _ptr(gold), _ptr(res), _stream(stream)),
+               "mine_link_gold_counts")
+        return res
+
     def mine(self, params: MineParams, out=None, stream=None):
         """The whole hot path (counts, similarity, alignment, threshold)."""
         out = out if out is not None else self.new_output()
@@ -319,13 +331,30 @@ class SoftAligner:
     def __init__(self, plan: Plan, counts, gold, gamma: float, tau: float = 0.05, eps: float = 1e-7):
         import torch
         self.plan, self.counts, self.gold = plan, counts, gold
-        self.opts = _SoftOpts(float(gamma), float(tau), float(eps))
+        self.opts = _SoftOpts(float(gamma), float(tau), float(eps), None, 0, 0)
+        self._sel = None
         n = lib().softnw_workspace_size(plan.handle)
         if n < 0:
             _check(int(n), "softnw_workspace_size")
         self.ws = torch.empty(max(int(n), 1), dtype=torch.uint8, device="cuda")
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         self.grad = torch.zeros(7, dtype=torch.float32, device="cuda")
+
+    def select(self, pairs=None):
+        """Restrict the next forward/backward to these pairs (a minibatch;
+        host indices, or None for all pairs); the loss is their cells' mean."""
+        import torch
+        if pairs is None:
+            self._sel = None
+            self.opts.pairs, self.opts.n_pairs, self.opts.n_cells = None, 0, 0
+            return
+        pairs = np.asarray(pairs, np.int32)
+        sizes = np.diff(self.plan.cell_offsets)[pairs]
+        pairs = pairs[np.argsort(-sizes, kind="stable")]  # largest first (load balance)
+        self._sel = torch.from_numpy(pairs).cuda()
+        self.opts.pairs = self._sel.data_ptr()
+        self.opts.n_pairs = len(pairs)
+        self.opts.n_cells = int(sizes.sum())
 
     def forward(self, params: MineParams, want_value=False, want_expected=False, stream=None):
         import torch

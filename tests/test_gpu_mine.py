@@ -275,3 +275,61 @@ def test_link_recount_by_warp_vote_matches_cached_counts():
         b = plan.mine(p)
         plan.check()
         _outputs_equal(a, b, batch.n_pairs)
+
+
+def test_graph_replay_equals_direct_launches():
+    """mine_pairs as one captured CUDA graph gives the results of direct
+    launches; new parameters or new output buffers re-capture it."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = _edge_batch()
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        plan.set_option("use_graph", 0)
+        direct = {k: v.clone() for k, v in plan.mine(_params()).items()}
+        direct2 = {k: v.clone() for k, v in plan.mine(_params(gap=0.2, thr=0.4)).items()}
+        torch.cuda.synchronize()
+        plan.set_option("use_graph", 1)
+        out = plan.new_output()
+        for _ in range(3):
+            g = plan.mine(_params(), out)
+        torch.cuda.synchronize()
+        assert plan.get_option("graph_captures") == 1
+        _outputs_equal(direct, g, batch.n_pairs)
+        g2 = plan.mine(_params(gap=0.2, thr=0.4), out)
+        torch.cuda.synchronize()
+        assert plan.get_option("graph_captures") == 2
+        _outputs_equal(direct2, g2, batch.n_pairs)
+        g3 = plan.mine(_params(gap=0.2, thr=0.4))  # new output buffers
+        torch.cuda.synchronize()
+        assert plan.get_option("graph_captures") == 3
+        _outputs_equal(direct2, g3, batch.n_pairs)
+        plan.check()
+
+
+def test_bounded_tile_wait_reports_timeout_and_recovers():
+    """A tile flag that nothing sets (fault injection): the waiting tiles give
+    up after a short bounded spin, mine_plan_check reports MINE_ETIMEOUT, the
+    context stays usable, and the next normal run is correct."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    ns, ms = [300, 40], [410, 50]
+    batch = synth.make_batch(83, 2, v_src=3000, v_tgt=3000, planted_frac=0.0, src_sizes=ns, tgt_sizes=ms)
+    p = _params(thr=-1.0)
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        plan.set_option("tile_min_cells", 1)
+        plan.set_option("tile_min_rows", 33)
+        plan.set_option("tile_cols", 64)
+        assert plan.get_option("n_tile_flags") > 0
+        ref = {k: v.clone() for k, v in plan.mine(p).items()}
+        plan.check()
+        plan.set_option("wait_limit", 2000)  # ~0.4 ms per wait
+        plan.set_option("fault_skip_flag", 0)
+        plan.mine(p)
+        with pytest.raises(miner.MinerError) as e:
+            plan.check()
+        assert e.value.code == miner.MINE_ETIMEOUT
+        plan.set_option("fault_skip_flag", -1)
+        plan.set_option("wait_limit", 1 << 24)
+        got = plan.mine(p)
+        plan.check()
+        _outputs_equal(ref, got, batch.n_pairs)

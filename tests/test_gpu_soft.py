@@ -160,3 +160,24 @@ def test_soft_hessian_vector_product_per_cell(gamma):
               f"sum Hu gpu {got.sum():.6e} oracle {h.sum():.6e}")
         assert err <= 1e-4 * np.abs(h).max()
         assert abs(got.sum() - h.sum()) <= 1e-4 * np.abs(h).sum()
+
+
+def test_minibatch_selection_equals_plan_of_the_subset():
+    """A selected subset of pairs gives the loss and gradient of a plan built
+    from just those pairs (the mean runs over the selected cells)."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = _batch(307, 12, 20)
+    pick = np.array([3, 7, 0, 10, 5])
+    full = _gpu_soft(batch, 0.1, want=False)
+    al = full["aligner"]
+    al.select(pick)
+    params = miner.params_from_theta(THETA)
+    loss, _, _ = al.forward(params)
+    grad = al.backward(params).cpu().numpy()
+    sub = _gpu_soft(batch.subset(np.sort(pick)), 0.1, want=False)
+    assert float(loss[0]) == pytest.approx(sub["loss"], rel=1e-5)
+    assert np.allclose(grad, sub["grad"], rtol=1e-4, atol=1e-7 * np.abs(sub["grad"]).max())
+    al.select(None)
+    loss_all, _, _ = al.forward(params)
+    assert float(loss_all[0]) == pytest.approx(full["loss"], rel=1e-6)
