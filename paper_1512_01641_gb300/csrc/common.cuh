@@ -108,6 +108,47 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// 1-D bulk async copy global -> shared (the copy engine behind TMA), with an
+// mbarrier that counts the arriving bytes.  One elected lane issues; every
+// lane waits with a bounded spin.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Order this thread's earlier shared-memory accesses before the async copy
+// that will overwrite them, then start the copy of `bytes` (multiple of 16,
+// both addresses 16-byte aligned) completing on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Wait for the phase with the given parity to complete; false after `limit`
+// polls (the caller reports a timeout and abandons the work item).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_t limit) {
+    for (int64_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Multiplicative hash of a token id into a table of 2^log_slots slots.
 __device__ __forceinline__ uint32_t hash_slot(int32_t t, int log_slots) {
     return ((uint32_t)t * 0x9E3779B1u) >> (32 - log_slots);

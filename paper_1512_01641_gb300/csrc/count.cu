@@ -18,6 +18,8 @@
 // definitions read: a source position counts once however many of its
 // translations hit; a target position counts once however many source tokens
 // translate to it.
+#include <cstddef>
+
 #include "kernels.h"
 
 namespace gbm {
@@ -176,12 +178,17 @@ constexpr int kPosCap = 992;   // source positions per strip item (32 rows x 31 
 constexpr int kTokCap = 992;   // target tokens per column block (32 sentences x 31 tokens)
 
 template <int LOG_SLOTS>
-struct StripSmem {
+struct alignas(16) StripSmem {
     static constexpr int S = 1 << LOG_SLOTS;
+    uint64_t bar;          // completion barrier of the bulk copies
+    uint32_t pad[2];
     int32_t key[S];
     uint32_t rowmask[S];
     uint32_t colmask[S];
-    uint32_t gh[kTokCap];  // row masks of the block's tokens, then the positions' column masks, then byte tiles
+    // staged tokens (the strip's source tokens, then each block's target
+    // tokens, replaced in place by their row masks), then the positions'
+    // column masks, then the byte tiles
+    uint32_t gh[kTokCap + 8];
     uint16_t ent[kEntCap];
     uint16_t pos_off[kPosCap + 2];
     uint16_t tslot[kTokCap];
@@ -189,8 +196,36 @@ struct StripSmem {
     uint8_t rowid[kPosCap];
 };
 static_assert(kTokCap >= kPosCap && kTokCap * 4 >= 2 * 32 * kPad, "shared buffer sizes");
+static_assert(offsetof(StripSmem<11>, gh) % 16 == 0 && sizeof(StripSmem<11>) % 16 == 0, "bulk copy alignment");
 
 constexpr uint16_t kNoSlot = 0xFFFFu;
+constexpr int64_t kBulkWaitLimit = 1 << 22;
+
+// Stage tokens [a, a+n) of `tok` into buf; returns the index of token a in
+// buf.  A bulk copy moves the 16-byte-aligned cover of the range when the array
+// allows it, plain loads otherwise.  On a copy that never completes the status
+// is flagged and ok is cleared (the caller stops).
+__device__ __forceinline__ int stage_tokens(const int32_t *__restrict__ tok, int64_t n_total, int64_t a, int n,
+                                            uint32_t *buf, uint64_t *bar, uint32_t &phase, bool bulk_ok, int lane,
+                                            uint32_t *status, bool &ok) {
+    const int64_t a16 = a & ~3LL, b16 = (a + n + 3) & ~3LL;
+    const int shift = (int)(a - a16);
+    __syncwarp();
+    if (bulk_ok && n > 0 && b16 <= n_total) {
+        if (lane == 0) bulk_copy_g2s(buf, tok + a16, (uint32_t)((b16 - a16) * 4), bar);
+        ok = mbar_wait(bar, phase, kBulkWaitLimit);
+        phase ^= 1u;
+        if (!ok) {
+            if (lane == 0) atomicOr(status, kStTimeout);
+            (void)mbar_wait(bar, phase ^ 1u, kBulkWaitLimit);  // let the copy in flight land
+        }
+    } else {
+        for (int x = lane; x < n; x += 32) buf[shift + x] = (uint32_t)tok[a + x];
+        ok = true;
+    }
+    __syncwarp();
+    return shift;
+}
 
 // Carry-save accumulation of 0/1 words into bit-sliced counters, four at a time.
 template <int K>
@@ -229,13 +264,16 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
 template <int LOG_SLOTS, int K>
 __global__ void __launch_bounds__(32 * kCountWarps)
 count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
-                   const CountStripItem *__restrict__ items, int64_t n_items, uint8_t *__restrict__ counts,
-                   uint32_t *status) {
+                   const CountStripItem *__restrict__ items, int64_t n_items, bool bulk_ok,
+                   uint8_t *__restrict__ counts, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Smem = StripSmem<LOG_SLOTS>;
     constexpr int S = Smem::S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem &sm = reinterpret_cast<Smem *>(smem_raw)[warp];
+    if (lane == 0) mbar_init(&sm.bar);
+    __syncwarp();
+    uint32_t phase = 0;
     uint8_t(*ms_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(sm.gh);
     uint8_t(*mt_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(reinterpret_cast<uint8_t *>(sm.gh) + 32 * kPad);
 
@@ -259,13 +297,18 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
             sm.colmask[x] = 0u;
         }
         for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
+        bool ok;
+        const int32_t *stok = reinterpret_cast<const int32_t *>(sm.gh) +
+                              stage_tokens(src.tok, src.n_tok, ptok0, n_pos, sm.gh, &sm.bar, phase, bulk_ok, lane,
+                                           status, ok);
+        if (!ok) return;
         // translation entry offsets of the positions
         int carry = 0;
         for (int base = 0; base < n_pos; base += 32) {
             const int p = base + lane;
             int f = 0;
             if (p < n_pos) {
-                const int32_t v = src.tok[ptok0 + p];
+                const int32_t v = stok[p];
                 f = dict.off[v + 1] - dict.off[v];
             }
             int tot;
@@ -281,7 +324,7 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
         __syncwarp();
         // row table
         for (int p = lane; p < n_pos; p += 32) {
-            const int32_t v = src.tok[ptok0 + p];
+            const int32_t v = stok[p];
             const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
             const uint32_t rbit = 1u << sm.rowid[p];
             const int o = sm.pos_off[p];
@@ -310,22 +353,25 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
             const int tpre = warp_excl_scan(my_lt, lane, n_tok);
             const int64_t ttok0 = tgt.sent[ts];
             for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
-            __syncwarp();
-            // column pass
+            const int tsh = stage_tokens(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, phase, bulk_ok, lane,
+                                         status, ok);
+            if (!ok) return;
+            // column pass (each token's row mask replaces it in place)
+            uint32_t *tg = sm.gh + tsh;
             for (int x = lane; x < n_tok; x += 32) {
-                const int slot = table_find<LOG_SLOTS>(sm.key, tgt.tok[ttok0 + x]);
+                const int slot = table_find<LOG_SLOTS>(sm.key, (int32_t)tg[x]);
                 uint32_t rm = 0u;
                 if (slot >= 0) {
                     rm = sm.rowmask[slot];
                     atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
                 }
                 sm.tslot[x] = slot >= 0 ? (uint16_t)slot : kNoSlot;
-                sm.gh[x] = rm;
+                tg[x] = rm;
             }
             __syncwarp();
             Acc4<K> mt;
             mt.c.clear();
-            for (int t = 0; t < my_lt; ++t) mt.add(sm.gh[tpre + t]);
+            for (int t = 0; t < my_lt; ++t) mt.add(tg[tpre + t]);
             mt.finish();
             __syncwarp();
             // row pass
@@ -367,7 +413,7 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
 
 template <int LOG_SLOTS, int K>
 cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
-                           const PairGeom *geom, const CountStripItem *items, int64_t n_items,
+                           const PairGeom *geom, const CountStripItem *items, int64_t n_items, bool bulk_ok,
                            uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st) {
     const size_t smem = sizeof(StripSmem<LOG_SLOTS>) * kCountWarps;
     auto kern = count_strip_kernel<LOG_SLOTS, K>;
@@ -380,7 +426,7 @@ cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const Dev
     int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
     int grid = (int)(want < cap ? want : cap);
     if (grid < 1) return cudaSuccess;
-    kern<<<grid, 32 * kCountWarps, smem, st>>>(src, tgt, dict, geom, items, n_items, counts, status);
+    kern<<<grid, 32 * kCountWarps, smem, st>>>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status);
     return cudaGetLastError();
 }
 
@@ -445,12 +491,13 @@ cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict,
 
 cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                                 const PairGeom *geom, const CountStripItem *items, int64_t n_items,
-                                int log_slots, int planes, uint8_t *counts, uint32_t *status, int n_sms,
-                                cudaStream_t st) {
+                                int log_slots, int planes, bool bulk_ok, uint8_t *counts, uint32_t *status,
+                                int n_sms, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     if (log_slots == 11)
-        return planes <= 5 ? launch_strip_t<11, 5>(src, tgt, dict, geom, items, n_items, counts, status, n_sms, st)
-                           : launch_strip_t<11, 8>(src, tgt, dict, geom, items, n_items, counts, status, n_sms, st);
+        return planes <= 5
+                   ? launch_strip_t<11, 5>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st)
+                   : launch_strip_t<11, 8>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st);
     return cudaErrorInvalidValue;
 }
 

@@ -13,6 +13,7 @@ struct DevCorpus {
     const int64_t *doc;   // n_docs+1
     const int64_t *sent;  // n_sents+1
     const int32_t *tok;
+    int64_t n_tok;        // tokens in tok (bounds of the bulk copies)
 };
 
 struct DevDict {
@@ -82,8 +83,8 @@ cudaError_t launch_count(const DevCorpus &src, const DevCorpus &tgt, const DevDi
 
 cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                                 const PairGeom *geom, const CountStripItem *items, int64_t n_items,
-                                int log_slots, int planes, uint8_t *counts, uint32_t *status, int n_sms,
-                                cudaStream_t st);
+                                int log_slots, int planes, bool bulk_ok, uint8_t *counts, uint32_t *status,
+                                int n_sms, cudaStream_t st);
 
 constexpr int kStripEntCap = 1440;  // translation entries per item of the strip count kernel
 constexpr int kStripLogSlots = 11;  // row-table slots of the strip count kernel (2^11)

@@ -129,6 +129,7 @@ struct mine_plan {
     CountStripItem *strip_items = nullptr;
     int64_t n_strip_items = 0;
     bool use_strips = false;  // strip count kernel (else the per-block kernel)
+    bool bulk_ok = false;     // token arrays 16-byte aligned: bulk-copy staging
     FillItem *fill_items = nullptr;
     uint8_t *counts = nullptr;
     AlignScratch S{};
@@ -359,8 +360,10 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     } while (0)
     PLAN_CK(cudaGetDevice(&p->device));
     PLAN_CK(cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device));
-    p->src = {src->doc_sent_off, src->sent_tok_off, src->tok};
-    p->tgt = {tgt->doc_sent_off, tgt->sent_tok_off, tgt->tok};
+    p->src = {src->doc_sent_off, src->sent_tok_off, src->tok, src->n_tok};
+    p->tgt = {tgt->doc_sent_off, tgt->sent_tok_off, tgt->tok, tgt->n_tok};
+    // token arrays starting on a 16-byte boundary can be staged by bulk copies
+    p->bulk_ok = ((uintptr_t)src->tok % 16 == 0) && ((uintptr_t)tgt->tok % 16 == 0);
     p->dict = {dict->off, dict->tgt};
     const int64_t n = src->n_docs;
     p->n_pairs = n;
@@ -506,7 +509,7 @@ int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     if (p->use_strips) {
         MINE_CK(timed(p, kKCount, st, [&] {
             return launch_count_strips(p->src, p->tgt, p->dict, p->geom, p->strip_items, p->n_strip_items,
-                                       kStripLogSlots, p->planes, counts, p->S.status, p->n_sms, st);
+                                       kStripLogSlots, p->planes, p->bulk_ok, counts, p->S.status, p->n_sms, st);
         }));
     } else {
         MINE_CK(timed(p, kKCount, st, [&] {
