@@ -130,6 +130,7 @@ struct SoftScratch {
     double *partial;      // n_pairs x 9: loss, V, seven gradients
     int32_t *queue;       // work counter
     float *E;             // expected alignment per cell
+    float *U;             // per cell: u = dL/dE, replaced by H u in the backward
     float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
     float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
     float *sbuf;          // per-warp strip buffers

@@ -613,7 +613,7 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct SoftLayout {
-    int64_t partial, queue, E, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
+    int64_t partial, queue, E, U, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
 };
 
 static SoftLayout soft_layout(const mine_plan *p) {
@@ -624,6 +624,8 @@ static SoftLayout soft_layout(const mine_plan *p) {
     L.queue = o;
     o = align_up(o + 4, 256);
     L.E = o;
+    o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
+    L.U = o;
     o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
     const int64_t rows = std::max<int64_t>(p->soft_rows, 1) * 4;
     L.ckv = o;
@@ -648,6 +650,7 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     W.partial = reinterpret_cast<double *>(b + L.partial);
     W.queue = reinterpret_cast<int32_t *>(b + L.queue);
     W.E = reinterpret_cast<float *>(b + L.E);
+    W.U = reinterpret_cast<float *>(b + L.U);
     W.ckv = reinterpret_cast<float *>(b + L.ckv);
     W.ckt = reinterpret_cast<float *>(b + L.ckt);
     W.qrow = reinterpret_cast<float *>(b + L.qrow);
