@@ -45,7 +45,8 @@ OPS_DP = 8     # 3 candidates, 2 max, 2 compare/select, 1 pack
 # DRAM bytes per cell of the dominant kernels, from one ncu capture
 # (profiles/), valid only while the kernel's source is unchanged.
 TRAFFIC = {
-    "count": {"file": "paper_1512_01641_gb300/csrc/count.cu", "sha1": None, "bytes_per_cell": None},
+    "count": {"file": "paper_1512_01641_gb300/csrc/count.cu", "sha1": "f8d75baa7b31f03db7ff064870149593c7fef561",
+              "bytes_per_cell": (265.509632e6 + 407.832320e6) / 218470577},
 }
 
 
