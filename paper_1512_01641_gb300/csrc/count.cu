@@ -50,6 +50,23 @@ __device__ __forceinline__ int table_insert(int32_t *key, int32_t t) {
     return -1;
 }
 
+// As table_insert, and tells whether this call created the key.
+template <int LOG_SLOTS>
+__device__ __forceinline__ bool table_insert_new(int32_t *key, int32_t t, int &slot) {
+    constexpr uint32_t S = 1u << LOG_SLOTS;
+    uint32_t h = hash_slot(t, LOG_SLOTS);
+    for (uint32_t n = 0; n < S; ++n) {
+        const int32_t old = atomicCAS(&key[h], kEmpty, t);
+        if (old == kEmpty || old == t) {
+            slot = (int)h;
+            return old == kEmpty;
+        }
+        h = (h + 1) & (S - 1);
+    }
+    slot = -1;
+    return false;
+}
+
 template <int LOG_SLOTS>
 __device__ __forceinline__ int table_find(const int32_t *key, int32_t t) {
     constexpr uint32_t S = 1u << LOG_SLOTS;
@@ -173,7 +190,7 @@ count_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restr
 // longest sentence; only the two accumulations run one row (column) per lane.
 // Counters are carry-save (four words per step), bytes are expanded by
 // multiply-spread and transposed through shared memory for coalesced writes.
-constexpr int kEntCap = 1440;  // translation entries per strip item (planner limit 0.7 * 2^11)
+constexpr int kEntCap = 1440;  // translation entries of one row group
 constexpr int kPosCap = 992;   // source positions per strip item (32 rows x 31 tokens)
 constexpr int kTokCap = 992;   // target tokens per column block (32 sentences x 31 tokens)
 
@@ -191,14 +208,13 @@ struct alignas(16) StripSmem {
     uint32_t gh[kTokCap + 8];
     uint16_t ent[kEntCap];
     uint16_t pos_off[kPosCap + 2];
-    uint16_t tslot[kTokCap];
     uint8_t colid[kTokCap];
     uint8_t rowid[kPosCap];
+    int32_t n_keys;  // distinct keys of the row table being built
+    int32_t pad2[3];
 };
 static_assert(kTokCap >= kPosCap && kTokCap * 4 >= 2 * 32 * kPad, "shared buffer sizes");
 static_assert(offsetof(StripSmem<11>, gh) % 16 == 0 && sizeof(StripSmem<11>) % 16 == 0, "bulk copy alignment");
-
-constexpr uint16_t kNoSlot = 0xFFFFu;
 constexpr int64_t kBulkWaitLimit = 1 << 22;
 
 // Stage tokens [a, a+n) of `tok` into buf; returns the index of token a in
@@ -261,6 +277,12 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
     return x - v;
 }
 
+// The row group of an item starts as the whole strip; when its translations
+// would fill the row table beyond kMaxLoad (or the entry buffer), the group is
+// halved and rebuilt -- rows are independent, so any grouping gives the same
+// counts.
+constexpr float kMaxLoad = 0.85f;
+
 template <int LOG_SLOTS, int K>
 __global__ void __launch_bounds__(32 * kCountWarps)
 count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
@@ -282,131 +304,142 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
         const CountStripItem item = items[it];
         const PairGeom g = geom[item.pair];
         const int r0 = item.strip * 32;
-        const int rhi = min(item.r_hi, g.n - r0);
-        const bool rv = lane >= item.r_lo && lane < rhi;
-        // source positions of the item's rows, flattened (rows are consecutive
-        // sentences, so their tokens are contiguous)
+        const int rend = min(item.r_hi, g.n - r0);
         const int64_t ssent0 = src.doc[item.pair] + r0;
-        const int my_len = rv ? (int)(src.sent[ssent0 + lane + 1] - src.sent[ssent0 + lane]) : 0;
-        int n_pos;
-        const int prow = warp_excl_scan(my_len, lane, n_pos);
-        const int64_t ptok0 = src.sent[ssent0 + item.r_lo];
-        for (int x = lane; x < S; x += 32) {
-            sm.key[x] = kEmpty;
-            sm.rowmask[x] = 0u;
-            sm.colmask[x] = 0u;
-        }
-        for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
-        bool ok;
-        const int32_t *stok = reinterpret_cast<const int32_t *>(sm.gh) +
-                              stage_tokens(src.tok, src.n_tok, ptok0, n_pos, sm.gh, &sm.bar, phase, bulk_ok, lane,
-                                           status, ok);
-        if (!ok) return;
-        // translation entry offsets of the positions
-        int carry = 0;
-        for (int base = 0; base < n_pos; base += 32) {
-            const int p = base + lane;
-            int f = 0;
-            if (p < n_pos) {
-                const int32_t v = stok[p];
-                f = dict.off[v + 1] - dict.off[v];
+        int group = 32;
+        for (int g_lo = item.r_lo; g_lo < rend;) {
+            const int g_hi = min(g_lo + group, rend);
+            const bool rv = lane >= g_lo && lane < g_hi;
+            // source positions of the group's rows, flattened (rows are
+            // consecutive sentences, so their tokens are contiguous)
+            const int my_len = rv ? (int)(src.sent[ssent0 + lane + 1] - src.sent[ssent0 + lane]) : 0;
+            int n_pos;
+            const int prow = warp_excl_scan(my_len, lane, n_pos);
+            const int64_t ptok0 = src.sent[ssent0 + g_lo];
+            for (int x = lane; x < S; x += 32) {
+                sm.key[x] = kEmpty;
+                sm.rowmask[x] = 0u;
+                sm.colmask[x] = 0u;
             }
-            int tot;
-            const int ex = warp_excl_scan(f, lane, tot);
-            if (p < n_pos) sm.pos_off[p] = (uint16_t)min(carry + ex, 0xFFFF);
-            carry += tot;
-        }
-        if (lane == 0) sm.pos_off[n_pos] = (uint16_t)min(carry, 0xFFFF);
-        if (carry > kEntCap) {
-            if (lane == 0) atomicOr(status, kStTableFull);
-            continue;
-        }
-        __syncwarp();
-        // row table
-        for (int p = lane; p < n_pos; p += 32) {
-            const int32_t v = stok[p];
-            const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
-            const uint32_t rbit = 1u << sm.rowid[p];
-            const int o = sm.pos_off[p];
-            for (int32_t e = e0; e < e1; ++e) {
-                const int h = table_insert<LOG_SLOTS>(sm.key, dict.tgt[e]);
-                if (h < 0) {
-                    atomicOr(status, kStTableFull);
-                    sm.ent[o + (e - e0)] = 0;
-                    continue;
-                }
-                atomicOr(&sm.rowmask[h], rbit);
-                sm.ent[o + (e - e0)] = (uint16_t)h;
-            }
-        }
-        __syncwarp();
-
-        const int nblk = (g.m + 31) >> 5;
-        const int64_t tdoc = tgt.doc[item.pair];
-        uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m);
-        for (int jb = 0; jb < nblk; ++jb) {
-            const int c0 = jb * 32;
-            const int nc = min(32, g.m - c0);
-            const int64_t ts = tdoc + c0;
-            const int my_lt = lane < nc ? (int)(tgt.sent[ts + lane + 1] - tgt.sent[ts + lane]) : 0;
-            int n_tok;
-            const int tpre = warp_excl_scan(my_lt, lane, n_tok);
-            const int64_t ttok0 = tgt.sent[ts];
-            for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
-            const int tsh = stage_tokens(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, phase, bulk_ok, lane,
-                                         status, ok);
+            if (lane == 0) sm.n_keys = 0;
+            for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
+            bool ok;
+            const int32_t *stok = reinterpret_cast<const int32_t *>(sm.gh) +
+                                  stage_tokens(src.tok, src.n_tok, ptok0, n_pos, sm.gh, &sm.bar, phase, bulk_ok, lane,
+                                               status, ok);
             if (!ok) return;
-            // column pass (each token's row mask replaces it in place)
-            uint32_t *tg = sm.gh + tsh;
-            for (int x = lane; x < n_tok; x += 32) {
-                const int slot = table_find<LOG_SLOTS>(sm.key, (int32_t)tg[x]);
-                uint32_t rm = 0u;
-                if (slot >= 0) {
-                    rm = sm.rowmask[slot];
-                    atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
+            // translation entry offsets of the positions
+            int carry = 0;
+            for (int base = 0; base < n_pos; base += 32) {
+                const int p = base + lane;
+                int f = 0;
+                if (p < n_pos) {
+                    const int32_t v = stok[p];
+                    f = dict.off[v + 1] - dict.off[v];
                 }
-                sm.tslot[x] = slot >= 0 ? (uint16_t)slot : kNoSlot;
-                tg[x] = rm;
+                int tot;
+                const int ex = warp_excl_scan(f, lane, tot);
+                if (p < n_pos) sm.pos_off[p] = (uint16_t)min(carry + ex, 0xFFFF);
+                carry += tot;
             }
+            if (lane == 0) sm.pos_off[n_pos] = (uint16_t)min(carry, 0xFFFF);
+            // row table
+            bool full = carry > kEntCap;
             __syncwarp();
-            Acc4<K> mt;
-            mt.c.clear();
-            for (int t = 0; t < my_lt; ++t) mt.add(tg[tpre + t]);
-            mt.finish();
-            __syncwarp();
-            // row pass
-            for (int p = lane; p < n_pos; p += 32) {
-                uint32_t h = 0u;
-                const int e1 = sm.pos_off[p + 1];
-                for (int e = sm.pos_off[p]; e < e1; ++e) h |= sm.colmask[sm.ent[e]];
-                sm.gh[p] = h;
-            }
-            __syncwarp();
-            Acc4<K> ms;
-            ms.c.clear();
-            for (int t = 0; t < my_len; ++t) ms.add(sm.gh[prow + t]);
-            ms.finish();
-            __syncwarp();
-            for (int x = lane; x < n_tok; x += 32) {
-                const uint16_t sl = sm.tslot[x];
-                if (sl != kNoSlot) sm.colmask[sl] = 0u;
-            }
-            // expand, transpose, write
-            uint32_t w[8];
-            ms.c.to_bytes(w);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&ms_t[lane][4 * m]) = w[m];
-            mt.c.to_bytes(w);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&mt_t[lane][4 * m]) = w[m];
-            __syncwarp();
-            if (lane < nc) {
-                for (int i = item.r_lo; i < rhi; ++i) {
-                    const uchar2 v = make_uchar2(ms_t[i][lane], mt_t[lane][i]);
-                    reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[lane] = v;
+            if (!full) {
+                for (int p = lane; p < n_pos; p += 32) {
+                    const int32_t v = stok[p];
+                    const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
+                    const uint32_t rbit = 1u << sm.rowid[p];
+                    const int o = sm.pos_off[p];
+                    for (int32_t e = e0; e < e1; ++e) {
+                        int h;
+                        const bool fresh = table_insert_new<LOG_SLOTS>(sm.key, dict.tgt[e], h);
+                        if (h < 0) {
+                            sm.ent[o + (e - e0)] = 0;
+                            continue;
+                        }
+                        if (fresh) atomicAdd(&sm.n_keys, 1);
+                        atomicOr(&sm.rowmask[h], rbit);
+                        sm.ent[o + (e - e0)] = (uint16_t)h;
+                    }
                 }
+                __syncwarp();
+                full = sm.n_keys > (int)(kMaxLoad * S);
             }
-            __syncwarp();
+            if (full) {
+                if (group == 1) {  // one row alone does not fit: give up on this item
+                    if (lane == 0) atomicOr(status, kStTableFull);
+                    break;
+                }
+                group >>= 1;
+                continue;
+            }
+
+            const int nblk = (g.m + 31) >> 5;
+            const int64_t tdoc = tgt.doc[item.pair];
+            uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m);
+            for (int jb = 0; jb < nblk; ++jb) {
+                const int c0 = jb * 32;
+                const int nc = min(32, g.m - c0);
+                const int64_t ts = tdoc + c0;
+                const int my_lt = lane < nc ? (int)(tgt.sent[ts + lane + 1] - tgt.sent[ts + lane]) : 0;
+                int n_tok;
+                const int tpre = warp_excl_scan(my_lt, lane, n_tok);
+                const int64_t ttok0 = tgt.sent[ts];
+                for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
+                const int tsh = stage_tokens(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, phase, bulk_ok, lane,
+                                             status, ok);
+                if (!ok) return;
+                // column pass (each token's row mask replaces it in place)
+                uint32_t *tg = sm.gh + tsh;
+                for (int x = lane; x < n_tok; x += 32) {
+                    const int slot = table_find<LOG_SLOTS>(sm.key, (int32_t)tg[x]);
+                    uint32_t rm = 0u;
+                    if (slot >= 0) {
+                        rm = sm.rowmask[slot];
+                        atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
+                    }
+                    tg[x] = rm;
+                }
+                __syncwarp();
+                Acc4<K> mt;
+                mt.c.clear();
+                for (int t = 0; t < my_lt; ++t) mt.add(tg[tpre + t]);
+                mt.finish();
+                __syncwarp();
+                // row pass
+                for (int p = lane; p < n_pos; p += 32) {
+                    uint32_t h = 0u;
+                    const int e1 = sm.pos_off[p + 1];
+                    for (int e = sm.pos_off[p]; e < e1; ++e) h |= sm.colmask[sm.ent[e]];
+                    sm.gh[p] = h;
+                }
+                __syncwarp();
+                Acc4<K> ms;
+                ms.c.clear();
+                for (int t = 0; t < my_len; ++t) ms.add(sm.gh[prow + t]);
+                ms.finish();
+                __syncwarp();
+                for (int x = lane; x < S / 4; x += 32) reinterpret_cast<uint4 *>(sm.colmask)[x] = make_uint4(0, 0, 0, 0);
+                // expand, transpose, write
+                uint32_t w[8];
+                ms.c.to_bytes(w);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&ms_t[lane][4 * m]) = w[m];
+                mt.c.to_bytes(w);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&mt_t[lane][4 * m]) = w[m];
+                __syncwarp();
+                if (lane < nc) {
+                    for (int i = g_lo; i < g_hi; ++i) {
+                        const uchar2 v = make_uchar2(ms_t[i][lane], mt_t[lane][i]);
+                        reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[lane] = v;
+                    }
+                }
+                __syncwarp();
+            }
+            g_lo = g_hi;
         }
     }
 }
@@ -450,44 +483,7 @@ cudaError_t launch_count_t(const DevCorpus &src, const DevCorpus &tgt, const Dev
 }
 
 
-// Translation totals of every 32-row strip (sizes the row tables) and the
-// largest per-sentence total (sizes the slot lists).
-__global__ void strip_translations_kernel(DevCorpus src, DevDict dict, const PairGeom *__restrict__ geom,
-                                          const int64_t *__restrict__ strip_off, int64_t n_pairs,
-                                          int32_t *__restrict__ strip_tr, int32_t *__restrict__ max_row) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride) {
-        const int N = geom[k].n;
-        const int64_t base = src.doc[k];
-        int best = 0;
-        for (int s = 0; s * 32 < N; ++s) {
-            int64_t tot = 0;
-            for (int r = s * 32; r < min(N, s * 32 + 32); ++r) {
-                int row = 0;
-                for (int64_t p = src.sent[base + r]; p < src.sent[base + r + 1]; ++p) {
-                    const int32_t v = src.tok[p];
-                    row += dict.off[v + 1] - dict.off[v];
-                }
-                best = max(best, row);
-                tot += row;
-            }
-            strip_tr[strip_off[k] + s] = (int32_t)(tot < 0x7fffffffLL ? tot : 0x7fffffffLL);
-        }
-        atomicMax(max_row, best);
-    }
-}
-
 }  // namespace
-
-cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict, const PairGeom *geom,
-                                      const int64_t *strip_off, int64_t n_pairs, int32_t *strip_tr,
-                                      int32_t *max_row, cudaStream_t st) {
-    if (n_pairs == 0) return cudaSuccess;
-    const int64_t blocks = (n_pairs + 127) / 128;
-    strip_translations_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 128, 0, st>>>(
-        src, dict, geom, strip_off, n_pairs, strip_tr, max_row);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                                 const PairGeom *geom, const CountStripItem *items, int64_t n_items,

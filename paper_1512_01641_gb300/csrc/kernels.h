@@ -86,12 +86,8 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
                                 int log_slots, int planes, bool bulk_ok, uint8_t *counts, uint32_t *status,
                                 int n_sms, cudaStream_t st);
 
-constexpr int kStripEntCap = 1440;  // translation entries per item of the strip count kernel
 constexpr int kStripLogSlots = 11;  // row-table slots of the strip count kernel (2^11)
-
-cudaError_t launch_strip_translations(const DevCorpus &src, const DevDict &dict, const PairGeom *geom,
-                                      const int64_t *strip_off, int64_t n_pairs, int32_t *strip_tr,
-                                      int32_t *max_row, cudaStream_t st);
+constexpr int kStripMaxFanout = 46; // dictionary fan-out up to which one row always fits the row table
 
 cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                          int64_t n_pairs, const DevParams &P, const uint8_t *counts, float *s,

@@ -39,7 +39,7 @@ __global__ void validate_corpus_kernel(DevCorpus c, int64_t n_sents, int64_t n_t
 }
 
 __global__ void validate_dict_kernel(DevDict d, int32_t v_src, int32_t v_tgt, int64_t n_entries,
-                                     uint32_t *status) {
+                                     uint32_t *status, int32_t *max_fanout) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < v_src; v += stride) {
         const int64_t a = d.off[v], b = d.off[v + 1];
@@ -47,6 +47,7 @@ __global__ void validate_dict_kernel(DevDict d, int32_t v_src, int32_t v_tgt, in
             atomicOr(status, kStBadDict);
             continue;
         }
+        atomicMax(max_fanout, (int32_t)(b - a < 0x7fffffffLL ? b - a : 0x7fffffffLL));
         int32_t prev = -1;
         for (int64_t e = a; e < b; ++e) {
             const int32_t t = d.tgt[e];
@@ -133,7 +134,7 @@ struct mine_plan {
     FillItem *fill_items = nullptr;
     uint8_t *counts = nullptr;
     AlignScratch S{};
-    int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens, max row translations]
+    int32_t *stats = nullptr;  // [max src len, max tgt len, max block tokens, max dictionary fan-out]
     int log_slots = 11, planes = 5, n_sms = 1, device = 0;
     // per-kernel timing hook
     bool timing = false;
@@ -212,10 +213,10 @@ static void plan_free(mine_plan *p) {
     delete p;
 }
 
-static int validate_dict(const mine_dict *d, uint32_t *status, cudaStream_t st) {
+static int validate_dict(const mine_dict *d, uint32_t *status, int32_t *max_fanout, cudaStream_t st) {
     int64_t blocks = std::min<int64_t>((d->v_src + 255) / 256, 4096);
     gbm::validate_dict_kernel<<<(unsigned)blocks, 256, 0, st>>>(DevDict{d->off, d->tgt}, d->v_src, d->v_tgt,
-                                                                d->n_entries, status);
+                                                                d->n_entries, status, max_fanout);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_last_cuda = (int)e;
@@ -388,7 +389,7 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     if (tgt->n_sents > 0)
         PLAN_CK(launch_validate_corpus(p->tgt, tgt->n_sents, tgt->n_tok, dict->v_tgt, p->S.status, p->stats + 1, st));
     {
-        int r = validate_dict(dict, p->S.status, st);
+        int r = validate_dict(dict, p->S.status, p->stats + 3, st);
         if (r != MINE_OK) return fail(r);
     }
 
@@ -427,57 +428,28 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     PLAN_CK(cudaStreamSynchronize(st));
     if (status[0] != 0) return fail(MINE_EINVAL);
 
-    // strip count kernel: translation totals per strip decide row-table splits
-    {
-        std::vector<int64_t> strip_off(n + 1, 0);
-        for (int64_t k = 0; k < n; ++k) strip_off[k + 1] = strip_off[k] + (p->geom_h[k].n + 31) / 32;
-        const int64_t n_strips = strip_off[n];
-        int64_t *d_off = nullptr;
-        int32_t *d_tr = nullptr;
-        PLAN_CK(dalloc(&d_off, n + 1));
-        e = dalloc(&d_tr, n_strips);
-        if (e != cudaSuccess) cudaFree(d_off);
-        PLAN_CK(e);
-        std::vector<int32_t> tr(n_strips > 0 ? n_strips : 1);
-        e = cudaMemcpyAsync(d_off, strip_off.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = launch_strip_translations(p->src, p->dict, p->geom, d_off, n, d_tr, p->stats + 3, st);
-        if (e == cudaSuccess && n_strips > 0)
-            e = cudaMemcpyAsync(tr.data(), d_tr, n_strips * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(stats, p->stats, sizeof stats, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        cudaFree(d_off);
-        cudaFree(d_tr);
-        PLAN_CK(e);
-        const int maxlen0 = std::max(stats[0], stats[1]);
-        p->use_strips = maxlen0 <= 31 && stats[3] <= kStripEntCap;
-        if (p->use_strips) {
-            // a strip whose translations would fill the row table past ~70% is
-            // split into 2, 4, ... row groups
-            const int64_t limit = std::min<int64_t>((int64_t)(0.7 * (1 << kStripLogSlots)), kStripEntCap);
-            std::vector<int32_t> order(n);
-            std::iota(order.begin(), order.end(), 0);
-            std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-                return (int64_t)p->geom_h[a].n * p->geom_h[a].m > (int64_t)p->geom_h[b].n * p->geom_h[b].m;
-            });
-            std::vector<CountStripItem> sitems;
-            for (int32_t k : order) {
-                if (p->geom_h[k].m == 0) continue;
-                const int ns = (p->geom_h[k].n + 31) / 32;
-                for (int sidx = 0; sidx < ns; ++sidx) {
-                    const int64_t t = tr[strip_off[k] + sidx];
-                    int parts = 1;
-                    while (parts < 32 && t > limit * parts) parts *= 2;
-                    const int rows = 32 / parts;
-                    for (int q = 0; q < parts; ++q) sitems.push_back({k, sidx, q * rows, (q + 1) * rows});
-                }
-            }
-            p->n_strip_items = (int64_t)sitems.size();
-            PLAN_CK(dalloc(&p->strip_items, sitems.size()));
-            PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
-                                    cudaMemcpyHostToDevice, st));
-            PLAN_CK(cudaStreamSynchronize(st));
+    // strip count kernel: one item per 32-row strip, largest pairs first (the
+    // kernel itself halves a strip's row group when its translations would
+    // overfill the row table); it needs sentences of at most 31 tokens (5
+    // counter planes) and a dictionary fan-out small enough for one row to fit
+    p->use_strips = std::max(stats[0], stats[1]) <= 31 && stats[3] <= kStripMaxFanout;
+    if (p->use_strips) {
+        std::vector<int32_t> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return (int64_t)p->geom_h[a].n * p->geom_h[a].m > (int64_t)p->geom_h[b].n * p->geom_h[b].m;
+        });
+        std::vector<CountStripItem> sitems;
+        for (int32_t k : order) {
+            if (p->geom_h[k].m == 0) continue;
+            const int ns = (p->geom_h[k].n + 31) / 32;
+            for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
         }
+        p->n_strip_items = (int64_t)sitems.size();
+        PLAN_CK(dalloc(&p->strip_items, sitems.size()));
+        PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
+                                cudaMemcpyHostToDevice, st));
+        PLAN_CK(cudaStreamSynchronize(st));
     }
     const int maxlen = std::max(stats[0], stats[1]);
     p->planes = maxlen <= 31 ? 5 : 8;
