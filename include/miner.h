@@ -167,14 +167,21 @@ int mine_link_gold_counts(mine_plan *plan, const mine_out *out, const uint8_t *g
                                       wait on it give up after MINE_OPT_WAIT_LIMIT spins
                                       and mine_plan_check reports MINE_ETIMEOUT (-1: off) */
 #define MINE_OPT_N_TILE_FLAGS 9   /* read-only: tile flags of the plan (tiled pairs) */
+#define MINE_OPT_SOFT_SPLIT 10    /* softnw sweeps: 0 one warp per pair; 1 a pair whose
+                                     serial chain (strips x (M + 32) steps) is above the
+                                     mean per warp is split over warps, one strip each,
+                                     in a wavefront (1); 2 every pair of two or more
+                                     strips is split.  Same results in every mode. */
 int mine_plan_set_option(mine_plan *plan, int option, int64_t value);
 /* Current value of an option, or MINE_EINVAL for an unknown option. */
 int64_t mine_plan_get_option(const mine_plan *plan, int option);
 
 /* Synchronise the stream and report device-side errors raised since the last
- * check: MINE_ETIMEOUT if a bounded wait of the cooperative fill gave up (its
- * results are then invalid), MINE_EINVAL if a count table overflowed, else
- * MINE_OK.  Clears the recorded errors. */
+ * check: MINE_ETIMEOUT if a bounded wait of the cooperative fill or of a
+ * split soft sweep gave up (its results are then invalid), MINE_EINVAL if a
+ * count table overflowed or a soft work list did not fit the workspace
+ * (repeated entries in softnw_opts.pairs), else MINE_OK.  Clears the recorded
+ * errors. */
 int mine_plan_check(mine_plan *plan, miner_stream_t stream);
 
 /* Per-kernel timing (profiling aid).  When enabled, every kernel launch of the
@@ -206,7 +213,8 @@ typedef struct {
     float gamma;           /* smoothing temperature (> 0); -> hard NW as gamma -> 0 */
     float tau;             /* gate temperature of the acceptance threshold (> 0) */
     float eps;             /* clamp of P (0 < eps < 0.5) */
-    const int32_t *pairs;  /* device: the pairs to include (a minibatch), or NULL for all */
+    const int32_t *pairs;  /* device: the pairs to include (a minibatch, distinct
+                              pair indices), or NULL for all */
     int64_t n_pairs;       /* number of entries of pairs (ignored when pairs is NULL) */
     int64_t n_cells;       /* cells of the listed pairs: the loss is their mean
                               (ignored when pairs is NULL) */

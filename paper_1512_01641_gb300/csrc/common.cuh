@@ -212,5 +212,6 @@ constexpr uint32_t kStUnsorted = 1u << 3;
 constexpr uint32_t kStBadDict = 1u << 4;
 constexpr uint32_t kStTableFull = 1u << 5;
 constexpr uint32_t kStTimeout = 1u << 6;
+constexpr uint32_t kStBadList = 1u << 7;  // soft work list over capacity (repeated pairs)
 
 }  // namespace gbm

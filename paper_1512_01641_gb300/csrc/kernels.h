@@ -121,16 +121,38 @@ cudaError_t launch_link_gold(const PairGeom *geom, int64_t n_pairs, const int64_
 // Soft alignment: scalar arguments and the caller's workspace, carved up.
 struct SoftArgs {
     float gamma, tau, eps, inv_cells;
+    int64_t wait_limit;  // bounded spins of a strip wait (split pairs)
+    uint32_t *status;    // plan status word (timeout bit)
+    int split;           // 0: one warp per pair, 1: split long pairs, 2: split every pair of >= 2 strips
+};
+constexpr int kSoftChunk = 4096;  // cells per chunk of the per-cell kernels
+constexpr int kSoftSlots = 8;     // per chunk: loss sum, seven gradient sums
+// Work item of the sweep kernels: a whole pair (kind 0), or one strip of a
+// split pair in the forward wavefront (kind 1) or in the adjoint wavefront
+// (kind 2); ctr = the pair's first progress counter.
+struct SoftItem {
+    int32_t pos, strip, kind, ctr;
+};
+// Chunk of the per-cell kernels: cells [c0, c0 + kSoftChunk) of listed pair pos.
+struct SoftChunk {
+    int32_t pos, pad;
+    int64_t c0;
 };
 struct SoftScratch {
-    double *partial;      // n_pairs x 9: loss, V, seven gradients
-    int32_t *queue;       // work counter
+    double *partial;      // per chunk: kSoftSlots sums
+    double *vpart;        // per listed pair: V(N,M)
+    int32_t *queue;       // [0] work counter, [1] items, [2] chunks
+    SoftItem *items;      // sweep work list
+    SoftChunk *chunks;    // per-cell work list
+    int32_t *prog1;       // per strip of a split pair: forward columns published
+    int32_t *prog2;       // per strip of a split pair: adjoint steps published
     float *E;             // expected alignment per cell
     float *U;             // per cell: u = dL/dE, replaced by H u in the backward
     float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
     float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
     float *sbuf;          // per-warp strip buffers
     int64_t sbuf_stride;  // floats per warp
+    int64_t items_cap, chunks_cap, ctr_cap;
 };
 
 int64_t soft_warps(int n_sms);

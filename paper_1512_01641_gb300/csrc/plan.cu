@@ -112,6 +112,7 @@ struct PlanKnobs {
     int link_recount = 0;              // 1: recount link overlaps by warp vote
     int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
     int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
+    int soft_split = 1;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs split over warps
 };
 
 struct mine_plan {
@@ -123,6 +124,7 @@ struct mine_plan {
     std::vector<int32_t> pair_order_h;  // pairs by decreasing size
     int32_t *pair_order = nullptr;
     int64_t soft_rows = 0;              // sum over pairs of nstrips * M
+    int64_t soft_strips = 0;            // sum over pairs of nstrips
     int32_t max_m = 0;
     PlanKnobs knobs;
     PairGeom *geom = nullptr;
@@ -238,6 +240,7 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->geom_h.assign(n, PairGeom{});
     p->cell_off_h.assign(n + 1, 0);
     p->soft_rows = 0;
+    p->soft_strips = 0;
     p->max_m = 0;
     int64_t cell = 0, link = 0, flags = 0;
     tbw = hrow = vcol = 0;
@@ -253,6 +256,7 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
         g.vcol_off = vcol;
         g.soft_off = p->soft_rows;
         p->soft_rows += ((g.n + 31) / 32) * (int64_t)g.m;
+        p->soft_strips += (g.n + 31) / 32;
         p->max_m = std::max(p->max_m, g.m);
         p->cell_off_h[k] = cell;
         const int64_t ns = (g.n + 31) / 32, nb = (g.m + 31) / 32;
@@ -585,16 +589,30 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct SoftLayout {
-    int64_t partial, queue, E, U, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
+    int64_t partial, vpart, queue, items, chunks, prog1, prog2, E, U, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
+    int64_t items_cap, chunks_cap, ctr_cap;
 };
 
 static SoftLayout soft_layout(const mine_plan *p) {
     SoftLayout L;
+    L.items_cap = p->n_pairs + 2 * p->soft_strips;
+    L.chunks_cap = p->n_pairs + p->n_cells / kSoftChunk + 1;
+    L.ctr_cap = p->soft_strips;
     int64_t o = 0;
     L.partial = o;
-    o = align_up(o + std::max<int64_t>(p->n_pairs, 1) * 9 * (int64_t)sizeof(double), 256);
+    o = align_up(o + L.chunks_cap * kSoftSlots * (int64_t)sizeof(double), 256);
+    L.vpart = o;
+    o = align_up(o + std::max<int64_t>(p->n_pairs, 1) * (int64_t)sizeof(double), 256);
     L.queue = o;
-    o = align_up(o + 4, 256);
+    o = align_up(o + 16, 256);
+    L.items = o;
+    o = align_up(o + std::max<int64_t>(L.items_cap, 1) * (int64_t)sizeof(SoftItem), 256);
+    L.chunks = o;
+    o = align_up(o + L.chunks_cap * (int64_t)sizeof(SoftChunk), 256);
+    L.prog1 = o;
+    o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
+    L.prog2 = o;
+    o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
     L.E = o;
     o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
     L.U = o;
@@ -620,7 +638,12 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     char *b = static_cast<char *>(ws);
     SoftScratch W;
     W.partial = reinterpret_cast<double *>(b + L.partial);
+    W.vpart = reinterpret_cast<double *>(b + L.vpart);
     W.queue = reinterpret_cast<int32_t *>(b + L.queue);
+    W.items = reinterpret_cast<SoftItem *>(b + L.items);
+    W.chunks = reinterpret_cast<SoftChunk *>(b + L.chunks);
+    W.prog1 = reinterpret_cast<int32_t *>(b + L.prog1);
+    W.prog2 = reinterpret_cast<int32_t *>(b + L.prog2);
     W.E = reinterpret_cast<float *>(b + L.E);
     W.U = reinterpret_cast<float *>(b + L.U);
     W.ckv = reinterpret_cast<float *>(b + L.ckv);
@@ -629,6 +652,9 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     W.qtrow = reinterpret_cast<float *>(b + L.qtrow);
     W.sbuf = reinterpret_cast<float *>(b + L.sbuf);
     W.sbuf_stride = L.sbuf_stride;
+    W.items_cap = L.items_cap;
+    W.chunks_cap = L.chunks_cap;
+    W.ctr_cap = L.ctr_cap;
     return W;
 }
 
@@ -637,6 +663,9 @@ static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, con
     A.gamma = o->gamma;
     A.tau = o->tau;
     A.eps = o->eps;
+    A.wait_limit = p->knobs.wait_limit;
+    A.status = p->S.status;
+    A.split = p->knobs.soft_split;
     int64_t cells = p->n_cells;
     order = p->pair_order;
     n = p->n_pairs;
@@ -741,6 +770,10 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
             p->knobs.skip_flag = value < 0 ? -1 : value;
             drop_graph(p);
             return MINE_OK;
+        case MINE_OPT_SOFT_SPLIT:
+            if (value < 0 || value > 2) return MINE_EINVAL;
+            p->knobs.soft_split = (int)value;
+            return MINE_OK;
         default:
             return MINE_EINVAL;
     }
@@ -780,6 +813,7 @@ int64_t mine_plan_get_option(const mine_plan *p, int option) {
         case MINE_OPT_GRAPH_CAPTURES: return p->graph_captures;
         case MINE_OPT_FAULT_SKIP_FLAG: return p->knobs.skip_flag;
         case MINE_OPT_N_TILE_FLAGS: return p->n_flags;
+        case MINE_OPT_SOFT_SPLIT: return p->knobs.soft_split;
         default: return MINE_EINVAL;
     }
 }

@@ -72,7 +72,29 @@ struct SoftCtx {
     SimCol *colv;          // shared: column constants of the block being prepared
     float (*svb)[32][32];  // shared: similarities of the current and previous block [2][row][col]
     float (*ub)[32][32];   // shared: u of the current and previous block
+    int64_t wait_limit;    // bounded spins of a strip wait
+    uint32_t *status;      // timeout bit
+    bool failed;           // a wait of the current item gave up
 };
+
+// Bounded wait until the progress counter *ctr reaches need.  Every lane
+// acquires, so that its own later loads see what the producer wrote before
+// it published; the warp leaves when every lane has seen enough.  After
+// wait_limit polls the wait gives up, sets the timeout bit and stops waiting
+// for the rest of the item (its results are then invalid, the status says so).
+__device__ __forceinline__ void soft_wait(SoftCtx &C, const int32_t *ctr, int need, int &have) {
+    if (C.failed || __all_sync(kFull, have >= need)) return;
+    for (int64_t it = 0;; ++it) {
+        have = ld_acquire(ctr);
+        if (__all_sync(kFull, have >= need)) return;
+        if (it >= C.wait_limit) {
+            C.failed = true;
+            if (C.lane == 0) atomicOr(C.status, kStTimeout);
+            return;
+        }
+        __nanosleep(100);
+    }
+}
 
 // Soft max of three candidates relative to a common base: returns D and the
 // three weights.
@@ -142,11 +164,16 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv
 // ck*_out: this strip's checkpoint row (written by the last lane), may be null.
 // vlast (may be null): receives the DOWN outputs of row N-1, V(N,j) - V(N,j-1) - p,
 // from which V(N,M) is summed in FP64 outside the sweep.
+// Split pairs (strips on different warps): wait_top (may be null) counts the
+// checkpoint columns the strip above has published, pub (may be null)
+// receives this strip's count (lane 31 writes column j at step j + 31, so
+// after block jb columns 0..32 jb are out).
 template <bool TAN, bool STORE>
 __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *__restrict__ ckv_top,
                                                const float *__restrict__ ckt_top, float *__restrict__ ckv_out,
                                                float *__restrict__ ckt_out, float *__restrict__ sbuf,
-                                               float *__restrict__ vlast) {
+                                               float *__restrict__ vlast, const int32_t *wait_top = nullptr,
+                                               int32_t *pub = nullptr) {
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
@@ -155,10 +182,12 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
     const int nb = (C.M + 31) >> 5;
     float b = -C.two_p, a_down = 0.0f;
     float bt = 0.0f, at_down = 0.0f;
+    int have = 0;
     for (int jb = 0; jb <= nb; ++jb) {
         if (jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
         const int colx = 32 * jb + lane;
         const bool top = s > 0 && colx < C.M;
+        if (wait_top && 32 * jb < C.M) soft_wait(C, wait_top, min(32 * jb + 32, C.M), have);
         const float hv = top ? __ldcg(ckv_top + colx) : -C.two_p;
         const float htv = (TAN && top) ? __ldcg(ckt_top + colx) : 0.0f;
 #pragma unroll 4
@@ -214,6 +243,7 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
                 if (vlast && r == C.N - 1) __stcg(vlast + j, a_down);
             }
         }
+        if (pub && lane == 31) st_release(pub, min(32 * jb + 1, C.M));
     }
     __syncwarp();
 }
@@ -223,9 +253,13 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
 // Reverse skew: lane i handles column M-1-(t-(31-i)) at step t, so that the
 // cell below (lane i+1) was done one step earlier; its outflows come up by a
 // shuffle, the strip below's through qrow/qtrow.
+// Split pairs: wait_below (may be null) counts the steps the strip below has
+// published, pub (may be null) receives this strip's count (lane 0 writes
+// column j of qrow at step M + 30 - j).
 template <bool TAN>
 __device__ __forceinline__ void soft_rev_strip(SoftCtx &C, int s, const float *__restrict__ sbuf, float *qrow,
-                                               float *qtrow, float rgamma) {
+                                               float *qtrow, float rgamma, const int32_t *wait_below = nullptr,
+                                               int32_t *pub = nullptr) {
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
@@ -236,9 +270,12 @@ __device__ __forceinline__ void soft_rev_strip(SoftCtx &C, int s, const float *_
     float qt_send = 0.0f, dtflow = 0.0f, qtright = 0.0f;
     constexpr int NC = TAN ? 6 : 3;
     constexpr int CH = 8;  // steps per prefetched chunk
+    int have = 0;
     // chunk loader: the weights of steps t0..t0+7 (registers) and, in lanes
     // 0..7, the inflow from the strip below for the columns lane 31 meets then
+    // (down to column M-8-t0, which the strip below writes at its step t0+38)
     auto load = [&](int t0, float (&w)[CH][NC], float &qb, float &qtb) {
+        if (wait_below) soft_wait(C, wait_below, min(t0 + CH + 31, T), have);
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
             const int t = t0 + k;
@@ -302,29 +339,24 @@ __device__ __forceinline__ void soft_rev_strip(SoftCtx &C, int s, const float *_
             }
         }
     };
+    auto publish = [&](int t0) {
+        if (pub && lane == 0) st_release(pub, min(t0 + CH, T));
+    };
     // two chunks in flight: load chunk c+1 while chunk c runs
     for (int t0 = 0; t0 < T; t0 += 2 * CH) {
         if (t0 + CH < T) load(t0 + CH, wb, qb, qtb);
         run(t0, wa, qa, qta);
+        publish(t0);
         if (t0 + CH >= T) break;
         if (t0 + 2 * CH < T) load(t0 + 2 * CH, wa, qa, qta);
         run(t0 + CH, wb, qb, qtb);
+        publish(t0 + CH);
     }
     __syncwarp();
 }
 
-// Per-pair partial results, at the pair's position in the work order:
-// [loss sum, V, dL/dw0..w3, dL/db, dL/dgap, dL/dthr]
-constexpr int kSoftSlots = 9;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
-}
-
-__device__ __forceinline__ bool next_pair(int32_t *queue, int64_t n, int lane, int64_t &it) {
-    int64_t x = 0;
+__device__ __forceinline__ bool next_item(int32_t *queue, int32_t n, int lane, int32_t &it) {
+    int32_t x = 0;
     if (lane == 0) x = atomicAdd(queue, 1);
     it = __shfl_sync(kFull, x, 0);
     return it < n;
@@ -357,6 +389,9 @@ __device__ __forceinline__ SoftCtx make_ctx(const DevParams &P, const SoftArgs &
     C.ktau = kLog2e / A.tau;
     C.eps = A.eps;
     C.inv_cells = A.inv_cells;
+    C.wait_limit = A.wait_limit;
+    C.status = A.status;
+    C.failed = false;
     return C;
 }
 
@@ -373,45 +408,65 @@ __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
     C.colv = sm.colv;
 }
 
-// Sweep 1 (value) + sweep 2 (adjoint): V(N,M) and E for every cell.
+// Sweep 1 (value) + sweep 2 (adjoint): V(N,M) and E for every cell.  A
+// whole pair runs both sweeps strip by strip on one warp; a split pair's
+// strips run on different warps, the value sweep top-down (kind 1) and the
+// recompute + adjoint sweep bottom-up (kind 2), each strip a little behind
+// its neighbour.  Every wait is on an item listed (so dequeued) earlier.
 __global__ void __launch_bounds__(32 * kSoftWarps)
 soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                    int64_t n_pairs, DevParams P, SoftArgs A, const uint8_t *__restrict__ counts,
-                    const uint8_t *__restrict__ gold, SoftScratch W) {
+                    DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
+                    SoftScratch W) {
     extern __shared__ __align__(16) unsigned char soft_smem[];
     SoftCtx C = make_ctx(P, A);
     bind_smem(C, soft_smem);
     const int lane = C.lane;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     float *sbuf = W.sbuf + gw * W.sbuf_stride;
-    int64_t it;
-    while (next_pair(W.queue, n_pairs, lane, it)) {
-        const int32_t k = order[it];
+    const int32_t n_items = W.queue[1];
+    int32_t it;
+    while (next_item(W.queue, n_items, lane, it)) {
+        const SoftItem I = W.items[it];
+        const int32_t k = order[I.pos];
         const PairGeom g = geom[k];
         ctx_for_pair(C, g, k, src, tgt, counts, gold, W);
-        if (C.N > 0 && C.M > 0) {
-            float *ckv = W.ckv + g.soft_off;
-            float *vlast = ckv + (int64_t)(C.nstrips - 1) * C.M;  // the last strip writes no checkpoint
-            for (int s = 0; s < C.nstrips; ++s)
-                soft_fwd_strip<false, false>(C, s, s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr, nullptr,
-                                             s + 1 < C.nstrips ? ckv + (int64_t)s * C.M : nullptr, nullptr, sbuf,
-                                             s + 1 == C.nstrips ? vlast : nullptr);
-            float *qrow = W.qrow + g.soft_off;
-            for (int s = C.nstrips - 1; s >= 0; --s) {
-                soft_fwd_strip<false, true>(C, s, s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr, nullptr, nullptr,
-                                            nullptr, sbuf, nullptr);
+        C.failed = false;
+        if (C.N <= 0 || C.M <= 0) continue;
+        const int S = C.nstrips;
+        float *ckv = W.ckv + g.soft_off;
+        float *vlast = ckv + (int64_t)(S - 1) * C.M;  // the last strip writes no checkpoint
+        float *qrow = W.qrow + g.soft_off;
+        auto top = [&](int s) { return s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr; };
+        if (I.kind == 0) {
+            for (int s = 0; s < S; ++s)
+                soft_fwd_strip<false, false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
+                                             nullptr, sbuf, s + 1 == S ? vlast : nullptr);
+            for (int s = S - 1; s >= 0; --s) {
+                soft_fwd_strip<false, true>(C, s, top(s), nullptr, nullptr, nullptr, sbuf, nullptr);
                 soft_rev_strip<false>(C, s, sbuf, qrow, nullptr, 0.0f);
+            }
+        } else {
+            const int s = I.strip;
+            int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
+            if (I.kind == 1) {
+                soft_fwd_strip<false, false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
+                                             nullptr, sbuf, s + 1 == S ? vlast : nullptr,
+                                             s > 0 ? p1 + s - 1 : nullptr, p1 + s);
+            } else {
+                soft_fwd_strip<false, true>(C, s, top(s), nullptr, nullptr, nullptr, sbuf, nullptr,
+                                            s > 0 ? p1 + s - 1 : nullptr, nullptr);
+                soft_rev_strip<false>(C, s, sbuf, qrow, nullptr, 0.0f, s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
             }
         }
     }
 }
 
 // Sweep 3 (value + tangent, checkpoints) + sweep 4 (adjoint and its tangent):
-// H u for every cell, written over u.
+// H u for every cell, written over u.  Same work list as the forward.
 __global__ void __launch_bounds__(32 * kSoftWarps)
 soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                     int64_t n_pairs, DevParams P, SoftArgs A, const uint8_t *__restrict__ counts,
-                     const uint8_t *__restrict__ gold, SoftScratch W) {
+                     DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
+                     SoftScratch W) {
     extern __shared__ __align__(16) unsigned char soft_smem[];
     SoftCtx C = make_ctx(P, A);
     bind_smem(C, soft_smem);
@@ -419,48 +474,188 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     float *sbuf = W.sbuf + gw * W.sbuf_stride;
     const float rgamma = 1.0f / A.gamma;
-    int64_t it;
-    while (next_pair(W.queue, n_pairs, lane, it)) {
-        const int32_t k = order[it];
+    const int32_t n_items = W.queue[1];
+    int32_t it;
+    while (next_item(W.queue, n_items, lane, it)) {
+        const SoftItem I = W.items[it];
+        const int32_t k = order[I.pos];
         const PairGeom g = geom[k];
         ctx_for_pair(C, g, k, src, tgt, counts, gold, W);
-        if (C.N > 0 && C.M > 0) {
-            float *ckv = W.ckv + g.soft_off;
-            float *ckt = W.ckt + g.soft_off;
-            float *qrow = W.qrow + g.soft_off;
-            float *qtrow = W.qtrow + g.soft_off;
-            for (int s = 0; s + 1 < C.nstrips; ++s)
-                soft_fwd_strip<true, false>(C, s, s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr,
-                                            s > 0 ? ckt + (int64_t)(s - 1) * C.M : nullptr, ckv + (int64_t)s * C.M,
-                                            ckt + (int64_t)s * C.M, sbuf, nullptr);
-            for (int s = C.nstrips - 1; s >= 0; --s) {
-                soft_fwd_strip<true, true>(C, s, s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr,
-                                           s > 0 ? ckt + (int64_t)(s - 1) * C.M : nullptr, nullptr, nullptr, sbuf,
-                                           nullptr);
+        C.failed = false;
+        if (C.N <= 0 || C.M <= 0) continue;
+        const int S = C.nstrips;
+        float *ckv = W.ckv + g.soft_off;
+        float *ckt = W.ckt + g.soft_off;
+        float *qrow = W.qrow + g.soft_off;
+        float *qtrow = W.qtrow + g.soft_off;
+        auto topv = [&](int s) { return s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr; };
+        auto topt = [&](int s) { return s > 0 ? ckt + (int64_t)(s - 1) * C.M : nullptr; };
+        if (I.kind == 0) {
+            for (int s = 0; s + 1 < S; ++s)
+                soft_fwd_strip<true, false>(C, s, topv(s), topt(s), ckv + (int64_t)s * C.M, ckt + (int64_t)s * C.M,
+                                            sbuf, nullptr);
+            for (int s = S - 1; s >= 0; --s) {
+                soft_fwd_strip<true, true>(C, s, topv(s), topt(s), nullptr, nullptr, sbuf, nullptr);
                 soft_rev_strip<true>(C, s, sbuf, qrow, qtrow, rgamma);
+            }
+        } else {
+            const int s = I.strip;
+            int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
+            if (I.kind == 1) {
+                if (s + 1 < S)  // the last strip's checkpoint is not needed
+                    soft_fwd_strip<true, false>(C, s, topv(s), topt(s), ckv + (int64_t)s * C.M,
+                                                ckt + (int64_t)s * C.M, sbuf, nullptr, s > 0 ? p1 + s - 1 : nullptr,
+                                                p1 + s);
+            } else {
+                soft_fwd_strip<true, true>(C, s, topv(s), topt(s), nullptr, nullptr, sbuf, nullptr,
+                                           s > 0 ? p1 + s - 1 : nullptr, nullptr);
+                soft_rev_strip<true>(C, s, sbuf, qrow, qtrow, rgamma, s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
             }
         }
     }
 }
 
-// Per-cell work of the loss: gate, clamped P and BCE (summed per pair), or
+// Exclusive prefix sum over the block (blockDim.x a multiple of 32, at most
+// 1024); total receives the block's sum.
+__device__ int64_t block_scan(int64_t v, int64_t &total) {
+    __shared__ int64_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    const int64_t base = wid > 0 ? ws[wid - 1] : 0;
+    total = ws[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// Work lists of one sweep (one block).  A listed pair of S >= 2 strips is
+// split when its serial chain S (M + 32) exceeds the mean chain per warp
+// (split = 1; every such pair with split = 2, none with split = 0).  Split
+// pairs come first, each as S value-sweep items (top-down) followed by S
+// adjoint items (bottom-up), then the whole pairs in list order.  Every
+// listed pair also gets ceil(cells / kSoftChunk) (at least one) chunks of
+// per-cell work.  Zeroes the progress counters and the work counter.
+__global__ void __launch_bounds__(1024)
+soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs,
+                  int64_t n_warps, int split, uint32_t *status, SoftScratch W) {
+    auto strips = [&](int64_t pos, int32_t &n, int32_t &m) {
+        const PairGeom g = geom[order[pos]];
+        n = g.n;
+        m = g.m;
+        return (int64_t)((g.n + 31) >> 5);
+    };
+    int64_t tot = 0, chain = 0;
+    for (int64_t pos = threadIdx.x; pos < n_pairs; pos += blockDim.x) {
+        int32_t n, m;
+        const int64_t S = strips(pos, n, m);
+        chain += S * (m + 32);
+    }
+    (void)block_scan(chain, tot);
+    const int64_t thr = split == 2 ? 0 : (split == 1 ? tot / (n_warps > 0 ? n_warps : 1) : INT64_MAX);
+    auto counts = [&](int64_t pos, int64_t &si, int64_t &sc, int64_t &wi, int64_t &ch) {
+        int32_t n, m;
+        const int64_t S = strips(pos, n, m);
+        const bool sp = S >= 2 && m > 0 && S * (m + 32) > thr;
+        si = sp ? 2 * S : 0;
+        sc = sp ? S : 0;
+        wi = sp ? 0 : 1;
+        const int64_t cells = (int64_t)n * m;
+        ch = cells > 0 ? (cells + kSoftChunk - 1) / kSoftChunk : 1;
+    };
+    // totals, checked against the workspace
+    int64_t a[4] = {0, 0, 0, 0};
+    for (int64_t pos = threadIdx.x; pos < n_pairs; pos += blockDim.x) {
+        int64_t si, sc, wi, ch;
+        counts(pos, si, sc, wi, ch);
+        a[0] += si;
+        a[1] += sc;
+        a[2] += wi;
+        a[3] += ch;
+    }
+    int64_t T[4];
+    for (int q = 0; q < 4; ++q) (void)block_scan(a[q], T[q]);
+    const bool fits = T[0] + T[2] <= W.items_cap && T[1] <= W.ctr_cap && T[3] <= W.chunks_cap;
+    if (!fits) {
+        if (threadIdx.x == 0) {
+            atomicOr(status, kStBadList);
+            W.queue[0] = 0;
+            W.queue[1] = 0;
+            W.queue[2] = 0;
+        }
+        return;
+    }
+    int64_t c_si = 0, c_sc = 0, c_wi = 0, c_ch = 0;
+    for (int64_t base = 0; base < n_pairs; base += blockDim.x) {
+        const int64_t pos = base + threadIdx.x;
+        int64_t si = 0, sc = 0, wi = 0, ch = 0;
+        if (pos < n_pairs) counts(pos, si, sc, wi, ch);
+        int64_t t0, t1, t2, t3;
+        const int64_t o_si = c_si + block_scan(si, t0);
+        const int64_t o_sc = c_sc + block_scan(sc, t1);
+        const int64_t o_wi = c_wi + block_scan(wi, t2);
+        const int64_t o_ch = c_ch + block_scan(ch, t3);
+        c_si += t0;
+        c_sc += t1;
+        c_wi += t2;
+        c_ch += t3;
+        if (pos >= n_pairs) continue;
+        if (si) {
+            const int32_t S = (int32_t)sc;
+            for (int32_t s = 0; s < S; ++s) {
+                W.items[o_si + s] = SoftItem{(int32_t)pos, s, 1, (int32_t)o_sc};
+                W.items[o_si + 2 * S - 1 - s] = SoftItem{(int32_t)pos, s, 2, (int32_t)o_sc};
+                W.prog1[o_sc + s] = 0;
+                W.prog2[o_sc + s] = 0;
+            }
+        } else {
+            W.items[T[0] + o_wi] = SoftItem{(int32_t)pos, 0, 0, 0};
+        }
+        for (int64_t c = 0; c < ch; ++c) W.chunks[o_ch + c] = SoftChunk{(int32_t)pos, 0, c * kSoftChunk};
+    }
+    if (threadIdx.x == 0) {
+        W.queue[0] = 0;
+        W.queue[1] = (int32_t)(T[0] + T[2]);
+        W.queue[2] = (int32_t)T[3];
+    }
+}
+
+// Per-cell work of the loss: gate, clamped P and BCE (summed per chunk), or
 // (WANT_U) the tangent direction u = dL/dE of the backward.  One block per
-// listed pair.
+// chunk of kSoftChunk cells; the first chunk of a pair also sums V(N,M).
 template <bool WANT_U>
 __global__ void __launch_bounds__(256)
 soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                 int64_t n_pairs, DevParams P, SoftArgs A, const uint8_t *__restrict__ counts,
-                 const uint8_t *__restrict__ gold, SoftScratch W) {
+                 DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
+                 SoftScratch W) {
     __shared__ double red[256];
     __shared__ double vred[256];
     SoftCtx C = make_ctx(P, A);
-    for (int64_t it = blockIdx.x; it < n_pairs; it += gridDim.x) {
-        const int32_t k = order[it];
+    const int32_t n_chunks = W.queue[2];
+    for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
+        const SoftChunk ch = W.chunks[x];
+        const int32_t k = order[ch.pos];
         const PairGeom g = geom[k];
         const int64_t sb = src.doc[k], tb = tgt.doc[k];
         const int64_t cells = (int64_t)g.n * g.m;
-        double acc = 0.0;
-        for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
+        float acc = 0.0f;  // at most kSoftChunk / 256 terms per thread
+        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x) {
             const int i = (int)(c / g.m), j = (int)(c - (int64_t)i * g.m);
             const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + c];
             const float sv = similarity(q.x, q.y, sim_row((int)(src.sent[sb + i + 1] - src.sent[sb + i]), P),
@@ -470,16 +665,16 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
             if (WANT_U)
                 W.U[g.cell_off + c] = __fmul_rn(lp, G);
             else
-                acc += (double)bce;
+                acc = __fadd_rn(acc, bce);
         }
         if (WANT_U) continue;
         // V(N,M) = -N p + sum_j (DOWN output of row N-1 at column j + p)
         double vs = 0.0;
-        if (g.n > 0 && g.m > 0) {
+        if (ch.c0 == 0 && g.n > 0 && g.m > 0) {
             const float *vlast = W.ckv + g.soft_off + (int64_t)((g.n + 31) / 32 - 1) * g.m;
             for (int j = threadIdx.x; j < g.m; j += blockDim.x) vs += (double)vlast[j] + (double)P.gap;
         }
-        red[threadIdx.x] = acc;
+        red[threadIdx.x] = (double)acc;
         vred[threadIdx.x] = vs;
         __syncthreads();
         for (int off = 128; off > 0; off >>= 1) {
@@ -490,29 +685,33 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            W.partial[it * kSoftSlots + 0] = red[0];
-            W.partial[it * kSoftSlots + 1] = (g.n > 0 && g.m > 0) ? vred[0] - (double)P.gap * (double)g.n
-                                                                  : -(double)P.gap * (double)(g.n + g.m);
+            W.partial[(int64_t)x * kSoftSlots] = red[0];
+            if (ch.c0 == 0)
+                W.vpart[ch.pos] = (g.n > 0 && g.m > 0) ? vred[0] - (double)P.gap * (double)g.n
+                                                       : -(double)P.gap * (double)(g.n + g.m);
         }
         __syncthreads();
     }
 }
 
 // Per-cell chain rule: dL/ds = H u + dL/dP E dG/ds, then to w, b (through
-// s(1-s) f), gap (2 H u) and thr (-dL/dP E dG/ds).  One block per listed pair.
+// s(1-s) f), gap (2 H u) and thr (-dL/dP E dG/ds).  One block per chunk.
 __global__ void __launch_bounds__(256)
 soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                  int64_t n_pairs, DevParams P, SoftArgs A, const uint8_t *__restrict__ counts,
-                  const uint8_t *__restrict__ gold, SoftScratch W, float *__restrict__ hvp) {
+                  DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
+                  SoftScratch W, float *__restrict__ hvp) {
     __shared__ double red[7][256];
     SoftCtx C = make_ctx(P, A);
-    for (int64_t it = blockIdx.x; it < n_pairs; it += gridDim.x) {
-        const int32_t k = order[it];
+    const int32_t n_chunks = W.queue[2];
+    for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
+        const SoftChunk ch = W.chunks[x];
+        const int32_t k = order[ch.pos];
         const PairGeom g = geom[k];
         const int64_t sb = src.doc[k], tb = tgt.doc[k];
         const int64_t cells = (int64_t)g.n * g.m;
-        double gr[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
+        float gr[7] = {0, 0, 0, 0, 0, 0, 0};  // at most kSoftChunk / 256 terms per thread
+        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x) {
             const int i = (int)(c / g.m), j = (int)(c - (int64_t)i * g.m);
             const int ls = (int)(src.sent[sb + i + 1] - src.sent[sb + i]);
             const int lt = (int)(tgt.sent[tb + j + 1] - tgt.sent[tb + j]);
@@ -530,13 +729,13 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
             float f[4];
             features(q.x, q.y, ls, lt, f);
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) gr[q4] += (double)dz * (double)f[q4];
-            gr[4] += (double)dz;
-            gr[5] += 2.0 * (double)Hu;
-            gr[6] -= (double)direct;
+            for (int q4 = 0; q4 < 4; ++q4) gr[q4] = __fmaf_rn(dz, f[q4], gr[q4]);
+            gr[4] = __fadd_rn(gr[4], dz);
+            gr[5] = __fmaf_rn(2.0f, Hu, gr[5]);
+            gr[6] = __fsub_rn(gr[6], direct);
         }
 #pragma unroll
-        for (int q7 = 0; q7 < 7; ++q7) red[q7][threadIdx.x] = gr[q7];
+        for (int q7 = 0; q7 < 7; ++q7) red[q7][threadIdx.x] = (double)gr[q7];
         __syncthreads();
         for (int off = 128; off > 0; off >>= 1) {
             if ((int)threadIdx.x < off)
@@ -544,19 +743,20 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
                 for (int q7 = 0; q7 < 7; ++q7) red[q7][threadIdx.x] += red[q7][threadIdx.x + off];
             __syncthreads();
         }
-        if (threadIdx.x < 7) W.partial[it * kSoftSlots + 2 + threadIdx.x] = red[threadIdx.x][0];
+        if (threadIdx.x < 7) W.partial[(int64_t)x * kSoftSlots + 1 + threadIdx.x] = red[threadIdx.x][0];
         __syncthreads();
     }
 }
 
-// Fixed-order reduction of the per-pair partials (one block).
+// Fixed-order reduction of the per-chunk partials (one block).
 __global__ void __launch_bounds__(256)
-soft_reduce_kernel(const double *__restrict__ partial, int64_t n_pairs, int first, int count, float scale,
-                   float *__restrict__ out) {
+soft_reduce_kernel(const double *__restrict__ partial, const int32_t *__restrict__ queue, int first, int count,
+                   float scale, float *__restrict__ out) {
     __shared__ double red[256];
+    const int64_t n = queue[2];
     for (int q = 0; q < count; ++q) {
         double v = 0.0;
-        for (int64_t k = threadIdx.x; k < n_pairs; k += 256) v += partial[k * kSoftSlots + first + q];
+        for (int64_t k = threadIdx.x; k < n; k += 256) v += partial[k * kSoftSlots + first + q];
         red[threadIdx.x] = v;
         __syncthreads();
         for (int off = 128; off > 0; off >>= 1) {
@@ -568,11 +768,11 @@ soft_reduce_kernel(const double *__restrict__ partial, int64_t n_pairs, int firs
     }
 }
 
-__global__ void copy_values_kernel(const double *__restrict__ partial, const int32_t *__restrict__ order,
+__global__ void copy_values_kernel(const double *__restrict__ vpart, const int32_t *__restrict__ order,
                                    int64_t n_pairs, float *__restrict__ value) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_pairs; x += stride)
-        value[order[x]] = (float)partial[x * kSoftSlots + 1];
+        value[order[x]] = (float)vpart[x];
 }
 
 int soft_grid(int n_sms) { return n_sms * 3; }
@@ -586,25 +786,26 @@ static cudaError_t set_soft_smem(const void *kern) {
                                 (int)(sizeof(SoftSmem) * kSoftWarps));
 }
 
+static void launch_soft_items(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const SoftArgs &A,
+                              const SoftScratch &W, int n_sms, cudaStream_t st) {
+    soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.status, W);
+}
+
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                                 const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
                                 const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float *loss,
                                 float *value, int n_sms, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(W.queue, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
+    launch_soft_items(geom, order, n_pairs, A, W, n_sms, st);
     if (n_pairs > 0) {
-        e = set_soft_smem((const void *)soft_forward_kernel);
+        cudaError_t e = set_soft_smem((const void *)soft_forward_kernel);
         if (e != cudaSuccess) return e;
         soft_forward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmem) * kSoftWarps, st>>>(
-            src, tgt, geom, order, n_pairs, P, A, counts, gold, W);
-        const int64_t nb = n_pairs < (int64_t)n_sms * 16 ? n_pairs : (int64_t)n_sms * 16;
-        soft_loss_kernel<false><<<(unsigned)nb, 256, 0, st>>>(src, tgt, geom, order, n_pairs, P, A, counts, gold, W);
+            src, tgt, geom, order, P, A, counts, gold, W);
+        soft_loss_kernel<false><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, n_pairs, 0, 1, A.inv_cells, loss);
+    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, W.queue, 0, 1, A.inv_cells, loss);
     if (value && n_pairs > 0)
-        copy_values_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(W.partial, order, n_pairs, value);
+        copy_values_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(W.vpart, order, n_pairs, value);
     return cudaGetLastError();
 }
 
@@ -612,21 +813,16 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
                                  const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
                                  const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float dloss,
                                  float *grad, float *hvp, int n_sms, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(W.queue, 0, sizeof(int32_t), st);
-    if (e != cudaSuccess) return e;
+    launch_soft_items(geom, order, n_pairs, A, W, n_sms, st);
     if (n_pairs > 0) {
-        e = set_soft_smem((const void *)soft_backward_kernel);
+        cudaError_t e = set_soft_smem((const void *)soft_backward_kernel);
         if (e != cudaSuccess) return e;
-        const int64_t nbu = n_pairs < (int64_t)n_sms * 16 ? n_pairs : (int64_t)n_sms * 16;
-        soft_loss_kernel<true><<<(unsigned)nbu, 256, 0, st>>>(src, tgt, geom, order, n_pairs, P, A, counts, gold, W);
+        soft_loss_kernel<true><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
         soft_backward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmem) * kSoftWarps, st>>>(
-            src, tgt, geom, order, n_pairs, P, A, counts, gold, W);
-        const int64_t nb = n_pairs < (int64_t)n_sms * 16 ? n_pairs : (int64_t)n_sms * 16;
-        soft_chain_kernel<<<(unsigned)nb, 256, 0, st>>>(src, tgt, geom, order, n_pairs, P, A, counts, gold, W, hvp);
+            src, tgt, geom, order, P, A, counts, gold, W);
+        soft_chain_kernel<<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W, hvp);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, n_pairs, 2, 7, dloss, grad);
+    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, W.queue, 1, 7, dloss, grad);
     return cudaGetLastError();
 }
 
