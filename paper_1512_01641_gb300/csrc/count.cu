@@ -171,25 +171,32 @@ count_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restr
 }
 
 // ---------------------------------------------------------------------------
-// Strip kernel: one warp owns the rows of a 32-row strip (or a row group of
-// it) and sweeps all 32-column blocks of the pair.  Once per strip a
-// shared-memory hash table is built over the dictionary translations of the
-// strip's source positions:  RT[t] = mask of the rows i with t in T_i.  Every
-// source position keeps the table slots of its translations.  Per block:
-//   column pass: every target token of the block looks itself up in RT; a hit
-//     records RT[t] (which rows' translation sets contain it) and sets the
-//     token's column bit in the slot's column mask;
-//   mt: lane j adds the recorded row masks of column j's tokens into
-//     bit-sliced counters (mt of 32 rows at once);
-//   row pass: every source position ORs the column masks of its translations
-//     (bit j: the position has a translation in target sentence j);
-//   ms: lane i adds the masks of row i's positions into bit-sliced counters
-//     (ms of 32 columns at once).
-// The table build, the column pass and the row pass are spread over the 32
-// lanes token by token (position by position), so no lane waits for the
-// longest sentence; only the two accumulations run one row (column) per lane.
+// Strip kernel: one CTA of four warps owns the rows of a 32-row strip (or a
+// row group of it) and sweeps all 32-column blocks of the pair.  Once per
+// strip a shared-memory hash table is built over the dictionary translations
+// of the strip's source positions:  RT[t] = mask of the rows i with t in T_i;
+// every translation entry is kept as (table slot, source position).  The
+// four warps then work on one 32 x 32 block at a time:
+//   column pass (all threads, token by token): every target token of the
+//     block looks itself up in RT; a hit records RT[t] (which rows'
+//     translation sets contain it) and sets the token's column bit in the
+//     slot's column mask;
+//   then, side by side: warp 0 adds column j's recorded row masks into
+//     bit-sliced counters (mt of 32 rows at once, lane = column), while
+//     warps 1-3 OR the column mask of every entry's slot into the entry's
+//     position word (bit j: the position has a translation in sentence j;
+//     most masks are 0, so few atomics);
+//   then warp 1 adds row i's position words into bit-sliced counters (ms of
+//     32 columns at once, lane = row) and clears them, warps 2-3 clear the
+//     column masks, and warp 0 stages the next block's target tokens (bulk
+//     async copy) so that the copy overlaps the rest of this block;
+//   finally all threads write the (ms, mt) bytes of the block, transposed
+//     through shared memory, one coalesced row at a time.
 // Counters are carry-save (four words per step), bytes are expanded by
-// multiply-spread and transposed through shared memory for coalesced writes.
+// multiply-spread.  One table per CTA serves four warps, so an SM holds five
+// CTAs (20 warps) where a table per warp allowed six warps.
+constexpr int kStripWarps = 4;
+constexpr int kStripThreads = 32 * kStripWarps;
 constexpr int kEntCap = 1440;  // translation entries of one row group
 constexpr int kPosCap = 992;   // source positions per strip item (32 rows x 31 tokens)
 constexpr int kTokCap = 992;   // target tokens per column block (32 sentences x 31 tokens)
@@ -202,69 +209,80 @@ struct alignas(16) StripSmem {
     int32_t key[S];
     uint32_t rowmask[S];
     uint32_t colmask[S];
-    // staged tokens (the strip's source tokens, then each block's target
-    // tokens, replaced in place by their row masks), then the positions'
-    // column masks, then the byte tiles
-    uint32_t gh[kTokCap + 8];
-    uint16_t ent[kEntCap];
-    uint16_t pos_off[kPosCap + 2];
+    uint32_t gh[kTokCap + 8];  // staged tokens: the strip's source tokens, then each block's target tokens
+                               // (replaced in place by their row masks)
+    uint32_t hpos[kPosCap];    // per source position: column mask of the current block
+    uint32_t ent[kEntCap];     // per translation entry: table slot | position << 16
+    uint8_t ms_t[32][kPad];    // [row][col]
+    uint8_t mt_t[32][kPad];    // [col][row]
     uint8_t colid[kTokCap];
     uint8_t rowid[kPosCap];
-    int32_t n_keys;  // distinct keys of the row table being built
-    int32_t pad2[3];
+    int32_t ctpre[33];         // per column of the staged block: first token index; [32] = token count
+    int32_t n_keys;            // distinct keys of the row table being built
+    int32_t n_ent;             // translation entries of the row table
+    int32_t full;              // the row group does not fit
+    int32_t tsh;               // index in gh of the staged block's first token
+    int32_t pad2[2];
 };
-static_assert(kTokCap >= kPosCap && kTokCap * 4 >= 2 * 32 * kPad, "shared buffer sizes");
+static_assert(kTokCap >= kPosCap, "shared buffer sizes");
 static_assert(offsetof(StripSmem<11>, gh) % 16 == 0 && sizeof(StripSmem<11>) % 16 == 0, "bulk copy alignment");
 constexpr int64_t kBulkWaitLimit = 1 << 22;
 
-// Stage tokens [a, a+n) of `tok` into buf; returns the index of token a in
-// buf.  A bulk copy moves the 16-byte-aligned cover of the range when the array
-// allows it, plain loads otherwise.  On a copy that never completes the status
-// is flagged and ok is cleared (the caller stops).
-__device__ __forceinline__ int stage_tokens(const int32_t *__restrict__ tok, int64_t n_total, int64_t a, int n,
-                                            uint32_t *buf, uint64_t *bar, uint32_t &phase, bool bulk_ok, int lane,
-                                            uint32_t *status, bool &ok) {
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Start staging tokens [a, a+n) of `tok` into buf (called by one warp):
+// returns the index of token a in buf.  A bulk copy moves the 16-byte-aligned
+// cover of the range when the array allows it (bulk = true, completes on
+// bar); otherwise the warp copies with plain loads.
+__device__ __forceinline__ int stage_issue(const int32_t *__restrict__ tok, int64_t n_total, int64_t a, int n,
+                                           uint32_t *buf, uint64_t *bar, bool bulk_ok, int lane, bool &bulk) {
     const int64_t a16 = a & ~3LL, b16 = (a + n + 3) & ~3LL;
     const int shift = (int)(a - a16);
-    __syncwarp();
-    if (bulk_ok && n > 0 && b16 <= n_total) {
+    bulk = bulk_ok && n > 0 && b16 <= n_total;
+    if (bulk) {
         if (lane == 0) bulk_copy_g2s(buf, tok + a16, (uint32_t)((b16 - a16) * 4), bar);
-        ok = mbar_wait(bar, phase, kBulkWaitLimit);
-        phase ^= 1u;
-        if (!ok) {
-            if (lane == 0) atomicOr(status, kStTimeout);
-            (void)mbar_wait(bar, phase ^ 1u, kBulkWaitLimit);  // let the copy in flight land
-        }
     } else {
         for (int x = lane; x < n; x += 32) buf[shift + x] = (uint32_t)tok[a + x];
-        ok = true;
     }
-    __syncwarp();
     return shift;
 }
 
-// Carry-save accumulation of 0/1 words into bit-sliced counters, four at a time.
+// All threads: wait for the staged copy (if any), agreeing on the outcome.  On
+// a copy that never completes the status is flagged and false is returned
+// (after a second bounded wait that lets the copy in flight land).
+__device__ __forceinline__ bool stage_wait(bool bulk, uint64_t *bar, uint32_t &phase, uint32_t *status) {
+    bool ok = true;
+    if (bulk) {
+        ok = mbar_wait(bar, phase, kBulkWaitLimit);
+        if (!ok) (void)mbar_wait(bar, phase, kBulkWaitLimit);
+        phase ^= 1u;
+    }
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
+    return ok;
+}
+
+// Adds n 0/1 words from shared memory into the counters, four per step.
 template <int K>
-struct Acc4 {
-    BitCounter<K> c;
-    uint32_t b0 = 0, b1 = 0, b2 = 0;
-    int n = 0;
-    __device__ __forceinline__ void add(uint32_t x) {
-        if (n == 3) {
-            c.add4(b0, b1, b2, x);
-            n = 0;
-        } else {
-            b2 = b1;
-            b1 = b0;
-            b0 = x;
-            ++n;
-        }
+__device__ __forceinline__ void acc_words(BitCounter<K> &c, const uint32_t *w, int n) {
+    int t = 0;
+    for (; t + 4 <= n; t += 4) c.add4(w[t], w[t + 1], w[t + 2], w[t + 3]);
+    if (t < n) c.add4(w[t], t + 1 < n ? w[t + 1] : 0u, t + 2 < n ? w[t + 2] : 0u, 0u);
+}
+
+// As acc_words, and clears the words.
+template <int K>
+__device__ __forceinline__ void acc_words_clear(BitCounter<K> &c, uint32_t *w, int n) {
+    int t = 0;
+    for (; t + 4 <= n; t += 4) {
+        c.add4(w[t], w[t + 1], w[t + 2], w[t + 3]);
+        w[t] = w[t + 1] = w[t + 2] = w[t + 3] = 0u;
     }
-    __device__ __forceinline__ void finish() {
-        if (n > 0) c.add4(b0, n > 1 ? b1 : 0u, n > 2 ? b2 : 0u, 0u);
-        n = 0;
+    for (; t < n; ++t) {
+        c.add(w[t]);
+        w[t] = 0u;
     }
-};
+}
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
     int x = v;
@@ -284,116 +302,153 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
 constexpr float kMaxLoad = 0.85f;
 
 template <int LOG_SLOTS, int K>
-__global__ void __launch_bounds__(32 * kCountWarps)
+__global__ void __launch_bounds__(kStripThreads)
 count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
                    const CountStripItem *__restrict__ items, int64_t n_items, bool bulk_ok,
                    uint8_t *__restrict__ counts, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Smem = StripSmem<LOG_SLOTS>;
     constexpr int S = Smem::S;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Smem &sm = reinterpret_cast<Smem *>(smem_raw)[warp];
-    if (lane == 0) mbar_init(&sm.bar);
-    __syncwarp();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    if (tid == 0) mbar_init(&sm.bar);
+    __syncthreads();
     uint32_t phase = 0;
-    uint8_t(*ms_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(sm.gh);
-    uint8_t(*mt_t)[kPad] = reinterpret_cast<uint8_t(*)[kPad]>(reinterpret_cast<uint8_t *>(sm.gh) + 32 * kPad);
 
-    for (int64_t it = (int64_t)blockIdx.x * kCountWarps + warp; it < n_items;
-         it += (int64_t)gridDim.x * kCountWarps) {
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const CountStripItem item = items[it];
         const PairGeom g = geom[item.pair];
         const int r0 = item.strip * 32;
         const int rend = min(item.r_hi, g.n - r0);
         const int64_t ssent0 = src.doc[item.pair] + r0;
+        const int64_t tdoc = tgt.doc[item.pair];
+        const int nblk = (g.m + 31) >> 5;
+        uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m);
         int group = 32;
         for (int g_lo = item.r_lo; g_lo < rend;) {
             const int g_hi = min(g_lo + group, rend);
             const bool rv = lane >= g_lo && lane < g_hi;
             // source positions of the group's rows, flattened (rows are
-            // consecutive sentences, so their tokens are contiguous)
+            // consecutive sentences, so their tokens are contiguous); every
+            // warp scans the 32 row lengths for itself
             const int my_len = rv ? (int)(src.sent[ssent0 + lane + 1] - src.sent[ssent0 + lane]) : 0;
             int n_pos;
             const int prow = warp_excl_scan(my_len, lane, n_pos);
             const int64_t ptok0 = src.sent[ssent0 + g_lo];
-            for (int x = lane; x < S; x += 32) {
+            for (int x = tid; x < S; x += kStripThreads) {
                 sm.key[x] = kEmpty;
                 sm.rowmask[x] = 0u;
                 sm.colmask[x] = 0u;
             }
-            if (lane == 0) sm.n_keys = 0;
-            for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
-            bool ok;
-            const int32_t *stok = reinterpret_cast<const int32_t *>(sm.gh) +
-                                  stage_tokens(src.tok, src.n_tok, ptok0, n_pos, sm.gh, &sm.bar, phase, bulk_ok, lane,
-                                               status, ok);
-            if (!ok) return;
-            // translation entry offsets of the positions
-            int carry = 0;
-            for (int base = 0; base < n_pos; base += 32) {
-                const int p = base + lane;
-                int f = 0;
+            for (int x = tid; x < n_pos; x += kStripThreads) sm.hpos[x] = 0u;
+            if (tid == 0) {
+                sm.n_keys = 0;
+                sm.n_ent = 0;
+                sm.full = 0;
+            }
+            if (warp == 0)
+                for (int t = 0; t < my_len; ++t) sm.rowid[prow + t] = (uint8_t)lane;
+            fence_proxy_async();
+            __syncthreads();
+            bool bulk = false;
+            int ssh = 0;
+            if (warp == 0) ssh = stage_issue(src.tok, src.n_tok, ptok0, n_pos, sm.gh, &sm.bar, bulk_ok, lane, bulk);
+            if (tid == 0) sm.tsh = ssh | (bulk ? 1 << 30 : 0);  // for every warp
+            __syncthreads();
+            bulk = (sm.tsh >> 30) & 1;
+            ssh = sm.tsh & ((1 << 30) - 1);
+            if (!stage_wait(bulk, &sm.bar, phase, status)) return;
+            const int32_t *stok = reinterpret_cast<const int32_t *>(sm.gh) + ssh;
+            // row table: positions in rounds of 128; each warp takes its
+            // round's entry offsets with one shared atomic
+            for (int base = 0; base < n_pos; base += kStripThreads) {
+                const int p = base + tid;
+                int32_t e0 = 0, e1 = 0;
                 if (p < n_pos) {
                     const int32_t v = stok[p];
-                    f = dict.off[v + 1] - dict.off[v];
+                    e0 = dict.off[v];
+                    e1 = dict.off[v + 1];
                 }
                 int tot;
-                const int ex = warp_excl_scan(f, lane, tot);
-                if (p < n_pos) sm.pos_off[p] = (uint16_t)min(carry + ex, 0xFFFF);
-                carry += tot;
-            }
-            if (lane == 0) sm.pos_off[n_pos] = (uint16_t)min(carry, 0xFFFF);
-            // row table
-            bool full = carry > kEntCap;
-            __syncwarp();
-            if (!full) {
-                for (int p = lane; p < n_pos; p += 32) {
-                    const int32_t v = stok[p];
-                    const int32_t e0 = dict.off[v], e1 = dict.off[v + 1];
+                const int ex = warp_excl_scan(e1 - e0, lane, tot);
+                int o = 0;
+                if (lane == 0 && tot > 0) o = atomicAdd(&sm.n_ent, tot);
+                o = __shfl_sync(kFull, o, 0) + ex;
+                if (o + (e1 - e0) > kEntCap) {
+                    sm.full = 1;
+                    continue;
+                }
+                if (p < n_pos) {
                     const uint32_t rbit = 1u << sm.rowid[p];
-                    const int o = sm.pos_off[p];
                     for (int32_t e = e0; e < e1; ++e) {
                         int h;
                         const bool fresh = table_insert_new<LOG_SLOTS>(sm.key, dict.tgt[e], h);
                         if (h < 0) {
-                            sm.ent[o + (e - e0)] = 0;
+                            sm.full = 1;
+                            sm.ent[o + (e - e0)] = (uint32_t)p << 16;
                             continue;
                         }
                         if (fresh) atomicAdd(&sm.n_keys, 1);
                         atomicOr(&sm.rowmask[h], rbit);
-                        sm.ent[o + (e - e0)] = (uint16_t)h;
+                        sm.ent[o + (e - e0)] = (uint32_t)h | ((uint32_t)p << 16);
                     }
                 }
-                __syncwarp();
-                full = sm.n_keys > (int)(kMaxLoad * S);
             }
+            fence_proxy_async();  // the source tokens are read before a copy replaces them
+            __syncthreads();
+            const bool full = sm.full != 0 || sm.n_keys > (int)(kMaxLoad * S);
+            const int n_ent = min(sm.n_ent, kEntCap);
             if (full) {
+                __syncthreads();  // everyone has read the flags before the rebuild clears them
                 if (group == 1) {  // one row alone does not fit: give up on this item
-                    if (lane == 0) atomicOr(status, kStTableFull);
+                    if (tid == 0) atomicOr(status, kStTableFull);
                     break;
                 }
                 group >>= 1;
                 continue;
             }
 
-            const int nblk = (g.m + 31) >> 5;
-            const int64_t tdoc = tgt.doc[item.pair];
-            uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m);
+            // stage block jb's target tokens (warp 0): column ids and token
+            // offsets into shared memory, then the copy
+            int64_t nx_lo = 0, nx_hi = 0;  // warp 0: sentence offsets of the next block to stage
+            auto offsets = [&](int jb) {
+                const int c = 32 * jb + lane;
+                if (jb < nblk && c < g.m) {
+                    nx_lo = tgt.sent[tdoc + c];
+                    nx_hi = tgt.sent[tdoc + c + 1];
+                } else {
+                    nx_lo = nx_hi = 0;
+                }
+            };
+            auto stage_block = [&](int jb, bool &bulk_b) {
+                const int nc = min(32, g.m - 32 * jb);
+                const int my_lt = lane < nc ? (int)(nx_hi - nx_lo) : 0;
+                const int64_t ttok0 = __shfl_sync(kFull, nx_lo, 0);
+                int n_tok;
+                const int tpre = warp_excl_scan(my_lt, lane, n_tok);
+                sm.ctpre[lane] = tpre;
+                if (lane == 0) sm.ctpre[32] = n_tok;
+                for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
+                const int sh = stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, bulk_ok, lane, bulk_b);
+                if (lane == 0) sm.tsh = sh | (bulk_b ? 1 << 30 : 0);
+            };
+            if (warp == 0) {
+                bool b;
+                offsets(0);
+                stage_block(0, b);
+                offsets(1);
+            }
+            __syncthreads();  // block 0's ctpre, colid, tsh; later blocks are staged before the
+                              // barrier that ends the previous block's ms phase
             for (int jb = 0; jb < nblk; ++jb) {
                 const int c0 = jb * 32;
                 const int nc = min(32, g.m - c0);
-                const int64_t ts = tdoc + c0;
-                const int my_lt = lane < nc ? (int)(tgt.sent[ts + lane + 1] - tgt.sent[ts + lane]) : 0;
-                int n_tok;
-                const int tpre = warp_excl_scan(my_lt, lane, n_tok);
-                const int64_t ttok0 = tgt.sent[ts];
-                for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
-                const int tsh = stage_tokens(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, phase, bulk_ok, lane,
-                                             status, ok);
-                if (!ok) return;
+                const int tshw = sm.tsh;
+                if (!stage_wait((tshw >> 30) & 1, &sm.bar, phase, status)) return;
+                const int n_tok = sm.ctpre[32];
+                uint32_t *tg = sm.gh + (tshw & ((1 << 30) - 1));
                 // column pass (each token's row mask replaces it in place)
-                uint32_t *tg = sm.gh + tsh;
-                for (int x = lane; x < n_tok; x += 32) {
+                for (int x = tid; x < n_tok; x += kStripThreads) {
                     const int slot = table_find<LOG_SLOTS>(sm.key, (int32_t)tg[x]);
                     uint32_t rm = 0u;
                     if (slot >= 0) {
@@ -402,43 +457,58 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                     }
                     tg[x] = rm;
                 }
-                __syncwarp();
-                Acc4<K> mt;
-                mt.c.clear();
-                for (int t = 0; t < my_lt; ++t) mt.add(tg[tpre + t]);
-                mt.finish();
-                __syncwarp();
-                // row pass
-                for (int p = lane; p < n_pos; p += 32) {
-                    uint32_t h = 0u;
-                    const int e1 = sm.pos_off[p + 1];
-                    for (int e = sm.pos_off[p]; e < e1; ++e) h |= sm.colmask[sm.ent[e]];
-                    sm.gh[p] = h;
-                }
-                __syncwarp();
-                Acc4<K> ms;
-                ms.c.clear();
-                for (int t = 0; t < my_len; ++t) ms.add(sm.gh[prow + t]);
-                ms.finish();
-                __syncwarp();
-                for (int x = lane; x < S / 4; x += 32) reinterpret_cast<uint4 *>(sm.colmask)[x] = make_uint4(0, 0, 0, 0);
-                // expand, transpose, write
-                uint32_t w[8];
-                ms.c.to_bytes(w);
+                __syncthreads();
+                if (warp == 0) {
+                    // mt of 32 rows for column `lane`
+                    BitCounter<K> mt;
+                    mt.clear();
+                    const int t0 = sm.ctpre[lane];
+                    acc_words(mt, tg + t0, lane < nc ? (lane < 31 ? sm.ctpre[lane + 1] : n_tok) - t0 : 0);
+                    uint32_t w[8];
+                    mt.to_bytes(w);
 #pragma unroll
-                for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&ms_t[lane][4 * m]) = w[m];
-                mt.c.to_bytes(w);
-#pragma unroll
-                for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&mt_t[lane][4 * m]) = w[m];
-                __syncwarp();
-                if (lane < nc) {
-                    for (int i = g_lo; i < g_hi; ++i) {
-                        const uchar2 v = make_uchar2(ms_t[i][lane], mt_t[lane][i]);
-                        reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[lane] = v;
+                    for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][4 * m]) = w[m];
+                } else {
+                    // row pass: entries' column masks into their positions' words
+#pragma unroll 4
+                    for (int e = tid - 32; e < n_ent; e += kStripThreads - 32) {
+                        const uint32_t en = sm.ent[e];
+                        const uint32_t cm = sm.colmask[en & 0xFFFFu];
+                        if (cm) atomicOr(&sm.hpos[en >> 16], cm);
                     }
                 }
-                __syncwarp();
+                fence_proxy_async();
+                __syncthreads();
+                if (warp == 1) {
+                    // ms of 32 columns for row `lane` (clears the position words)
+                    BitCounter<K> ms;
+                    ms.clear();
+                    acc_words_clear(ms, sm.hpos + prow, my_len);
+                    uint32_t w[8];
+                    ms.to_bytes(w);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&sm.ms_t[lane][4 * m]) = w[m];
+                } else if (warp == 0) {
+                    if (jb + 1 < nblk) {
+                        bool b;
+                        stage_block(jb + 1, b);
+                        offsets(jb + 2);
+                    }
+                } else {
+                    for (int x = tid - 64; x < S / 4; x += kStripThreads - 64)
+                        reinterpret_cast<uint4 *>(sm.colmask)[x] = make_uint4(0, 0, 0, 0);
+                }
+                __syncthreads();
+                // write the block's rows of the group
+                for (int x = tid; x < 32 * 32; x += kStripThreads) {
+                    const int i = x >> 5, c = x & 31;
+                    if (i >= g_lo && i < g_hi && c < nc) {
+                        const uchar2 v = make_uchar2(sm.ms_t[i][c], sm.mt_t[c][i]);
+                        reinterpret_cast<uchar2 *>(out_strip + 2 * ((int64_t)i * g.m + c0))[c] = v;
+                    }
+                }
             }
+            __syncthreads();  // the last block's tiles and tokens are read before the next group or item
             g_lo = g_hi;
         }
     }
@@ -448,18 +518,17 @@ template <int LOG_SLOTS, int K>
 cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                            const PairGeom *geom, const CountStripItem *items, int64_t n_items, bool bulk_ok,
                            uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st) {
-    const size_t smem = sizeof(StripSmem<LOG_SLOTS>) * kCountWarps;
+    const size_t smem = sizeof(StripSmem<LOG_SLOTS>);
     auto kern = count_strip_kernel<LOG_SLOTS, K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kCountWarps, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStripThreads, smem);
     if (e != cudaSuccess) return e;
-    int64_t want = (n_items + kCountWarps - 1) / kCountWarps;
     int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
-    int grid = (int)(want < cap ? want : cap);
+    int grid = (int)(n_items < cap ? n_items : cap);
     if (grid < 1) return cudaSuccess;
-    kern<<<grid, 32 * kCountWarps, smem, st>>>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status);
+    kern<<<grid, kStripThreads, smem, st>>>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status);
     return cudaGetLastError();
 }
 
