@@ -19,23 +19,51 @@ struct FillCtx {
     DevParams P;
 };
 
+// Values of the next block, loaded one block ahead so that their global
+// latency overlaps the current block's sweep.
+struct FillAhead {
+    float hv;  // UP candidate of the strip's first row at this lane's column
+    int lt;    // length of this lane's target sentence
+};
+
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Loads the look-ahead values of block jb and prefetches the lane's count
+// bytes of that block (64 bytes of its row) into L1.
+__device__ __forceinline__ void fill_ahead(const FillCtx &C, int jb, int nb, bool first_strip,
+                                           const float *__restrict__ hrow, FillAhead &A) {
+    const int col = C.c0 + 32 * jb + C.lane;
+    const bool in = jb < nb && col < C.c1;
+    A.hv = first_strip ? -C.two_p : (in ? __ldcg(hrow + col) : 0.0f);
+    A.lt = in ? (int)(C.tsent[col + 1] - C.tsent[col]) : 1;
+    if (jb < nb && C.rv) {
+        const uchar2 *q = C.rowp + C.c0 + 32 * jb;
+        prefetch_l1(q);
+        prefetch_l1(q + 16);
+        prefetch_l1(q + 31);
+    }
+}
+
 // One 32-column block iteration of a strip sweep.  cur receives the
 // similarities of block jb (rotated); prev holds block jb-1.  rc/rp are the
-// 64-bit traceback registers of this and the previous iteration.
+// 64-bit traceback registers of this and the previous iteration.  A holds
+// block jb's look-ahead values on entry and block jb+1's on return.
 __device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, bool first_strip,
                                            const float *__restrict__ hrow, float *__restrict__ hrow_w,
                                            float (&cur)[32], const float (&prev)[32], uint64_t &rc,
                                            const uint64_t &rp, float &a_down, float &b,
-                                           uint64_t *__restrict__ tb_strip) {
+                                           uint64_t *__restrict__ tb_strip, FillAhead &A) {
     const int lane = C.lane;
     const int col_base = C.c0 + 32 * jb;
-    const bool lane_col = col_base + lane < C.c1;
     // UP candidates of the first row of the strip for the 32 columns of this block
-    const float hv = first_strip ? -C.two_p : (lane_col ? __ldcg(hrow + col_base + lane) : 0.0f);
+    const float hv = A.hv;
     if (jb < nb) {
         __syncwarp();
-        C.colv[lane] = sim_col(lane_col ? (int)(C.tsent[col_base + lane + 1] - C.tsent[col_base + lane]) : 1, C.P);
+        C.colv[lane] = sim_col(A.lt, C.P);
         __syncwarp();
+        fill_ahead(C, jb + 1, nb, first_strip, hrow, A);
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const int c = (x - lane) & 31;
@@ -56,17 +84,18 @@ __device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, boo
         if (lane == 0) a_up = h0;
         const int j = col_base + u - lane;
         const float sv = (u >= lane) ? cur[u] : prev[u];
-        if (C.rv && j >= C.c0 && j < C.c1) {
-            const float d = fmaxf(fmaxf(sv, a_up), b);
-            const uint64_t bits = (d == a_up) ? (uint64_t)kUp << (2 * u)
-                                              : ((d == b) ? (uint64_t)kLeft << (2 * u) : 0ull);
-            rc |= bits;
-            const float e = __fsub_rn(d, C.two_p);
-            const float nb2 = __fsub_rn(e, a_up);
-            a_down = __fsub_rn(e, b);
-            b = nb2;
-            if (lane == 31) __stcg(hrow_w + j, a_down);
-        }
+        // branch-free step: computed in every lane, committed where the cell
+        // exists (the skew leaves lanes outside the pair at both ends)
+        const bool valid = C.rv && j >= C.c0 && j < C.c1;
+        const float d = fmaxf(fmaxf(sv, a_up), b);
+        const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : 0u);
+        rc |= valid ? (uint64_t)code << (2 * u) : 0ull;
+        const float e = __fsub_rn(d, C.two_p);
+        const float nb2 = __fsub_rn(e, a_up);
+        const float nd = __fsub_rn(e, b);
+        a_down = valid ? nd : a_down;
+        b = valid ? nb2 : b;
+        if (valid && lane == 31) __stcg(hrow_w + j, nd);
     }
     // the word of block jb-1 is complete: its columns came at steps u >= lane
     // of iteration jb-1 and u < lane of iteration jb
@@ -81,7 +110,10 @@ __device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, boo
 // Sweep strip s (rows 32s..32s+31) over columns [C.c0, C.c1).  b0 holds the
 // LEFT candidates of column c0 (-2p at the left border); returns each lane's
 // LEFT candidate after the last column.  hrow holds the UP candidates of the
-// row above the strip and receives those of the strip's last row.
+// row above the strip and receives those of the strip's last row (lane 31
+// writes column j at the step after every lane has read it: block jb reads
+// columns 32 jb .. 32 jb + 31 one block ahead, and lane 31 reaches them only
+// in blocks jb and jb + 1).
 __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__restrict__ ssent,
                                             const uint8_t *__restrict__ counts, int64_t cell_off,
                                             float *__restrict__ hrow, uint64_t *__restrict__ tb_pair,
@@ -99,10 +131,17 @@ __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__
     for (int x = 0; x < 32; ++x) B[x] = 0.0f;
     uint64_t RA = 0, RB = 0;
     uint64_t *tb_strip = tb_pair + (int64_t)s * nblk_pair * 32;
-    for (int jb = 0; jb <= nb; jb += 2) {
-        fill_block(C, jb, nb, s == 0, hrow, hrow, A, B, RA, RB, a_down, b, tb_strip);
-        if (jb + 1 > nb) break;
-        fill_block(C, jb + 1, nb, s == 0, hrow, hrow, B, A, RB, RA, a_down, b, tb_strip);
+    FillAhead ah;
+    fill_ahead(C, 0, nb, s == 0, hrow, ah);
+    // one instance of the (fully unrolled) block body: the current block's
+    // similarities become the previous block's by a register copy, which
+    // keeps the loop's code half the size of two alternating instances
+#pragma unroll 1
+    for (int jb = 0; jb <= nb; ++jb) {
+        fill_block(C, jb, nb, s == 0, hrow, hrow, A, B, RA, RB, a_down, b, tb_strip, ah);
+#pragma unroll
+        for (int x = 0; x < 32; ++x) B[x] = A[x];
+        RB = RA;
     }
     return b;
 }
