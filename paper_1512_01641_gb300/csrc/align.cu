@@ -40,17 +40,20 @@ constexpr int kTailWarps = 4;
 // Bounded wait for a nonzero tile flag.
 __device__ bool wait_flag(const int32_t *f, int64_t limit) {
     for (int64_t it = 0; it < limit; ++it) {
-        if (ld_acquire(f) != 0) return true;
+        if (ld_relaxed(f) != 0) return true;  // the caller acquires
         __nanosleep(200);
     }
     return false;
 }
 
-__global__ void __launch_bounds__(32 * kFillWarps)
+__global__ void __launch_bounds__(32 * kFillWarps, 3)
 fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             const FillItem *__restrict__ items, int64_t n_items, DevParams P,
-            const uint8_t *__restrict__ counts, AlignScratch S, int64_t wait_limit, int64_t skip_flag) {
+            const uint8_t *__restrict__ counts, int64_t counts_bytes, AlignScratch S, int64_t wait_limit,
+            int64_t skip_flag) {
     __shared__ SimCol colv_all[kFillWarps][32];
+    __shared__ __align__(16) unsigned char stage_all[kFillWarps][2][32][kStageBytes];
+    __shared__ uint64_t bar_all[kFillWarps][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     FillCtx C;
     C.lane = lane;
@@ -58,6 +61,12 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
     C.two_p = __fadd_rn(P.gap, P.gap);
     C.k = sim_const(P);
     C.colv = colv_all[warp];
+    C.counts = counts;
+    C.counts_bytes = counts_bytes;
+    C.stage = stage_all[warp];
+    C.stage_bar = bar_all[warp];
+    C.status = S.status;
+    fill_stage_init(C);
     for (;;) {
         int64_t it = 0;
         if (lane == 0) it = atomicAdd(S.queue, 1);
@@ -347,8 +356,8 @@ int tail_grid(int64_t warps_wanted, int n_sms) {
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit, int64_t skip_flag,
-                        int n_sms, cudaStream_t st) {
+                        const uint8_t *counts, int64_t counts_bytes, const AlignScratch &S, int64_t wait_limit,
+                        int64_t skip_flag, int n_sms, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_kernel, 32 * kFillWarps, 0);
@@ -358,8 +367,8 @@ cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGe
     if (blocks > want) blocks = want;
     e = cudaMemsetAsync(S.queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    fill_kernel<<<(unsigned)blocks, 32 * kFillWarps, 0, st>>>(src, tgt, geom, items, n_items, P, counts, S,
-                                                               wait_limit, skip_flag);
+    fill_kernel<<<(unsigned)blocks, 32 * kFillWarps, 0, st>>>(src, tgt, geom, items, n_items, P, counts,
+                                                               counts_bytes, S, wait_limit, skip_flag);
     return cudaGetLastError();
 }
 

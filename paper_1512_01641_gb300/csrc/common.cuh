@@ -99,6 +99,14 @@ __device__ __forceinline__ float similarity(int ms, int mt, const SimRow &r, con
 }
 
 // PTX acquire/release accesses for the tile flags of the cooperative fill.
+// Waits poll with relaxed loads and acquire once the value is seen: an
+// acquire at GPU scope must keep later loads off stale L1 lines, so polling
+// with it would keep clearing the L1 that the SM's working warps rely on.
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -114,9 +122,14 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 // lane waits with a bounded spin.
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t arrivals = 1) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(arrivals) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Plain arrival (no bytes expected) of this thread on bar.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // Order this thread's earlier shared-memory accesses before the async copy

@@ -226,6 +226,10 @@ struct alignas(16) StripSmem {
 };
 static_assert(kTokCap >= kPosCap, "shared buffer sizes");
 static_assert(offsetof(StripSmem<11>, gh) % 16 == 0 && sizeof(StripSmem<11>) % 16 == 0, "bulk copy alignment");
+static_assert(offsetof(StripSmem<11>, key) % 16 == 0 && offsetof(StripSmem<11>, rowmask) % 16 == 0 &&
+                  offsetof(StripSmem<11>, colmask) % 16 == 0 && offsetof(StripSmem<11>, hpos) % 16 == 0 &&
+                  kPosCap % 4 == 0,
+              "16-byte clears");
 constexpr int64_t kBulkWaitLimit = 1 << 22;
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -312,6 +316,10 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     if (tid == 0) mbar_init(&sm.bar);
+    // column masks and position words return to zero at the end of every
+    // block (and stay zero when a row group is rebuilt): cleared once here
+    for (int x = tid; x < S / 4; x += kStripThreads) reinterpret_cast<uint4 *>(sm.colmask)[x] = make_uint4(0, 0, 0, 0);
+    for (int x = tid; x < kPosCap / 4; x += kStripThreads) reinterpret_cast<uint4 *>(sm.hpos)[x] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     uint32_t phase = 0;
 
@@ -335,12 +343,10 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
             int n_pos;
             const int prow = warp_excl_scan(my_len, lane, n_pos);
             const int64_t ptok0 = src.sent[ssent0 + g_lo];
-            for (int x = tid; x < S; x += kStripThreads) {
-                sm.key[x] = kEmpty;
-                sm.rowmask[x] = 0u;
-                sm.colmask[x] = 0u;
+            for (int x = tid; x < S / 4; x += kStripThreads) {
+                reinterpret_cast<int4 *>(sm.key)[x] = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
+                reinterpret_cast<uint4 *>(sm.rowmask)[x] = make_uint4(0, 0, 0, 0);
             }
-            for (int x = tid; x < n_pos; x += kStripThreads) sm.hpos[x] = 0u;
             if (tid == 0) {
                 sm.n_keys = 0;
                 sm.n_ent = 0;

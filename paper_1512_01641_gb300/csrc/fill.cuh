@@ -7,17 +7,83 @@
 
 namespace gbm {
 
+// Bytes of one lane's staged count segment: 32 cells (64 bytes) inside
+// their 16-byte-aligned cover.
+constexpr int kStageBytes = 80;
+constexpr int64_t kStageWaitLimit = 1 << 22;
+
 struct FillCtx {
     int lane, N, M, c0, c1, r;
     bool rv;
     float two_p;
     SimRow row;
     SimConst k;
-    const uchar2 *rowp;   // counts of row r
     const int64_t *tsent; // target sentence offsets of the pair
     SimCol *colv;         // shared: per-column similarity constants of the current block
     DevParams P;
+    // staging of the count bytes (per warp, double-buffered by block parity)
+    const uint8_t *counts;      // the whole counts array ...
+    int64_t counts_bytes;       // ... and its length (a cover never reads past it)
+    int64_t row_byte;           // byte offset of row r's first cell in counts
+    unsigned char (*stage)[32][kStageBytes];  // shared [2][lane][byte]
+    uint64_t *stage_bar;        // shared [2] mbarriers, 32 arrivals each
+    uint32_t stage_phase;       // bit b: parity of buffer b's next completion
+    int stage_off0, stage_off1; // byte offset of the segment in the lane's staged row, per buffer
+    uint32_t *status;           // timeout bit (may be null)
 };
+
+// Per-warp setup of the staging barriers (lane 0 initialises, all lanes
+// wait at the __syncwarp that follows).
+__device__ __forceinline__ void fill_stage_init(FillCtx &C) {
+    if (C.lane == 0) {
+        mbar_init(C.stage_bar, 32);
+        mbar_init(C.stage_bar + 1, 32);
+    }
+    C.stage_phase = 0;
+    C.stage_off0 = C.stage_off1 = 0;
+    __syncwarp();
+}
+
+// Start staging block jb's count bytes into buffer jb & 1: every lane copies
+// its own row's 64 bytes with one bulk async copy of their cover aligned to
+// 16-byte ADDRESSES (the array itself may start anywhere), or with plain
+// loads when that cover would reach outside the array; then it arrives on
+// the buffer's barrier.
+__device__ __forceinline__ void fill_stage(FillCtx &C, int jb, int nb) {
+    if (jb >= nb) return;
+    const int buf = jb & 1;
+    const int col_base = C.c0 + 32 * jb;
+    const int ncol = min(32, C.c1 - col_base);
+    uint64_t *bar = C.stage_bar + buf;
+    unsigned char *dst = C.stage[buf][C.lane];
+    int off = 0;
+    if (C.rv) {
+        const uintptr_t base = reinterpret_cast<uintptr_t>(C.counts);
+        const uintptr_t a = base + (uintptr_t)(C.row_byte + 2 * (int64_t)col_base);
+        const uintptr_t a16 = a & ~(uintptr_t)15, e16 = (a + 2 * ncol + 15) & ~(uintptr_t)15;
+        off = (int)(a - a16);
+        if (a16 >= base && e16 <= base + (uintptr_t)C.counts_bytes) {
+            bulk_copy_g2s(dst, reinterpret_cast<const void *>(a16), (uint32_t)(e16 - a16), bar);
+        } else {
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(a);
+            for (int t = 0; t < 2 * ncol; ++t) dst[off + t] = src[t];
+            mbar_arrive(bar);
+        }
+    } else {
+        mbar_arrive(bar);
+    }
+    if (buf) C.stage_off1 = off;
+    else C.stage_off0 = off;
+}
+
+// Wait until block jb's staged bytes have landed; returns the lane's row.
+__device__ __forceinline__ const unsigned char *fill_stage_wait(FillCtx &C, int jb) {
+    const int buf = jb & 1;
+    if (!mbar_wait(C.stage_bar + buf, (C.stage_phase >> buf) & 1u, kStageWaitLimit) && C.status)
+        atomicOr(C.status, kStTimeout);
+    C.stage_phase ^= 1u << buf;
+    return C.stage[buf][C.lane] + (buf ? C.stage_off1 : C.stage_off0);
+}
 
 // Values of the next block, loaded one block ahead so that their global
 // latency overlaps the current block's sweep.
@@ -26,31 +92,20 @@ struct FillAhead {
     int lt;    // length of this lane's target sentence
 };
 
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-// Loads the look-ahead values of block jb and prefetches the lane's count
-// bytes of that block (64 bytes of its row) into L1.
+// Loads the look-ahead values of block jb.
 __device__ __forceinline__ void fill_ahead(const FillCtx &C, int jb, int nb, bool first_strip,
                                            const float *__restrict__ hrow, FillAhead &A) {
     const int col = C.c0 + 32 * jb + C.lane;
     const bool in = jb < nb && col < C.c1;
     A.hv = first_strip ? -C.two_p : (in ? __ldcg(hrow + col) : 0.0f);
     A.lt = in ? (int)(C.tsent[col + 1] - C.tsent[col]) : 1;
-    if (jb < nb && C.rv) {
-        const uchar2 *q = C.rowp + C.c0 + 32 * jb;
-        prefetch_l1(q);
-        prefetch_l1(q + 16);
-        prefetch_l1(q + 31);
-    }
 }
 
 // One 32-column block iteration of a strip sweep.  cur receives the
 // similarities of block jb (rotated); prev holds block jb-1.  rc/rp are the
 // 64-bit traceback registers of this and the previous iteration.  A holds
 // block jb's look-ahead values on entry and block jb+1's on return.
-__device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, bool first_strip,
+__device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool first_strip,
                                            const float *__restrict__ hrow, float *__restrict__ hrow_w,
                                            float (&cur)[32], const float (&prev)[32], uint64_t &rc,
                                            const uint64_t &rp, float &a_down, float &b,
@@ -64,13 +119,15 @@ __device__ __forceinline__ void fill_block(const FillCtx &C, int jb, int nb, boo
         C.colv[lane] = sim_col(A.lt, C.P);
         __syncwarp();
         fill_ahead(C, jb + 1, nb, first_strip, hrow, A);
+        fill_stage(C, jb + 1, nb);
+        const unsigned char *st = fill_stage_wait(C, jb);
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const int c = (x - lane) & 31;
             const int col = col_base + c;
             float v = 0.0f;
             if (C.rv && col < C.c1) {
-                const uchar2 q = C.rowp[col];
+                const uchar2 q = *reinterpret_cast<const uchar2 *>(st + 2 * c);
                 v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
             }
             cur[x] = v;
@@ -123,7 +180,7 @@ __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__
     C.rv = C.r < C.N;
     const int ls = C.rv ? (int)(ssent[C.r + 1] - ssent[C.r]) : 1;
     C.row = sim_row(ls, C.P);
-    C.rowp = reinterpret_cast<const uchar2 *>(counts) + cell_off + (int64_t)C.r * C.M;
+    C.row_byte = 2 * (cell_off + (int64_t)C.r * C.M);
     const int nb = (C.c1 - C.c0 + 31) >> 5;
     float b = b0, a_down = 0.0f;
     float A[32], B[32];
@@ -133,6 +190,7 @@ __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__
     uint64_t *tb_strip = tb_pair + (int64_t)s * nblk_pair * 32;
     FillAhead ah;
     fill_ahead(C, 0, nb, s == 0, hrow, ah);
+    fill_stage(C, 0, nb);
     // one instance of the (fully unrolled) block body: the current block's
     // similarities become the previous block's by a register copy, which
     // keeps the loop's code half the size of two alternating instances

@@ -95,8 +95,8 @@ cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairG
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, const AlignScratch &S, int64_t wait_limit, int64_t skip_flag,
-                        int n_sms, cudaStream_t st);
+                        const uint8_t *counts, int64_t counts_bytes, const AlignScratch &S, int64_t wait_limit,
+                        int64_t skip_flag, int n_sms, cudaStream_t st);
 
 cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
                         cudaStream_t st);

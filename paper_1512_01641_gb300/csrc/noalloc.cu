@@ -36,6 +36,8 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
                          int32_t *__restrict__ link_i, int32_t *__restrict__ link_j, float *__restrict__ link_s,
                          int32_t *__restrict__ n_links, float *__restrict__ pair_score) {
     __shared__ SimCol colv[32];
+    __shared__ __align__(16) unsigned char stage[2][32][kStageBytes];
+    __shared__ uint64_t stage_bar[2];
     const int lane = threadIdx.x;
     const int nstrips = (N + 31) >> 5, nblk = (M + 31) >> 5;
     const int cap = min(N, M);
@@ -52,6 +54,12 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
         C.two_p = __fadd_rn(P.gap, P.gap);
         C.k = sim_const(P);
         C.colv = colv;
+        C.counts = counts;
+        C.counts_bytes = 2 * (int64_t)N * M;
+        C.stage = stage;
+        C.stage_bar = stage_bar;
+        C.status = nullptr;
+        fill_stage_init(C);
         C.N = N;
         C.M = M;
         C.c0 = 0;

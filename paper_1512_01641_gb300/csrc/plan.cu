@@ -518,7 +518,7 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
     const int64_t n = p->n_pairs;
     if (p->n_flags > 0) MINE_CK(cudaMemsetAsync(S.flags, 0, p->n_flags * sizeof(int32_t), st));
     MINE_CK(timed(p, kKFill, st, [&] {
-        return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, S,
+        return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, 2 * p->n_cells, S,
                            p->knobs.wait_limit, p->knobs.skip_flag, p->n_sms, st);
     }));
     MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, n, S, p->n_sms, st); }));

@@ -78,15 +78,19 @@ struct SoftCtx {
 };
 
 // Bounded wait until the progress counter *ctr reaches need.  Every lane
+// polls with relaxed loads and, once the whole warp has seen enough,
 // acquires, so that its own later loads see what the producer wrote before
-// it published; the warp leaves when every lane has seen enough.  After
+// it published (the acquired value is at least the polled one).  After
 // wait_limit polls the wait gives up, sets the timeout bit and stops waiting
 // for the rest of the item (its results are then invalid, the status says so).
 __device__ __forceinline__ void soft_wait(SoftCtx &C, const int32_t *ctr, int need, int &have) {
     if (C.failed || __all_sync(kFull, have >= need)) return;
     for (int64_t it = 0;; ++it) {
-        have = ld_acquire(ctr);
-        if (__all_sync(kFull, have >= need)) return;
+        have = ld_relaxed(ctr);
+        if (__all_sync(kFull, have >= need)) {
+            have = ld_acquire(ctr);  // orders this lane's later loads after the producer's writes
+            return;
+        }
         if (it >= C.wait_limit) {
             C.failed = true;
             if (C.lane == 0) atomicOr(C.status, kStTimeout);

@@ -119,6 +119,34 @@ def test_fused_equals_count_then_align(case):
         assert torch.equal(out[key][:n], gpu["out"][key][:n]), key
 
 
+@pytest.mark.parametrize("shift", [2, 6, 14])
+def test_align_from_counts_at_any_address(shift):
+    """mine_align reads the counts wherever the caller put them: a copy at a
+    2-byte-aligned (not 16-byte-aligned) address gives the same links and
+    scores, with tiled and untiled pairs."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    ns = [300, 97, 5, 64, 40]
+    ms = [410, 33, 300, 97, 700]
+    batch = synth.make_batch(83, len(ns), v_src=4000, v_tgt=4000, planted_frac=0.5, src_sizes=ns, tgt_sizes=ms)
+    p = _params()
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        plan.set_option("tile_min_cells", 1 << 14)
+        plan.set_option("tile_min_rows", 33)
+        plan.set_option("tile_cols", 64)
+        counts = plan.count()
+        ref = plan.align(p, counts)
+        torch.cuda.synchronize()
+        ref = {k: v.clone() for k, v in ref.items()}
+        raw = torch.zeros(counts.numel() + 64, dtype=torch.uint8, device="cuda")
+        moved = raw[shift:shift + counts.numel()]
+        moved.copy_(counts.reshape(-1))
+        assert moved.data_ptr() % 16 == shift % 16
+        got = plan.align(p, moved)
+        plan.check()
+        _outputs_equal(ref, got, batch.n_pairs)
+
+
 def test_deterministic():
     import torch
     from paper_1512_01641_gb300 import miner
