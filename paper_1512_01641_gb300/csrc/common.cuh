@@ -90,11 +90,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// Exact float of a small non-negative integer (x < 2^23) with two full-rate
+// operations: 2^23 + x has x in its low mantissa bits, so subtracting 2^23
+// is exact.  Same value as (float)x, which is a quarter-rate conversion.
+__device__ __forceinline__ float small_int_float(int x) {
+    return __fsub_rn(__int_as_float(0x4B000000 | x), 8388608.0f);
+}
 __device__ __forceinline__ float similarity(int ms, int mt, const SimRow &r, const SimCol &c, const SimConst &k) {
     const float q = fminf(__fmul_rn(r.len, c.rlen), __fmul_rn(c.len, r.rlen));
     float y = __fmaf_rn(k.c1, q, k.c0);
-    y = __fmaf_rn(c.b, (float)mt, y);
-    y = __fmaf_rn(r.a, (float)ms, y);
+    y = __fmaf_rn(c.b, small_int_float(mt), y);
+    y = __fmaf_rn(r.a, small_int_float(ms), y);
     return rcp_approx(__fadd_rn(1.0f, ex2_approx(y)));
 }
 

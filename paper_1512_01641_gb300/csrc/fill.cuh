@@ -121,16 +121,15 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         fill_ahead(C, jb + 1, nb, first_strip, hrow, A);
         fill_stage(C, jb + 1, nb);
         const unsigned char *st = fill_stage_wait(C, jb);
+        // branch-free, so that the 32 independent cells overlap: every cell
+        // is computed from the staged row (in bounds for any c) and the ones
+        // outside the pair are zeroed
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const int c = (x - lane) & 31;
-            const int col = col_base + c;
-            float v = 0.0f;
-            if (C.rv && col < C.c1) {
-                const uchar2 q = *reinterpret_cast<const uchar2 *>(st + 2 * c);
-                v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
-            }
-            cur[x] = v;
+            const uchar2 q = *reinterpret_cast<const uchar2 *>(st + 2 * c);
+            const float v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
+            cur[x] = (C.rv && col_base + c < C.c1) ? v : 0.0f;
         }
     }
     rc = 0;
@@ -142,17 +141,20 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         const int j = col_base + u - lane;
         const float sv = (u >= lane) ? cur[u] : prev[u];
         // branch-free step: computed in every lane, committed where the cell
-        // exists (the skew leaves lanes outside the pair at both ends)
+        // exists (the skew leaves lanes outside the pair at both ends).  Only
+        // one max waits for the shuffled value.  a_down needs no commit: a
+        // lane's output of an invalid step reaches the next lane only at a
+        // step where that lane is invalid too (before its first column, after
+        // its last, or below the last row).
         const bool valid = C.rv && j >= C.c0 && j < C.c1;
-        const float d = fmaxf(fmaxf(sv, a_up), b);
+        const float d = fmaxf(fmaxf(sv, b), a_up);
         const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : 0u);
         rc |= valid ? (uint64_t)code << (2 * u) : 0ull;
         const float e = __fsub_rn(d, C.two_p);
         const float nb2 = __fsub_rn(e, a_up);
-        const float nd = __fsub_rn(e, b);
-        a_down = valid ? nd : a_down;
+        a_down = __fsub_rn(e, b);
         b = valid ? nb2 : b;
-        if (valid && lane == 31) __stcg(hrow_w + j, nd);
+        if (valid && lane == 31) __stcg(hrow_w + j, a_down);
     }
     // the word of block jb-1 is complete: its columns came at steps u >= lane
     // of iteration jb-1 and u < lane of iteration jb
