@@ -67,6 +67,20 @@ __device__ __forceinline__ bool table_insert_new(int32_t *key, int32_t t, int &s
     return false;
 }
 
+// Continues a lookup of t at slot h (after a first probe that found
+// neither t nor an empty slot).
+template <int LOG_SLOTS>
+__device__ __forceinline__ int table_find_from(const int32_t *key, int32_t t, uint32_t h) {
+    constexpr uint32_t S = 1u << LOG_SLOTS;
+    for (uint32_t n = 1; n < S; ++n) {
+        const int32_t k = key[h];
+        if (k == t) return (int)h;
+        if (k == kEmpty) return -1;
+        h = (h + 1) & (S - 1);
+    }
+    return -1;
+}
+
 template <int LOG_SLOTS>
 __device__ __forceinline__ int table_find(const int32_t *key, int32_t t) {
     constexpr uint32_t S = 1u << LOG_SLOTS;
@@ -187,9 +201,10 @@ count_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restr
 //     position word (bit j: the position has a translation in sentence j;
 //     most masks are 0, so few atomics);
 //   then warp 1 adds row i's position words into bit-sliced counters (ms of
-//     32 columns at once, lane = row) and clears them, warps 2-3 clear the
-//     column masks, and warp 0 stages the next block's target tokens (bulk
-//     async copy) so that the copy overlaps the rest of this block;
+//     32 columns at once, lane = row), clears them and expands its counters
+//     to bytes, warp 0 expands the mt counters, warp 2 clears the column
+//     masks, and warp 3 stages the next block's target tokens (bulk async
+//     copy) so that the copy overlaps the rest of this block;
 //   finally all threads write the (ms, mt) bytes of the block, transposed
 //     through shared memory, one coalesced row at a time.
 // Counters are carry-save (four words per step), bytes are expanded by
@@ -200,6 +215,7 @@ constexpr int kStripThreads = 32 * kStripWarps;
 constexpr int kEntCap = 1440;  // translation entries of one row group
 constexpr int kPosCap = 992;   // source positions per strip item (32 rows x 31 tokens)
 constexpr int kTokCap = 992;   // target tokens per column block (32 sentences x 31 tokens)
+constexpr int kColRounds = (kTokCap + kStripThreads - 1) / kStripThreads;  // target tokens per thread
 
 template <int LOG_SLOTS>
 struct alignas(16) StripSmem {
@@ -306,7 +322,7 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
 constexpr float kMaxLoad = 0.85f;
 
 template <int LOG_SLOTS, int K>
-__global__ void __launch_bounds__(kStripThreads)
+__global__ void __launch_bounds__(kStripThreads, 5)
 count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *__restrict__ geom,
                    const CountStripItem *__restrict__ items, int64_t n_items, bool bulk_ok,
                    uint8_t *__restrict__ counts, uint32_t *status) {
@@ -414,9 +430,9 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                 continue;
             }
 
-            // stage block jb's target tokens (warp 0): column ids and token
+            // stage block jb's target tokens (warp 3): column ids and token
             // offsets into shared memory, then the copy
-            int64_t nx_lo = 0, nx_hi = 0;  // warp 0: sentence offsets of the next block to stage
+            int64_t nx_lo = 0, nx_hi = 0;  // warp 3: sentence offsets of the next block to stage
             auto offsets = [&](int jb) {
                 const int c = 32 * jb + lane;
                 if (jb < nblk && c < g.m) {
@@ -438,7 +454,7 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                 const int sh = stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.gh, &sm.bar, bulk_ok, lane, bulk_b);
                 if (lane == 0) sm.tsh = sh | (bulk_b ? 1 << 30 : 0);
             };
-            if (warp == 0) {
+            if (warp == 3) {
                 bool b;
                 offsets(0);
                 stage_block(0, b);
@@ -453,27 +469,45 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                 if (!stage_wait((tshw >> 30) & 1, &sm.bar, phase, status)) return;
                 const int n_tok = sm.ctpre[32];
                 uint32_t *tg = sm.gh + (tshw & ((1 << 30) - 1));
-                // column pass (each token's row mask replaces it in place)
-                for (int x = tid; x < n_tok; x += kStripThreads) {
-                    const int slot = table_find<LOG_SLOTS>(sm.key, (int32_t)tg[x]);
-                    uint32_t rm = 0u;
-                    if (slot >= 0) {
-                        rm = sm.rowmask[slot];
-                        atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
+                // column pass (each token's row mask replaces it in place): the
+                // first probe of all of a thread's tokens goes out as one batch
+                // of loads; the rare longer probe chains continue one by one
+                {
+                    int32_t tk[kColRounds];
+                    uint32_t hs[kColRounds];
+                    int32_t k0[kColRounds];
+#pragma unroll
+                    for (int k = 0; k < kColRounds; ++k) {
+                        const int x = tid + kStripThreads * k;
+                        tk[k] = x < n_tok ? (int32_t)tg[x] : kEmpty;
+                        hs[k] = hash_slot(tk[k], LOG_SLOTS);
+                        k0[k] = x < n_tok ? sm.key[hs[k]] : kEmpty;
                     }
-                    tg[x] = rm;
+#pragma unroll
+                    for (int k = 0; k < kColRounds; ++k) {
+                        if (kStripThreads * k >= n_tok) break;  // same in every thread
+                        const int x = tid + kStripThreads * k;
+                        if (x < n_tok) {
+                            int slot = -1;
+                            if (k0[k] == tk[k])
+                                slot = (int)hs[k];
+                            else if (k0[k] != kEmpty)
+                                slot = table_find_from<LOG_SLOTS>(sm.key, tk[k], (hs[k] + 1) & (S - 1));
+                            uint32_t rm = 0u;
+                            if (slot >= 0) {
+                                rm = sm.rowmask[slot];
+                                atomicOr(&sm.colmask[slot], 1u << sm.colid[x]);
+                            }
+                            tg[x] = rm;
+                        }
+                    }
                 }
                 __syncthreads();
+                BitCounter<K> mt;  // warp 0: mt of 32 rows for column `lane`
                 if (warp == 0) {
-                    // mt of 32 rows for column `lane`
-                    BitCounter<K> mt;
                     mt.clear();
                     const int t0 = sm.ctpre[lane];
                     acc_words(mt, tg + t0, lane < nc ? (lane < 31 ? sm.ctpre[lane + 1] : n_tok) - t0 : 0);
-                    uint32_t w[8];
-                    mt.to_bytes(w);
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][4 * m]) = w[m];
                 } else {
                     // row pass: entries' column masks into their positions' words
 #pragma unroll 4
@@ -495,13 +529,19 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
 #pragma unroll
                     for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&sm.ms_t[lane][4 * m]) = w[m];
                 } else if (warp == 0) {
+                    // mt bytes, beside the ms accumulation
+                    uint32_t w[8];
+                    mt.to_bytes(w);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][4 * m]) = w[m];
+                } else if (warp == 3) {
                     if (jb + 1 < nblk) {
                         bool b;
                         stage_block(jb + 1, b);
                         offsets(jb + 2);
                     }
                 } else {
-                    for (int x = tid - 64; x < S / 4; x += kStripThreads - 64)
+                    for (int x = lane; x < S / 4; x += 32)
                         reinterpret_cast<uint4 *>(sm.colmask)[x] = make_uint4(0, 0, 0, 0);
                 }
                 __syncthreads();
