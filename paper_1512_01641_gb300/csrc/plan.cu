@@ -233,8 +233,7 @@ static int validate_dict(const mine_dict *d, uint32_t *status, int32_t *max_fano
 // interleaved between the diagonals so that warps find ready work while the
 // wavefronts of the large pairs advance.
 static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const std::vector<int64_t> &td,
-                           std::vector<CountItem> &citems, std::vector<FillItem> &fitems, int64_t &tbw,
-                           int64_t &hrow, int64_t &vcol) {
+                           std::vector<FillItem> &fitems, int64_t &tbw, int64_t &hrow, int64_t &vcol) {
     const int64_t n = p->n_pairs;
     const PlanKnobs &K = p->knobs;
     p->geom_h.assign(n, PairGeom{});
@@ -244,7 +243,8 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->max_m = 0;
     int64_t cell = 0, link = 0, flags = 0;
     tbw = hrow = vcol = 0;
-    std::vector<int32_t> small, tiled;
+    // (cells, pair) of every pair: one sort gives every work order below
+    std::vector<std::pair<int64_t, int32_t>> by_size((size_t)n);
     for (int64_t k = 0; k < n; ++k) {
         PairGeom &g = p->geom_h[k];
         g.n = (int32_t)(sd[k + 1] - sd[k]);
@@ -267,13 +267,12 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
             g.nchunk = (g.m + g.cw - 1) / g.cw;
             g.flag_off = flags;
             flags += ns * g.nchunk;
-            tiled.push_back((int32_t)k);
         } else {
             g.cw = (int32_t)std::max<int64_t>(32, nb * 32);
             g.nchunk = 1;
             g.flag_off = -1;
-            if (cells > 0) small.push_back((int32_t)k);
         }
+        by_size[(size_t)k] = {-cells, (int32_t)k};
         cell += cells;
         tbw += ns * nb * 32;
         link += std::min(g.n, g.m);
@@ -285,22 +284,17 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->link_cap = link;
     p->n_flags = flags;
 
-    auto cells_of = [&](int32_t k) { return (int64_t)p->geom_h[k].n * p->geom_h[k].m; };
-    std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
-    std::stable_sort(tiled.begin(), tiled.end(), [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
+    // pairs by decreasing size, ties by index (the order of a stable sort)
+    std::sort(by_size.begin(), by_size.end());
     p->pair_order_h.resize(n);
-    std::iota(p->pair_order_h.begin(), p->pair_order_h.end(), 0);
-    std::stable_sort(p->pair_order_h.begin(), p->pair_order_h.end(),
-                     [&](int32_t a, int32_t b) { return cells_of(a) > cells_of(b); });
-
-    // count items: 32 x 32 blocks, large pairs first
-    citems.clear();
-    std::vector<int32_t> all(tiled);
-    all.insert(all.end(), small.begin(), small.end());
-    for (int32_t k : all) {
-        const int ns = (p->geom_h[k].n + 31) / 32, nb = (p->geom_h[k].m + 31) / 32;
-        for (int s = 0; s < ns; ++s)
-            for (int b = 0; b < nb; ++b) citems.push_back({k, (s << 16) | b});
+    std::vector<int32_t> small, tiled;
+    for (int64_t x = 0; x < n; ++x) {
+        const int32_t k = by_size[(size_t)x].second;
+        p->pair_order_h[x] = k;
+        if (p->geom_h[k].flag_off >= 0)
+            tiled.push_back(k);
+        else if (by_size[(size_t)x].first < 0)
+            small.push_back(k);
     }
 
     // fill items
@@ -330,8 +324,19 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
         const int32_t k = small[next_small];
         fitems.push_back({k, 0, (p->geom_h[k].n + 31) / 32, 0});
     }
-    p->n_count_items = (int64_t)citems.size();
     p->n_fill_items = (int64_t)fitems.size();
+}
+
+// Items of the per-block count kernel (used when the strip kernel cannot
+// be): 32 x 32 blocks, large pairs first.
+static void build_count_items(const mine_plan *p, std::vector<CountItem> &citems) {
+    citems.clear();
+    for (int32_t k : p->pair_order_h) {
+        const int ns = (p->geom_h[k].n + 31) / 32, nb = (p->geom_h[k].m + 31) / 32;
+        if ((int64_t)ns * nb == 0) continue;
+        for (int s = 0; s < ns; ++s)
+            for (int b = 0; b < nb; ++b) citems.push_back({k, (s << 16) | b});
+    }
 }
 
 extern "C" {
@@ -397,14 +402,11 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         if (r != MINE_OK) return fail(r);
     }
 
-    std::vector<CountItem> citems;
     std::vector<FillItem> fitems;
     int64_t tbw = 0, hrow = 0, vcol = 0;
-    build_geometry(p, sd, td, citems, fitems, tbw, hrow, vcol);
+    build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
     PLAN_CK(dalloc(&p->geom, n));
     PLAN_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
-    PLAN_CK(dalloc(&p->count_items, citems.size()));
-    PLAN_CK(cudaMemcpyAsync(p->count_items, citems.data(), citems.size() * sizeof(CountItem), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->pair_order, n));
     PLAN_CK(cudaMemcpyAsync(p->pair_order, p->pair_order_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->fill_items, fitems.size()));
@@ -438,13 +440,9 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     // counter planes) and a dictionary fan-out small enough for one row to fit
     p->use_strips = std::max(stats[0], stats[1]) <= 31 && stats[3] <= kStripMaxFanout;
     if (p->use_strips) {
-        std::vector<int32_t> order(n);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-            return (int64_t)p->geom_h[a].n * p->geom_h[a].m > (int64_t)p->geom_h[b].n * p->geom_h[b].m;
-        });
         std::vector<CountStripItem> sitems;
-        for (int32_t k : order) {
+        sitems.reserve((size_t)p->soft_strips);
+        for (int32_t k : p->pair_order_h) {  // largest pairs first
             if (p->geom_h[k].m == 0) continue;
             const int ns = (p->geom_h[k].n + 31) / 32;
             for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
@@ -452,6 +450,14 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         p->n_strip_items = (int64_t)sitems.size();
         PLAN_CK(dalloc(&p->strip_items, sitems.size()));
         PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
+                                cudaMemcpyHostToDevice, st));
+        PLAN_CK(cudaStreamSynchronize(st));
+    } else {
+        std::vector<CountItem> citems;
+        build_count_items(p, citems);
+        p->n_count_items = (int64_t)citems.size();
+        PLAN_CK(dalloc(&p->count_items, citems.size()));
+        PLAN_CK(cudaMemcpyAsync(p->count_items, citems.data(), citems.size() * sizeof(CountItem),
                                 cudaMemcpyHostToDevice, st));
         PLAN_CK(cudaStreamSynchronize(st));
     }
@@ -480,7 +486,7 @@ int mine_plan_cell_offsets(const mine_plan *p, int64_t *host_out) {
 
 int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
-    if (p->n_count_items == 0) return MINE_OK;
+    if (p->n_cells == 0) return MINE_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (p->use_strips) {
         MINE_CK(timed(p, kKCount, st, [&] {
@@ -785,10 +791,9 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
         td[x + 1] = td[x] + p->geom_h[x].m;
     }
     p->knobs = k;
-    std::vector<CountItem> citems;
     std::vector<FillItem> fitems;
     int64_t tbw, hrow, vcol;
-    build_geometry(p, sd, td, citems, fitems, tbw, hrow, vcol);
+    build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
     MINE_CK(cudaDeviceSynchronize());
     cudaFree(p->fill_items);
     cudaFree(p->S.flags);
