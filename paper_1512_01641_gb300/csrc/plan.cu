@@ -227,6 +227,30 @@ static int validate_dict(const mine_dict *d, uint32_t *status, int32_t *max_fano
     return MINE_OK;
 }
 
+// Indices 0..n-1 ordered by key (ascending, ties by index): a stable LSD
+// radix sort on 11-bit digits; a pass whose digit is the same for every key
+// is skipped (sizes fit two or three digits).
+static void radix_order(const std::vector<uint64_t> &key, std::vector<int32_t> &order) {
+    constexpr int kBits = 11;
+    constexpr uint64_t kMask = (1u << kBits) - 1;
+    const size_t n = key.size();
+    std::vector<int32_t> a(n), b(n);
+    std::iota(a.begin(), a.end(), 0);
+    std::vector<uint32_t> cnt(kMask + 2);
+    for (int shift = 0; shift < 64 && n > 1; shift += kBits) {
+        const uint64_t d0 = (key[0] >> shift) & kMask;
+        bool same = true;
+        for (size_t i = 1; i < n && same; ++i) same = ((key[i] >> shift) & kMask) == d0;
+        if (same) continue;
+        std::fill(cnt.begin(), cnt.end(), 0u);
+        for (size_t i = 0; i < n; ++i) ++cnt[((key[i] >> shift) & kMask) + 1];
+        for (size_t d = 1; d < cnt.size(); ++d) cnt[d] += cnt[d - 1];
+        for (size_t i = 0; i < n; ++i) b[cnt[(key[a[i]] >> shift) & kMask]++] = a[i];
+        a.swap(b);
+    }
+    order.swap(a);
+}
+
 // Geometry, tiling and work order.  Tiled pairs are cut into 32-row x
 // tile_cols tiles listed in anti-diagonal order (every tile after the tile
 // above it and the tile to its left); whole small pairs (largest first) are
@@ -243,8 +267,8 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->max_m = 0;
     int64_t cell = 0, link = 0, flags = 0;
     tbw = hrow = vcol = 0;
-    // (cells, pair) of every pair: one sort gives every work order below
-    std::vector<std::pair<int64_t, int32_t>> by_size((size_t)n);
+    // every work order below comes from one order of the pairs by size
+    std::vector<uint64_t> size_key((size_t)n);  // ascending key = descending cells
     for (int64_t k = 0; k < n; ++k) {
         PairGeom &g = p->geom_h[k];
         g.n = (int32_t)(sd[k + 1] - sd[k]);
@@ -272,7 +296,7 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
             g.nchunk = 1;
             g.flag_off = -1;
         }
-        by_size[(size_t)k] = {-cells, (int32_t)k};
+        size_key[(size_t)k] = (uint64_t)((int64_t)1 << 62) - (uint64_t)cells;
         cell += cells;
         tbw += ns * nb * 32;
         link += std::min(g.n, g.m);
@@ -284,16 +308,13 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->link_cap = link;
     p->n_flags = flags;
 
-    // pairs by decreasing size, ties by index (the order of a stable sort)
-    std::sort(by_size.begin(), by_size.end());
-    p->pair_order_h.resize(n);
+    // pairs by decreasing size, ties by index
+    radix_order(size_key, p->pair_order_h);
     std::vector<int32_t> small, tiled;
-    for (int64_t x = 0; x < n; ++x) {
-        const int32_t k = by_size[(size_t)x].second;
-        p->pair_order_h[x] = k;
+    for (int32_t k : p->pair_order_h) {
         if (p->geom_h[k].flag_off >= 0)
             tiled.push_back(k);
-        else if (by_size[(size_t)x].first < 0)
+        else if ((int64_t)p->geom_h[k].n * p->geom_h[k].m > 0)
             small.push_back(k);
     }
 
