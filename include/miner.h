@@ -103,6 +103,11 @@ typedef struct mine_plan mine_plan;
  * lists unsorted or repeated or out of range. */
 int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
                      mine_plan **out, miner_stream_t stream);
+/* Releases the plan without waiting: its device memory returns to the
+ * library's pool (a stream-ordered pool per device that keeps up to 16 GiB
+ * of freed memory for later plans) once the work enqueued by the last call
+ * that used the plan has finished on that call's stream.  Inputs may be freed
+ * once that work has finished. */
 void mine_plan_destroy(mine_plan *plan);
 
 int64_t mine_plan_n_pairs(const mine_plan *plan);

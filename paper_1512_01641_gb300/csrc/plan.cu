@@ -1,5 +1,6 @@
 // Plan creation, input validation and the C ABI entry points of miner.h.
 #include <algorithm>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -74,11 +75,41 @@ __global__ void block_tokens_kernel(DevCorpus tgt, const PairGeom *geom, int64_t
     }
 }
 
+// Plan scratch comes from a library-owned stream-ordered memory pool per
+// device that keeps up to kPoolKeep bytes of freed memory for reuse, so that
+// creating and destroying plans batch after batch neither maps new memory nor
+// synchronises the device (beyond kPoolKeep, freed memory goes back to the
+// system at the next synchronisation).
+constexpr int kMaxDevices = 64;
+constexpr uint64_t kPoolKeep = 16ull << 30;
+cudaError_t scratch_pool(int device, cudaMemPool_t *out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaError_t e = cudaMemPoolCreate(&pools[device], &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = kPoolKeep;
+        e = cudaMemPoolSetAttribute(pools[device], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+    }
+    *out = pools[device];
+    return cudaSuccess;
+}
+
 template <class T>
-cudaError_t dalloc(T **p, size_t n) {
+cudaError_t dalloc(T **p, size_t n, int device, cudaStream_t st) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cudaMalloc((void **)p, n * sizeof(T));
+    cudaMemPool_t pool;
+    const cudaError_t e = scratch_pool(device, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync((void **)p, n * sizeof(T), pool, st);
 }
 
 }  // namespace
@@ -150,6 +181,8 @@ struct mine_plan {
     // whole-batch CUDA graph of mine_pairs, keyed by the output buffers and
     // the parameters baked into its kernel arguments
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // plan-owned: releases the scratch, rebuilds work lists
+    cudaEvent_t done = nullptr;         // recorded after the work of every call that used the plan
     cudaGraphExec_t graph = nullptr;
     mine_out graph_out{};
     mine_params graph_params{};
@@ -174,6 +207,16 @@ static cudaError_t timed(mine_plan *p, int kind, cudaStream_t st, F &&f) {
     }
     return e;
 }
+
+// Records the plan's completion event on the caller's stream when a call
+// that enqueued work returns (not while the plan captures its own graph).
+struct DoneMark {
+    mine_plan *p;
+    cudaStream_t st;
+    ~DoneMark() {
+        if (p && p->done && st != p->cap_stream) cudaEventRecord(p->done, st);
+    }
+};
 
 static void drain_pending(mine_plan *p) {
     for (auto &q : p->pending) {
@@ -210,8 +253,15 @@ static void plan_free(mine_plan *p) {
     void *bufs[] = {p->geom, p->pair_order, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
                     p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
                     p->S.diag_off, p->S.n_links, p->stats};
-    for (void *b : bufs)
-        if (b) cudaFree(b);
+    // back to the pool after the work last enqueued on the plan (the
+    // caller's streams may be gone by now: the plan waits on its own event)
+    if (p->own_stream) {
+        if (p->done) cudaStreamWaitEvent(p->own_stream, p->done, 0);
+        for (void *b : bufs)
+            if (b) cudaFreeAsync(b, p->own_stream);
+        cudaStreamDestroy(p->own_stream);
+    }
+    if (p->done) cudaEventDestroy(p->done);
     delete p;
 }
 
@@ -376,7 +426,9 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     cudaStream_t st = (cudaStream_t)stream;
     mine_plan *p = new (std::nothrow) mine_plan();
     if (!p) return MINE_ENOMEM;
+    DoneMark mark{nullptr, st};  // armed once the plan exists
     auto fail = [&](int code) {
+        mark.p = nullptr;
         plan_free(p);
         return code;
     };
@@ -390,6 +442,9 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         }                                                                           \
     } while (0)
     PLAN_CK(cudaGetDevice(&p->device));
+    PLAN_CK(cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking));
+    PLAN_CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    mark.p = p;
     PLAN_CK(cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, p->device));
     p->src = {src->doc_sent_off, src->sent_tok_off, src->tok, src->n_tok};
     p->tgt = {tgt->doc_sent_off, tgt->sent_tok_off, tgt->tok, tgt->n_tok};
@@ -410,8 +465,8 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
             return fail(MINE_EINVAL);
 
     // validation kernels
-    PLAN_CK(dalloc(&p->S.status, 4));
-    PLAN_CK(dalloc(&p->stats, 4));
+    PLAN_CK(dalloc(&p->S.status, 4, p->device, st));
+    PLAN_CK(dalloc(&p->stats, 4, p->device, st));
     PLAN_CK(cudaMemsetAsync(p->S.status, 0, 4 * sizeof(uint32_t), st));
     PLAN_CK(cudaMemsetAsync(p->stats, 0, 4 * sizeof(int32_t), st));
     if (src->n_sents > 0)
@@ -426,26 +481,26 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     std::vector<FillItem> fitems;
     int64_t tbw = 0, hrow = 0, vcol = 0;
     build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
-    PLAN_CK(dalloc(&p->geom, n));
+    PLAN_CK(dalloc(&p->geom, n, p->device, st));
     PLAN_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
-    PLAN_CK(dalloc(&p->pair_order, n));
+    PLAN_CK(dalloc(&p->pair_order, n, p->device, st));
     PLAN_CK(cudaMemcpyAsync(p->pair_order, p->pair_order_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    PLAN_CK(dalloc(&p->fill_items, fitems.size()));
+    PLAN_CK(dalloc(&p->fill_items, fitems.size(), p->device, st));
     PLAN_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice, st));
 
     // scratch
-    PLAN_CK(dalloc(&p->counts, 2 * p->n_cells));
-    PLAN_CK(dalloc(&p->S.tb, tbw));
-    PLAN_CK(dalloc(&p->S.hrow, hrow));
-    PLAN_CK(dalloc(&p->S.vcol, vcol));
-    PLAN_CK(dalloc(&p->S.flags, p->n_flags));
-    PLAN_CK(dalloc(&p->S.queue, 1));
-    PLAN_CK(dalloc(&p->S.diag_i, p->link_cap));
-    PLAN_CK(dalloc(&p->S.diag_j, p->link_cap));
-    PLAN_CK(dalloc(&p->S.diag_s, p->link_cap));
-    PLAN_CK(dalloc(&p->S.n_diag, n));
-    PLAN_CK(dalloc(&p->S.diag_off, n + 1));
-    PLAN_CK(dalloc(&p->S.n_links, n));
+    PLAN_CK(dalloc(&p->counts, 2 * p->n_cells, p->device, st));
+    PLAN_CK(dalloc(&p->S.tb, tbw, p->device, st));
+    PLAN_CK(dalloc(&p->S.hrow, hrow, p->device, st));
+    PLAN_CK(dalloc(&p->S.vcol, vcol, p->device, st));
+    PLAN_CK(dalloc(&p->S.flags, p->n_flags, p->device, st));
+    PLAN_CK(dalloc(&p->S.queue, 1, p->device, st));
+    PLAN_CK(dalloc(&p->S.diag_i, p->link_cap, p->device, st));
+    PLAN_CK(dalloc(&p->S.diag_j, p->link_cap, p->device, st));
+    PLAN_CK(dalloc(&p->S.diag_s, p->link_cap, p->device, st));
+    PLAN_CK(dalloc(&p->S.n_diag, n, p->device, st));
+    PLAN_CK(dalloc(&p->S.diag_off, n + 1, p->device, st));
+    PLAN_CK(dalloc(&p->S.n_links, n, p->device, st));
     PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
 
     uint32_t status[4];
@@ -469,7 +524,7 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
             for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
         }
         p->n_strip_items = (int64_t)sitems.size();
-        PLAN_CK(dalloc(&p->strip_items, sitems.size()));
+        PLAN_CK(dalloc(&p->strip_items, sitems.size(), p->device, st));
         PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
                                 cudaMemcpyHostToDevice, st));
         PLAN_CK(cudaStreamSynchronize(st));
@@ -477,7 +532,7 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
         std::vector<CountItem> citems;
         build_count_items(p, citems);
         p->n_count_items = (int64_t)citems.size();
-        PLAN_CK(dalloc(&p->count_items, citems.size()));
+        PLAN_CK(dalloc(&p->count_items, citems.size(), p->device, st));
         PLAN_CK(cudaMemcpyAsync(p->count_items, citems.data(), citems.size() * sizeof(CountItem),
                                 cudaMemcpyHostToDevice, st));
         PLAN_CK(cudaStreamSynchronize(st));
@@ -509,6 +564,7 @@ int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
     if (p->n_cells == 0) return MINE_OK;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     if (p->use_strips) {
         MINE_CK(timed(p, kKCount, st, [&] {
             return launch_count_strips(p->src, p->tgt, p->dict, p->geom, p->strip_items, p->n_strip_items,
@@ -527,6 +583,7 @@ int mine_score(mine_plan *p, const mine_params *params, const uint8_t *counts, f
                miner_stream_t stream) {
     if (!p || !params || ((!counts || !s) && p->n_cells > 0)) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     const DevParams P = to_dev(*params);
     MINE_CK(timed(p, kKScore, st,
                   [&] { return launch_score(p->src, p->tgt, p->geom, p->n_pairs, P, counts, s, feat, st); }));
@@ -540,6 +597,7 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
     if (p->link_cap > 0 && (!out->link_i || !out->link_j || !out->link_s)) return MINE_EINVAL;
     if (p->n_cells > 0 && !counts) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     const DevParams P = to_dev(*params);
     const AlignScratch &S = p->S;
     const int64_t n = p->n_pairs;
@@ -571,6 +629,7 @@ static int enqueue_pairs(mine_plan *p, const mine_params *params, mine_out *out,
 int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_stream_t stream) {
     if (!p || !params || !out) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     if (p->timing || !p->knobs.use_graph) return enqueue_pairs(p, params, out, st);
     // capture once on a plan-owned stream (the caller's stream may be the
     // legacy default stream, which cannot be captured), replay on the caller's
@@ -717,6 +776,7 @@ int softnw_fwd(mine_plan *p, const mine_params *params, const softnw_opts *opts,
     if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
     if (p->max_m > (1 << 20)) return MINE_ENOTSUP;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     const SoftScratch W = soft_scratch(p, ws);
     const DevParams P = to_dev(*params);
     MINE_CK(timed(p, kKSoftFwd, st, [&] {
@@ -736,6 +796,7 @@ int softnw_bwd(mine_plan *p, const mine_params *params, const softnw_opts *opts,
     if (!p || !params || !ws || !grad || !soft_args(p, opts, A, order, n)) return MINE_EINVAL;
     if (p->n_cells > 0 && (!counts || !gold)) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     const SoftScratch W = soft_scratch(p, ws);
     const DevParams P = to_dev(*params);
     MINE_CK(timed(p, kKSoftBwd, st, [&] {
@@ -748,6 +809,7 @@ int softnw_bwd(mine_plan *p, const mine_params *params, const softnw_opts *opts,
 int mine_link_gold_counts(mine_plan *p, const mine_out *out, const uint8_t *gold, uint64_t *counts3,
                           miner_stream_t stream) {
     if (!p || !out || !out->link_off || !counts3 || (p->n_cells > 0 && !gold)) return MINE_EINVAL;
+    DoneMark mark{p, (cudaStream_t)stream};
     MINE_CK(launch_link_gold(p->geom, p->n_pairs, out->link_off, out->link_i, out->link_j, gold,
                              reinterpret_cast<unsigned long long *>(counts3), p->n_sms, (cudaStream_t)stream));
     return MINE_OK;
@@ -756,6 +818,7 @@ int mine_link_gold_counts(mine_plan *p, const mine_out *out, const uint8_t *gold
 int mine_plan_check(mine_plan *p, miner_stream_t stream) {
     if (!p) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
     uint32_t status = 0;
     MINE_CK(cudaMemcpyAsync(&status, p->S.status, sizeof status, cudaMemcpyDeviceToHost, st));
     MINE_CK(cudaStreamSynchronize(st));
@@ -816,14 +879,17 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
     int64_t tbw, hrow, vcol;
     build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
     MINE_CK(cudaDeviceSynchronize());
-    cudaFree(p->fill_items);
-    cudaFree(p->S.flags);
+    cudaStream_t st = p->own_stream;
+    MINE_CK(cudaFreeAsync(p->fill_items, st));
+    MINE_CK(cudaFreeAsync(p->S.flags, st));
     p->fill_items = nullptr;
     p->S.flags = nullptr;
-    MINE_CK(dalloc(&p->fill_items, fitems.size()));
-    MINE_CK(dalloc(&p->S.flags, p->n_flags));
-    MINE_CK(cudaMemcpy(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice));
-    MINE_CK(cudaMemcpy(p->geom, p->geom_h.data(), p->n_pairs * sizeof(PairGeom), cudaMemcpyHostToDevice));
+    MINE_CK(dalloc(&p->fill_items, fitems.size(), p->device, st));
+    MINE_CK(dalloc(&p->S.flags, p->n_flags, p->device, st));
+    MINE_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice,
+                            st));
+    MINE_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), p->n_pairs * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
+    MINE_CK(cudaStreamSynchronize(st));
     return MINE_OK;
 }
 
