@@ -1,0 +1,40 @@
+"""Streaming batches from host memory through BatchPipeline gives, batch by
+batch, exactly the links and scores of Plan.mine on the same batch."""
+import numpy as np
+import pytest
+
+from paper_1512_01641_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pipeline_results_equal_plan_mine():
+    import torch
+    from paper_1512_01641_gb300 import miner
+    from paper_1512_01641_gb300.pipeline import BatchPipeline
+    rng = np.random.Generator(np.random.PCG64(11))
+    dic = synth.make_dictionary(rng, 3000, 3000)
+    batches = [synth.make_batch(90 + k, 40 + 7 * k, dic=dic) for k in range(4)]
+    params = miner.MineParams()
+    ref = []
+    for b in batches:
+        with miner.Plan(miner.DeviceBatch.from_batch(b)) as plan:
+            out = plan.mine(params)
+            n = int(out["link_off"][-1])
+            ref.append({"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"][:plan.n_pairs].cpu(),
+                        "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(),
+                        "link_s": out["link_s"][:n].cpu()})
+    pipe = BatchPipeline(params, dic.v_src, dic.v_tgt)
+    got = []
+    for b in batches:
+        host = [b.src.doc_sent_off, b.src.sent_tok_off, b.src.tok, b.tgt.doc_sent_off, b.tgt.sent_tok_off,
+                b.tgt.tok, b.dic.off, b.dic.tgt]
+        r = pipe.submit([torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host])
+        if r is not None:
+            got.append(r)
+    got.append(pipe.flush())
+    assert pipe.flush() is None
+    assert len(got) == len(batches)
+    for a, b in zip(ref, got):
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
