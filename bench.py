@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--tune-eval", type=int, default=10_000)
     ap.add_argument("--tune-steps", type=int, default=200)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--soft-step", action="store_true",
+                    help="only time one soft-NW forward+backward on a 4,096-pair tuning minibatch (profiling)")
     return ap.parse_args()
 
 
@@ -215,6 +217,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def soft_step(args):
+    """One soft-NW forward + backward (the unit of an Adam step) on 4,096
+    planted pairs of the tuning batch, after two warm-up passes; prints one
+    JSON line with the CUDA-event times."""
+    import torch
+    from paper_1512_01641_gb300 import miner, tune
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
+    dic = synth.make_dictionary(rng, 50_000, 50_000)
+    td = tune.TuneData(synth.tune_batch(4096, seed=synth.SEED_BASE + 4, dic=dic))
+    al = miner.SoftAligner(td.plan, td.counts, td.gold, 0.1, 0.05)
+    p = miner.params_from_theta(tune.THETA0)
+    for _ in range(max(args.warmup, 2)):
+        al.forward(p)
+        al.backward(p)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    al.forward(p)
+    ev[1].record()
+    al.backward(p)
+    ev[2].record()
+    torch.cuda.synchronize()
+    print(json.dumps({"soft_step": {"pairs": td.plan.n_pairs, "cells": td.plan.n_cells, "gamma": 0.1,
+                                    "forward_ms": ev[0].elapsed_time(ev[1]),
+                                    "backward_ms": ev[1].elapsed_time(ev[2])}}))
+
+
 def run_tune(args):
     """Soft-NW gradient tuning (Adam) vs the 7^3 grid search, same GPU,
     evaluated by hard-NW micro-F1 on held-out planted pairs."""
@@ -291,6 +320,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.soft_step:
+        soft_step(args)
         return
     import torch
     rank, world, lrank = dist_env()
