@@ -86,7 +86,7 @@ def grid_search(train: TuneData, held_out: TuneData, theta0=THETA0, grid=GRID) -
 
 
 def adam_tune(train: TuneData, held_out: TuneData, steps: int = 200, lr: float = 0.05, gamma: float = 0.1,
-              tau: float = 0.05, betas=(0.9, 0.999), theta0=THETA0, batch_pairs: int | None = 4096,
+              tau: float = 0.05, betas=(0.9, 0.999), theta0=THETA0, batch_pairs: int | None = 1024,
               seed: int = 0) -> TuneResult:
     """Adam on the soft-alignment loss; every step is one softnw_fwd + softnw_bwd
     over a minibatch of batch_pairs training pairs drawn without replacement
