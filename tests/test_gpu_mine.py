@@ -361,3 +361,33 @@ def test_bounded_tile_wait_reports_timeout_and_recovers():
         got = plan.mine(p)
         plan.check()
         _outputs_equal(ref, got, batch.n_pairs)
+
+
+def test_destroy_while_mining_in_flight_then_reuse_pool():
+    """mine_plan_destroy returns at once; the scratch goes back to the pool only
+    after the plan's work has finished, so a plan destroyed with its mining
+    still in flight on a side stream leaves that output intact, and a new plan
+    that reuses the memory right away mines correctly."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    a = synth.make_batch(95, 60, v_src=3000, v_tgt=3000)
+    b = synth.make_batch(96, 50, v_src=3000, v_tgt=3000)
+    p = _params()
+    refs = []
+    for bt in (a, b):
+        with miner.Plan(miner.DeviceBatch.from_batch(bt)) as plan:
+            out = plan.mine(p)
+            torch.cuda.synchronize()
+            refs.append({k: v.clone() for k, v in out.items()})
+    side = torch.cuda.Stream()
+    for rep in range(3):
+        pa = miner.Plan(miner.DeviceBatch.from_batch(a), stream=side)
+        with torch.cuda.stream(side):
+            oa = pa.mine(p, stream=side)
+        pa.close()  # work still in flight on `side`
+        with miner.Plan(miner.DeviceBatch.from_batch(b)) as pb:
+            ob = pb.mine(p)
+            torch.cuda.synchronize()
+            _outputs_equal(refs[1], ob, b.n_pairs)
+        side.synchronize()
+        _outputs_equal(refs[0], oa, a.n_pairs)
