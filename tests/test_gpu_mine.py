@@ -391,3 +391,50 @@ def test_destroy_while_mining_in_flight_then_reuse_pool():
             _outputs_equal(refs[1], ob, b.n_pairs)
         side.synchronize()
         _outputs_equal(refs[0], oa, a.n_pairs)
+
+
+@pytest.mark.slow
+def test_uneven_batch_full_size_in_the_bench_launch_configuration():
+    """The bench workload as the bench launches it: 100,000 Wikipedia-shaped
+    pairs + 8 pairs of 5,000 x 5,000 sentences in one graph-replayed
+    mine_pairs with 64-column tiles.  200 sampled small pairs (the largest
+    included) are compared in full with the oracle (counts, score, path), two
+    long pairs by score and path, and every long pair on 400 sampled cells of
+    its counts."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = synth.uneven_batch()
+    n = batch.n_pairs
+    p_all = _params(thr=-1.0)
+    with miner.Plan(miner.DeviceBatch.from_batch(batch)) as plan:
+        plan.set_option("tile_cols", 64)
+        plan.set_option("tile_min_cells", 1 << 20)
+        plan.mine(p_all)
+        out = plan.mine(p_all)  # graph replay
+        counts = plan.count()
+        torch.cuda.synchronize()
+        assert plan.get_option("graph_captures") >= 1
+        plan.check()
+        off = plan.cell_offsets
+        score = out["pair_score"][:n].cpu().numpy()
+        links = miner.links_per_pair(out, n)
+        sizes = batch.src.doc_sizes() * batch.tgt.doc_sizes()
+        rng = np.random.default_rng(5)
+        small = np.arange(n - 8)
+        pick = np.unique(np.concatenate([small[np.argsort(sizes[small])[-5:]], rng.choice(small, 195, replace=False)]))
+        sub = batch.subset(pick)
+        ref = oracle.mine(sub, p_all.w, p_all.b, p_all.gap, p_all.thr, want_counts=True, want_sim=True)
+        for x, k in enumerate(pick):
+            got = counts[off[k]:off[k + 1]].cpu().numpy().reshape(ref["counts"][x].shape)
+            assert np.array_equal(got, ref["counts"][x]), k
+        ties = check_alignment(sub, p_all, {"score": score[pick], "links": [links[k] for k in pick]}, ref)
+        assert ties <= len(pick) // 3
+        for k in (n - 8, n - 7):
+            one = batch.subset(np.array([k]))
+            r1 = oracle.mine(one, p_all.w, p_all.b, p_all.gap, p_all.thr, want_sim=True)
+            assert check_alignment(one, p_all, {"score": score[[k]], "links": [links[k]]}, r1) <= 1
+        for k in range(n - 8, n):
+            src, tgt = batch.src.doc(k), batch.tgt.doc(k)
+            c = counts[off[k]:off[k + 1]].view(5000, 5000, 2)
+            for i, j in rng.integers(0, 5000, size=(400, 2)):
+                assert tuple(c[i, j].tolist()) == oracle.counts(src[i], tgt[j], batch.dic), (k, i, j)
