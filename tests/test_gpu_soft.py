@@ -230,3 +230,35 @@ def test_split_sweep_multi_strip_pair_vs_oracle():
         Vo, Eo, _ = oracle.soft_nw(r["sim"][k], THETA[5], 0.1)
         assert abs(value[k] - Vo[-1, -1]) <= 1e-4 * max(1.0, abs(Vo[-1, -1]))
         assert np.abs(E[off[k]:off[k + 1]].reshape(Eo.shape) - Eo).max() <= 2e-4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("gamma", [1.0, 0.1, 0.01])
+def test_soft_full_size_4096_pairs_sampled(gamma):
+    """The soft configuration at full size (4,096 planted pairs of ~100 x 100
+    sentences, the long ones split over warps): soft V(N,M) and the expected
+    alignment E of 24 sampled pairs against the FP64 oracle."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = synth.soft_batch()
+    plan = miner.Plan(miner.DeviceBatch.from_batch(batch))
+    counts = plan.count()
+    gold = torch.from_numpy(miner.gold_cells(batch, plan)).cuda()
+    al = miner.SoftAligner(plan, counts, gold, gamma, TAU)
+    params = miner.params_from_theta(THETA)
+    _, value, exp = al.forward(params, want_value=True, want_expected=True)
+    plan.check()
+    sizes = batch.src.doc_sizes() * batch.tgt.doc_sizes()
+    rng = np.random.default_rng(9)
+    pick = np.unique(np.concatenate([np.argsort(sizes)[-4:], rng.choice(batch.n_pairs, 20, replace=False)]))
+    sub = batch.subset(pick)
+    r = oracle.mine(sub, THETA[:4], THETA[4], THETA[5], THETA[6], want_sim=True)
+    off = plan.cell_offsets
+    etol = 2e-3 if gamma < 0.05 else 2e-4
+    for x, k in enumerate(pick):
+        V, E, _ = oracle.soft_nw(r["sim"][x], THETA[5], gamma)
+        v = float(value[k])
+        assert abs(v - V[-1, -1]) <= 1e-4 * max(1.0, abs(V[-1, -1])), (k, v, V[-1, -1])
+        Eg = exp[off[k]:off[k + 1]].cpu().numpy().reshape(E.shape)
+        assert np.abs(Eg - E).max() <= etol, (k, np.abs(Eg - E).max())
+    plan.close()
