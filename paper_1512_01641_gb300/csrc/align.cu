@@ -85,6 +85,11 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
         C.tsent = tgt.sent + tgt.doc[w.pair];
         float *hrow = S.hrow + g.hrow_off;
         for (int s = w.s0; s < w.s1; ++s) {
+            // the loads that do not depend on the neighbouring tiles go out
+            // before the wait for them
+            FillAhead ah;
+            int nb;
+            fill_strip_prepare(C, s, src.sent + sbase, g.cell_off, ah, nb);
             if (tiled) {
                 if (lane == 0) {
                     bool ok = true;
@@ -98,7 +103,7 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             }
             float b = -C.two_p;
             if (C.c0 > 0 && 32 * s + lane < C.N) b = __ldcg(S.vcol + g.vcol_off + 32 * s + lane);
-            b = fill_strip(C, s, src.sent + sbase, counts, g.cell_off, hrow, S.tb + g.tb_off, nblk_pair, b);
+            b = fill_strip_run(C, s, hrow, S.tb + g.tb_off, nblk_pair, b, ah, nb);
             if (tiled) {
                 if (C.c1 < C.M && C.rv) __stcg(S.vcol + g.vcol_off + C.r, b);
                 __threadfence();

@@ -93,12 +93,21 @@ struct FillAhead {
 };
 
 // Loads the look-ahead values of block jb.
-__device__ __forceinline__ void fill_ahead(const FillCtx &C, int jb, int nb, bool first_strip,
-                                           const float *__restrict__ hrow, FillAhead &A) {
+__device__ __forceinline__ void fill_ahead_hv(const FillCtx &C, int jb, int nb, bool first_strip,
+                                              const float *__restrict__ hrow, FillAhead &A) {
     const int col = C.c0 + 32 * jb + C.lane;
     const bool in = jb < nb && col < C.c1;
     A.hv = first_strip ? -C.two_p : (in ? __ldcg(hrow + col) : 0.0f);
+}
+__device__ __forceinline__ void fill_ahead_lt(const FillCtx &C, int jb, int nb, FillAhead &A) {
+    const int col = C.c0 + 32 * jb + C.lane;
+    const bool in = jb < nb && col < C.c1;
     A.lt = in ? (int)(C.tsent[col + 1] - C.tsent[col]) : 1;
+}
+__device__ __forceinline__ void fill_ahead(const FillCtx &C, int jb, int nb, bool first_strip,
+                                           const float *__restrict__ hrow, FillAhead &A) {
+    fill_ahead_hv(C, jb, nb, first_strip, hrow, A);
+    fill_ahead_lt(C, jb, nb, A);
 }
 
 // One 32-column block iteration of a strip sweep.  cur receives the
@@ -166,33 +175,41 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
 }
 
 
-// Sweep strip s (rows 32s..32s+31) over columns [C.c0, C.c1).  b0 holds the
-// LEFT candidates of column c0 (-2p at the left border); returns each lane's
-// LEFT candidate after the last column.  hrow holds the UP candidates of the
-// row above the strip and receives those of the strip's last row (lane 31
-// writes column j at the step after every lane has read it: block jb reads
-// columns 32 jb .. 32 jb + 31 one block ahead, and lane 31 reaches them only
-// in blocks jb and jb + 1).
-__device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__restrict__ ssent,
-                                            const uint8_t *__restrict__ counts, int64_t cell_off,
-                                            float *__restrict__ hrow, uint64_t *__restrict__ tb_pair,
-                                            int nblk_pair, float b0) {
+// First part of the sweep of strip s over columns [C.c0, C.c1): everything
+// that does not depend on the strip above or the tile to the left -- row
+// constants, block 0's target sentence lengths and the staging of its count
+// bytes -- so that a tile can start these loads before it waits for its
+// neighbours.  nb receives the number of 32-column blocks.
+__device__ __forceinline__ void fill_strip_prepare(FillCtx &C, int s, const int64_t *__restrict__ ssent,
+                                                   int64_t cell_off, FillAhead &ah, int &nb) {
     const int lane = C.lane;
     C.r = 32 * s + lane;
     C.rv = C.r < C.N;
     const int ls = C.rv ? (int)(ssent[C.r + 1] - ssent[C.r]) : 1;
     C.row = sim_row(ls, C.P);
     C.row_byte = 2 * (cell_off + (int64_t)C.r * C.M);
-    const int nb = (C.c1 - C.c0 + 31) >> 5;
+    nb = (C.c1 - C.c0 + 31) >> 5;
+    fill_ahead_lt(C, 0, nb, ah);
+    fill_stage(C, 0, nb);
+}
+
+// The sweep itself, once the strip's boundaries are complete.  b0 holds the
+// LEFT candidates of column c0 (-2p at the left border); returns each lane's
+// LEFT candidate after the last column.  hrow holds the UP candidates of the
+// row above the strip and receives those of the strip's last row (lane 31
+// writes column j at the step after every lane has read it: block jb reads
+// columns 32 jb .. 32 jb + 31 one block ahead, and lane 31 reaches them only
+// in blocks jb and jb + 1).
+__device__ __forceinline__ float fill_strip_run(FillCtx &C, int s, float *__restrict__ hrow,
+                                                uint64_t *__restrict__ tb_pair, int nblk_pair, float b0,
+                                                FillAhead &ah, int nb) {
     float b = b0, a_down = 0.0f;
     float A[32], B[32];
 #pragma unroll
     for (int x = 0; x < 32; ++x) B[x] = 0.0f;
     uint64_t RA = 0, RB = 0;
     uint64_t *tb_strip = tb_pair + (int64_t)s * nblk_pair * 32;
-    FillAhead ah;
-    fill_ahead(C, 0, nb, s == 0, hrow, ah);
-    fill_stage(C, 0, nb);
+    fill_ahead_hv(C, 0, nb, s == 0, hrow, ah);
     // one instance of the (fully unrolled) block body: the current block's
     // similarities become the previous block's by a register copy, which
     // keeps the loop's code half the size of two alternating instances
@@ -204,6 +221,18 @@ __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__
         RB = RA;
     }
     return b;
+}
+
+// Sweep strip s (rows 32s..32s+31) over columns [C.c0, C.c1) in one go.
+__device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__restrict__ ssent,
+                                            const uint8_t *__restrict__ counts, int64_t cell_off,
+                                            float *__restrict__ hrow, uint64_t *__restrict__ tb_pair,
+                                            int nblk_pair, float b0) {
+    (void)counts;  // read through C.counts (staged)
+    FillAhead ah;
+    int nb;
+    fill_strip_prepare(C, s, ssent, cell_off, ah, nb);
+    return fill_strip_run(C, s, hrow, tb_pair, nblk_pair, b0, ah, nb);
 }
 
 // Walk back from (N,M) to (0,0) for one pair (whole warp, same path in every
