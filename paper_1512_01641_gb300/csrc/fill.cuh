@@ -131,14 +131,14 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         fill_stage(C, jb + 1, nb);
         const unsigned char *st = fill_stage_wait(C, jb);
         // branch-free, so that the 32 independent cells overlap: every cell
-        // is computed from the staged row (in bounds for any c) and the ones
-        // outside the pair are zeroed
+        // is computed from the staged row (in bounds for any c); a cell
+        // outside the pair gets a finite value from stale bytes, which only
+        // feeds steps whose results are discarded
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const int c = (x - lane) & 31;
             const uchar2 q = *reinterpret_cast<const uchar2 *>(st + 2 * c);
-            const float v = similarity(q.x, q.y, C.row, C.colv[c], C.k);
-            cur[x] = (C.rv && col_base + c < C.c1) ? v : 0.0f;
+            cur[x] = similarity(q.x, q.y, C.row, C.colv[c], C.k);
         }
     }
     rc = 0;
@@ -154,11 +154,13 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         // one max waits for the shuffled value.  a_down needs no commit: a
         // lane's output of an invalid step reaches the next lane only at a
         // step where that lane is invalid too (before its first column, after
-        // its last, or below the last row).
+        // its last, or below the last row).  Nor do the code bits: those of
+        // an invalid cell land in a word that is never stored (before the
+        // first block) or at a cell the walk never visits.
         const bool valid = C.rv && j >= C.c0 && j < C.c1;
         const float d = fmaxf(fmaxf(sv, b), a_up);
         const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : 0u);
-        rc |= valid ? (uint64_t)code << (2 * u) : 0ull;
+        rc |= (uint64_t)code << (2 * u);
         const float e = __fsub_rn(d, C.two_p);
         const float nb2 = __fsub_rn(e, a_up);
         a_down = __fsub_rn(e, b);
