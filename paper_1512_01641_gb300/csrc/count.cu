@@ -50,23 +50,6 @@ __device__ __forceinline__ int table_insert(int32_t *key, int32_t t) {
     return -1;
 }
 
-// As table_insert, and tells whether this call created the key.
-template <int LOG_SLOTS>
-__device__ __forceinline__ bool table_insert_new(int32_t *key, int32_t t, int &slot) {
-    constexpr uint32_t S = 1u << LOG_SLOTS;
-    uint32_t h = hash_slot(t, LOG_SLOTS);
-    for (uint32_t n = 0; n < S; ++n) {
-        const int32_t old = atomicCAS(&key[h], kEmpty, t);
-        if (old == kEmpty || old == t) {
-            slot = (int)h;
-            return old == kEmpty;
-        }
-        h = (h + 1) & (S - 1);
-    }
-    slot = -1;
-    return false;
-}
-
 // Continues a lookup of t at slot h (after a first probe that found
 // neither t nor an empty slot).
 template <int LOG_SLOTS>
@@ -234,11 +217,10 @@ struct alignas(16) StripSmem {
     uint8_t colid[kTokCap];
     uint8_t rowid[kPosCap];
     int32_t ctpre[33];         // per column of the staged block: first token index; [32] = token count
-    int32_t n_keys;            // distinct keys of the row table being built
     int32_t n_ent;             // translation entries of the row table
     int32_t full;              // the row group does not fit
     int32_t tsh;               // index in gh of the staged block's first token
-    int32_t pad2[2];
+    int32_t pad2[3];
 };
 static_assert(kTokCap >= kPosCap, "shared buffer sizes");
 static_assert(offsetof(StripSmem<11>, gh) % 16 == 0 && sizeof(StripSmem<11>) % 16 == 0, "bulk copy alignment");
@@ -316,10 +298,10 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int &total) {
 }
 
 // The row group of an item starts as the whole strip; when its translations
-// would fill the row table beyond kMaxLoad (or the entry buffer), the group is
-// halved and rebuilt -- rows are independent, so any grouping gives the same
-// counts.
-constexpr float kMaxLoad = 0.85f;
+// would overfill the entry buffer (kEntCap entries, which also keeps the row
+// table at most 71 % full: at most one key per entry), the group is halved and
+// rebuilt -- rows are independent, so any grouping gives the same counts.
+static_assert(kEntCap * 100 <= (1 << kStripLogSlots) * 71, "entry cap bounds the row table's load");
 
 template <int LOG_SLOTS, int K>
 __global__ void __launch_bounds__(kStripThreads, 5)
@@ -364,7 +346,6 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                 reinterpret_cast<uint4 *>(sm.rowmask)[x] = make_uint4(0, 0, 0, 0);
             }
             if (tid == 0) {
-                sm.n_keys = 0;
                 sm.n_ent = 0;
                 sm.full = 0;
             }
@@ -402,23 +383,29 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
                 }
                 if (p < n_pos) {
                     const uint32_t rbit = 1u << sm.rowid[p];
-                    for (int32_t e = e0; e < e1; ++e) {
-                        int h;
-                        const bool fresh = table_insert_new<LOG_SLOTS>(sm.key, dict.tgt[e], h);
-                        if (h < 0) {
-                            sm.full = 1;
-                            sm.ent[o + (e - e0)] = (uint32_t)p << 16;
-                            continue;
+                    // the position's translations, four loads at a time
+                    for (int32_t e = e0; e < e1; e += 4) {
+                        int32_t tt[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) tt[u] = e + u < e1 ? dict.tgt[e + u] : kEmpty;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (e + u >= e1) break;
+                            const int h = table_insert<LOG_SLOTS>(sm.key, tt[u]);
+                            if (h < 0) {
+                                sm.full = 1;
+                                sm.ent[o + (e + u - e0)] = (uint32_t)p << 16;
+                                continue;
+                            }
+                            atomicOr(&sm.rowmask[h], rbit);
+                            sm.ent[o + (e + u - e0)] = (uint32_t)h | ((uint32_t)p << 16);
                         }
-                        if (fresh) atomicAdd(&sm.n_keys, 1);
-                        atomicOr(&sm.rowmask[h], rbit);
-                        sm.ent[o + (e - e0)] = (uint32_t)h | ((uint32_t)p << 16);
                     }
                 }
             }
             fence_proxy_async();  // the source tokens are read before a copy replaces them
             __syncthreads();
-            const bool full = sm.full != 0 || sm.n_keys > (int)(kMaxLoad * S);
+            const bool full = sm.full != 0;
             const int n_ent = min(sm.n_ent, kEntCap);
             if (full) {
                 __syncthreads();  // everyone has read the flags before the rebuild clears them
