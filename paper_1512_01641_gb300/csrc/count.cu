@@ -264,6 +264,20 @@ __device__ __forceinline__ bool stage_wait(bool bulk, uint64_t *bar, uint32_t &p
     return ok;
 }
 
+// Each thread: wait for the staged copy (if any), with no CTA barrier.  On a
+// copy that never completes the status is flagged (after a second bounded
+// wait that lets the copy in flight land) and the thread carries on: every
+// index the block derives from the staged words stays in bounds, and the host
+// discards the results of a launch that flagged a timeout.
+__device__ __forceinline__ void stage_wait_own(bool bulk, uint64_t *bar, uint32_t &phase, uint32_t *status) {
+    if (!bulk) return;
+    if (!mbar_wait(bar, phase, kBulkWaitLimit)) {
+        (void)mbar_wait(bar, phase, kBulkWaitLimit);
+        atomicOr(status, kStTimeout);
+    }
+    phase ^= 1u;
+}
+
 // Adds n 0/1 words from shared memory into the counters, four per step.
 template <int K>
 __device__ __forceinline__ void acc_words(BitCounter<K> &c, const uint32_t *w, int n) {
@@ -452,8 +466,11 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
             for (int jb = 0; jb < nblk; ++jb) {
                 const int c0 = jb * 32;
                 const int nc = min(32, g.m - c0);
+                // no CTA barrier here: the previous block's output (tiles) and
+                // this block's column pass (tokens, column masks) share no data,
+                // so one warp's stores overlap another's lookups
                 const int tshw = sm.tsh;
-                if (!stage_wait((tshw >> 30) & 1, &sm.bar, phase, status)) return;
+                stage_wait_own((tshw >> 30) & 1, &sm.bar, phase, status);
                 const int n_tok = sm.ctpre[32];
                 uint32_t *tg = sm.gh + (tshw & ((1 << 30) - 1));
                 // column pass (each token's row mask replaces it in place): the
