@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--e2e-stream-steps", type=int, default=8)
+    ap.add_argument("--e2e-stream-steps", type=int, default=16)
     ap.add_argument("--cpu-pairs", type=int, default=8000, help="pairs in the oracle's timed sample")
     ap.add_argument("--no-tune", action="store_true", help="skip the tuning comparison")
     ap.add_argument("--tune-pairs", type=int, default=50_000)
@@ -264,9 +264,10 @@ def _pinned_inputs(batch):
     return [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host]
 
 
-def e2e_run(batch, params, steps):
+def e2e_run(batch, params, steps, options=None):
     """Public API from pinned host buffers, one batch at a time: upload,
-    plan, mine, download, destroy.  Median seconds per step."""
+    plan (with the given plan options), mine, download, destroy.  Median
+    seconds per step."""
     import torch
     from paper_1512_01641_gb300 import miner
     pinned = _pinned_inputs(batch)
@@ -277,7 +278,7 @@ def e2e_run(batch, params, steps):
         t0 = time.perf_counter()
         dev = [t.to("cuda", non_blocking=True) for t in pinned]
         db = miner.DeviceBatch(*dev, batch.dic.v_src, batch.dic.v_tgt)
-        plan = miner.Plan(db)
+        plan = miner.Plan(db, options=options)
         out = plan.mine(params)
         n = int(out["link_off"][-1].item())
         res = {"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"].cpu(),
@@ -290,16 +291,17 @@ def e2e_run(batch, params, steps):
     return float(np.median(times)), h2d, d2h
 
 
-def e2e_pipelined(batch, params, steps):
+def e2e_pipelined(batch, params, steps, options=None):
     """Public API from pinned host buffers, batches streamed through
     BatchPipeline (the next batch's upload and plan overlap the current
-    batch's mining); every step uploads its inputs and downloads its links.
+    batch's mining, the previous batch's download overlaps the next mining);
+    every step uploads its inputs and downloads its links.
     Seconds per step over the whole stream (pipeline fill and drain
     included)."""
     import torch
     from paper_1512_01641_gb300.pipeline import BatchPipeline
     pinned = _pinned_inputs(batch)
-    pipe = BatchPipeline(params, batch.dic.v_src, batch.dic.v_tgt)
+    pipe = BatchPipeline(params, batch.dic.v_src, batch.dic.v_tgt, options=options)
     pipe.submit(pinned)  # warm-up batch
     pipe.flush()
     torch.cuda.synchronize()
@@ -406,13 +408,15 @@ def main():
     e2e = None
     if not args.no_e2e:
         plan_keep = plan
-        e_seq, h2d, d2h = e2e_run(batch, params, args.e2e_steps)
-        e_t, d2h_p = e2e_pipelined(batch, params, args.e2e_stream_steps)
+        opts = dict(tuned["best"]) if tuned else {}
+        e_seq, h2d, d2h = e2e_run(batch, params, args.e2e_steps, opts)
+        e_t, d2h_p = e2e_pipelined(batch, params, args.e2e_stream_steps, opts)
         e2e = {"value": cells_step / world / e_t * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h_p, "seconds_per_step": e_t,
                "includes": "per step: H2D of the inputs from pinned host memory, plan creation (validation, "
                            "geometry, scratch), mine_pairs, D2H of links and scores; batches streamed "
                            f"through BatchPipeline ({args.e2e_stream_steps} steps incl. pipeline fill and drain)",
+               "plan_options": opts,
                "sequential": {"value": cells_step / world / e_seq * world, "seconds_per_step": e_seq,
                               "includes": "one batch at a time, nothing overlapped"}}
         plan = plan_keep

@@ -103,6 +103,16 @@ typedef struct mine_plan mine_plan;
  * lists unsorted or repeated or out of range. */
 int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
                      mine_plan **out, miner_stream_t stream);
+/* As mine_plan_create, with plan options (MINE_OPT_*, see below) set before
+ * the work lists are built: options[x] takes values[x], in order.  Setting the
+ * tiling options this way costs nothing, where mine_plan_set_option on an
+ * existing plan rebuilds its fill work lists.  options and values: host
+ * arrays of n_options entries (both may be NULL when n_options is 0).
+ * MINE_EINVAL, before any device work, for n_options < 0, an unknown or
+ * read-only option, or a value mine_plan_set_option would reject. */
+int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                                  const int32_t *options, const int64_t *values, int n_options,
+                                  mine_plan **out, miner_stream_t stream);
 /* Releases the plan without waiting: its device memory returns to the
  * library's pool (a stream-ordered pool per device that keeps up to 16 GiB
  * of freed memory for later plans) once the work enqueued by the last call
@@ -153,8 +163,10 @@ int mine_link_gold_counts(mine_plan *plan, const mine_out *out, const uint8_t *g
                           miner_stream_t stream);
 
 /* Plan options: the tuning knobs of the planner (defaults in parentheses).
- * Setting a tiling option rebuilds the plan's work lists synchronously; do
- * not call it while work on the plan is in flight. */
+ * Setting a tiling option to a new value rebuilds the plan's work lists on
+ * the host and replaces them on the device after the plan's last enqueued
+ * work (synchronous: returns once they are in place); set tiling options at
+ * creation (mine_plan_create_with_options) where they are known then. */
 #define MINE_OPT_TILE_COLS 1      /* fill tile width in columns, multiple of 32 (128) */
 #define MINE_OPT_TILE_MIN_CELLS 2 /* a pair with at least this many cells ... (262144) */
 #define MINE_OPT_TILE_MIN_ROWS 3  /* ... and this many rows is filled as tiles (64) */

@@ -410,12 +410,74 @@ static void build_count_items(const mine_plan *p, std::vector<CountItem> &citems
     }
 }
 
+// What a knob change requires of an existing plan.
+constexpr int kKnobPlain = 0;   // nothing (read at the next call)
+constexpr int kKnobGraph = 1;   // the captured graph holds the value: drop it
+constexpr int kKnobTiling = 2;  // the fill work lists and tile flags depend on it: rebuild
+
+// Applies one option to a knob set (MINE_EINVAL for an unknown or read-only
+// option or a value out of range; the knobs are then unchanged).
+static int knob_apply(PlanKnobs &k, int option, int64_t value, int *effect) {
+    *effect = kKnobPlain;
+    switch (option) {
+        case MINE_OPT_TILE_COLS:
+            if (value < 32 || value % 32 || value > (1 << 20)) return MINE_EINVAL;
+            k.tile_cols = (int)value;
+            *effect = kKnobTiling;
+            return MINE_OK;
+        case MINE_OPT_TILE_MIN_CELLS:
+            if (value < 1) return MINE_EINVAL;
+            k.tile_min_cells = value;
+            *effect = kKnobTiling;
+            return MINE_OK;
+        case MINE_OPT_TILE_MIN_ROWS:
+            if (value < 1) return MINE_EINVAL;
+            k.tile_min_rows = (int)std::min<int64_t>(value, 1 << 30);
+            *effect = kKnobTiling;
+            return MINE_OK;
+        case MINE_OPT_WAIT_LIMIT:
+            if (value < 1) return MINE_EINVAL;
+            k.wait_limit = value;
+            *effect = kKnobGraph;
+            return MINE_OK;
+        case MINE_OPT_LINK_RECOUNT:
+            k.link_recount = value != 0;
+            *effect = kKnobGraph;
+            return MINE_OK;
+        case MINE_OPT_USE_GRAPH:
+            k.use_graph = value != 0;
+            return MINE_OK;
+        case MINE_OPT_FAULT_SKIP_FLAG:
+            k.skip_flag = value < 0 ? -1 : value;
+            *effect = kKnobGraph;
+            return MINE_OK;
+        case MINE_OPT_SOFT_SPLIT:
+            if (value < 0 || value > 2) return MINE_EINVAL;
+            k.soft_split = (int)value;
+            return MINE_OK;
+        default:
+            return MINE_EINVAL;
+    }
+}
+
 extern "C" {
 
 int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
                      mine_plan **out, miner_stream_t stream) {
+    return mine_plan_create_with_options(src, tgt, dict, nullptr, nullptr, 0, out, stream);
+}
+
+int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                                  const int32_t *options, const int64_t *values, int n_options,
+                                  mine_plan **out, miner_stream_t stream) {
     if (!src || !tgt || !dict || !out) return MINE_EINVAL;
     *out = nullptr;
+    if (n_options < 0 || (n_options > 0 && (!options || !values))) return MINE_EINVAL;
+    PlanKnobs knobs;
+    for (int x = 0; x < n_options; ++x) {
+        int effect;
+        if (knob_apply(knobs, options[x], values[x], &effect) != MINE_OK) return MINE_EINVAL;
+    }
     if (src->n_docs != tgt->n_docs || src->n_docs < 0 || src->n_sents < 0 || tgt->n_sents < 0 ||
         src->n_tok < 0 || tgt->n_tok < 0 || dict->v_src <= 0 || dict->v_tgt <= 0 || dict->n_entries < 0)
         return MINE_EINVAL;
@@ -426,6 +488,7 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     cudaStream_t st = (cudaStream_t)stream;
     mine_plan *p = new (std::nothrow) mine_plan();
     if (!p) return MINE_ENOMEM;
+    p->knobs = knobs;
     DoneMark mark{nullptr, st};  // armed once the plan exists
     auto fail = [&](int code) {
         mark.p = nullptr;
@@ -831,41 +894,16 @@ int mine_plan_check(mine_plan *p, miner_stream_t stream) {
 int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
     if (!p) return MINE_EINVAL;
     PlanKnobs k = p->knobs;
-    switch (option) {
-        case MINE_OPT_TILE_COLS:
-            if (value < 32 || value % 32 || value > (1 << 20)) return MINE_EINVAL;
-            k.tile_cols = (int)value;
-            break;
-        case MINE_OPT_TILE_MIN_CELLS:
-            if (value < 1) return MINE_EINVAL;
-            k.tile_min_cells = value;
-            break;
-        case MINE_OPT_TILE_MIN_ROWS:
-            if (value < 1) return MINE_EINVAL;
-            k.tile_min_rows = (int)std::min<int64_t>(value, 1 << 30);
-            break;
-        case MINE_OPT_WAIT_LIMIT:
-            if (value < 1) return MINE_EINVAL;
-            p->knobs.wait_limit = value;
-            drop_graph(p);
-            return MINE_OK;
-        case MINE_OPT_LINK_RECOUNT:
-            p->knobs.link_recount = value != 0;
-            drop_graph(p);
-            return MINE_OK;
-        case MINE_OPT_USE_GRAPH:
-            p->knobs.use_graph = value != 0;
-            return MINE_OK;
-        case MINE_OPT_FAULT_SKIP_FLAG:
-            p->knobs.skip_flag = value < 0 ? -1 : value;
-            drop_graph(p);
-            return MINE_OK;
-        case MINE_OPT_SOFT_SPLIT:
-            if (value < 0 || value > 2) return MINE_EINVAL;
-            p->knobs.soft_split = (int)value;
-            return MINE_OK;
-        default:
-            return MINE_EINVAL;
+    int effect = 0;
+    const int rc = knob_apply(k, option, value, &effect);
+    if (rc != MINE_OK) return rc;
+    const bool same_tiling = k.tile_cols == p->knobs.tile_cols && k.tile_min_cells == p->knobs.tile_min_cells &&
+                             k.tile_min_rows == p->knobs.tile_min_rows;
+    if (effect == kKnobTiling && same_tiling) return MINE_OK;
+    if (effect != kKnobTiling) {
+        if (effect == kKnobGraph) drop_graph(p);
+        p->knobs = k;
+        return MINE_OK;
     }
     drop_graph(p);
     // tiling changed: rebuild the work lists and the tile flags (synchronous)
@@ -878,8 +916,11 @@ int mine_plan_set_option(mine_plan *p, int option, int64_t value) {
     std::vector<FillItem> fitems;
     int64_t tbw, hrow, vcol;
     build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
-    MINE_CK(cudaDeviceSynchronize());
+    // the old work lists and flags are released, and the geometry rewritten,
+    // after the plan's last enqueued work (its completion event), on the
+    // plan-owned stream; other work on the device is not waited for
     cudaStream_t st = p->own_stream;
+    MINE_CK(cudaStreamWaitEvent(st, p->done, 0));
     MINE_CK(cudaFreeAsync(p->fill_items, st));
     MINE_CK(cudaFreeAsync(p->S.flags, st));
     p->fill_items = nullptr;

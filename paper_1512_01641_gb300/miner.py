@@ -60,6 +60,9 @@ class _Out(C.Structure):
 _SIGS = {
     "mine_plan_create": (C.c_int, [C.POINTER(_Corpus), C.POINTER(_Corpus), C.POINTER(_Dict),
                                    C.POINTER(C.c_void_p), C.c_void_p]),
+    "mine_plan_create_with_options": (C.c_int, [C.POINTER(_Corpus), C.POINTER(_Corpus), C.POINTER(_Dict),
+                                                C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int,
+                                                C.POINTER(C.c_void_p), C.c_void_p]),
     "mine_plan_destroy": (None, [C.c_void_p]),
     "mine_plan_n_pairs": (C.c_int64, [C.c_void_p]),
     "mine_plan_n_cells": (C.c_int64, [C.c_void_p]),
@@ -181,15 +184,21 @@ class DeviceBatch:
 
 
 class Plan:
-    """A mining plan (mine_plan_create) over a DeviceBatch."""
+    """A mining plan (mine_plan_create) over a DeviceBatch.  options: plan
+    options by OPTIONS name, set before the work lists are built
+    (mine_plan_create_with_options)."""
 
-    def __init__(self, dbatch: DeviceBatch, stream=None):
+    def __init__(self, dbatch: DeviceBatch, stream=None, options: dict | None = None):
         L = lib()
         self.dbatch = dbatch  # keeps the inputs alive
         self._src, self._tgt, self._dict = dbatch.c_structs()
         h = C.c_void_p()
-        _check(L.mine_plan_create(C.byref(self._src), C.byref(self._tgt), C.byref(self._dict), C.byref(h),
-                                  _stream(stream)), "mine_plan_create")
+        opts = dict(options or {})
+        ids = (C.c_int32 * max(len(opts), 1))(*[OPTIONS[k] for k in opts])
+        vals = (C.c_int64 * max(len(opts), 1))(*[int(v) for v in opts.values()])
+        _check(L.mine_plan_create_with_options(C.byref(self._src), C.byref(self._tgt), C.byref(self._dict), ids,
+                                               vals, len(opts), C.byref(h), _stream(stream)),
+               "mine_plan_create_with_options")
         self._h = h
         self.n_pairs = L.mine_plan_n_pairs(h)
         self.n_cells = L.mine_plan_n_cells(h)

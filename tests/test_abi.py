@@ -50,3 +50,31 @@ def test_strerror_without_gpu(libpath):
     assert L.mine_strerror(0) == b"ok"
     assert b"invalid" in L.mine_strerror(-1)
     assert L.mine_strerror(-4).startswith(b"device-side wait")
+
+
+@pytest.mark.parametrize("opts", [
+    [(99, 1)],                       # unknown option
+    [(7, 0)],                        # MINE_OPT_GRAPH_CAPTURES is read-only
+    [(9, 0)],                        # MINE_OPT_N_TILE_FLAGS is read-only
+    [(1, 48)],                       # tile width not a multiple of 32
+    [(1, 64), (2, 0)],               # a valid option followed by an invalid one
+    [(10, 3)],                       # soft split mode out of range
+])
+def test_create_with_options_rejects_bad_options_before_device_work(libpath, opts):
+    # option validation comes before any CUDA call, so this runs without a GPU;
+    # the corpora only need non-null pointers to reach it
+    L = miner.lib()
+    buf = (ctypes.c_int64 * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    src = miner._Corpus(1, 1, 1, p, p, p)
+    tgt = miner._Corpus(1, 1, 1, p, p, p)
+    dic = miner._Dict(4, 4, 1, p, p)
+    ids = (ctypes.c_int32 * len(opts))(*[o for o, _ in opts])
+    vals = (ctypes.c_int64 * len(opts))(*[v for _, v in opts])
+    h = ctypes.c_void_p()
+    rc = L.mine_plan_create_with_options(ctypes.byref(src), ctypes.byref(tgt), ctypes.byref(dic), ids, vals,
+                                         len(opts), ctypes.byref(h), None)
+    assert rc == miner.MINE_EINVAL and not h.value
+    rc = L.mine_plan_create_with_options(ctypes.byref(src), ctypes.byref(tgt), ctypes.byref(dic), ids, vals, -1,
+                                         ctypes.byref(h), None)
+    assert rc == miner.MINE_EINVAL and not h.value

@@ -288,6 +288,35 @@ def test_tiled_fill_equals_single_warp_fill(tile_cols):
     check_alignment(batch, p, sel, ora)
 
 
+def test_options_at_creation_equal_options_set_later():
+    """A plan created with its tiling options (mine_plan_create_with_options)
+    reports them and mines exactly what a plan whose options were set after
+    creation (work lists rebuilt, while earlier work of the plan is in flight)
+    mines."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    ns = [300, 97, 64, 257, 40]
+    ms = [410, 300, 97, 64, 700]
+    batch = synth.make_batch(82, len(ns), v_src=4000, v_tgt=4000, src_sizes=ns, tgt_sizes=ms)
+    p = _params()
+    opts = {"tile_cols": 64, "tile_min_cells": 1, "tile_min_rows": 33}
+    db = miner.DeviceBatch.from_batch(batch)
+    with miner.Plan(db, options=opts) as plan:
+        assert {k: plan.get_option(k) for k in opts} == opts
+        assert plan.get_option("n_tile_flags") > 0
+        a = plan.mine(p)
+        plan.check()
+        torch.cuda.synchronize()
+        a = {k: v.clone() for k, v in a.items()}
+    with miner.Plan(db) as plan:
+        plan.mine(p)  # in flight while the options below rebuild the work lists
+        for k, v in opts.items():
+            plan.set_option(k, v)
+        b = plan.mine(p)
+        plan.check()
+        _outputs_equal(a, b, batch.n_pairs)
+
+
 def test_link_recount_by_warp_vote_matches_cached_counts():
     """Recounting the overlaps of the aligned pairs by warp vote gives exactly
     the similarities computed from the cached bit-sliced counts."""

@@ -1,5 +1,7 @@
 """Streaming batches from host memory through BatchPipeline gives, batch by
-batch, exactly the links and scores of Plan.mine on the same batch."""
+batch, exactly the links and scores of Plan.mine on the same batch (with the
+pipeline's plans at the default options, and with every pair of a batch
+filled as tiles: the fill's arithmetic per cell does not depend on tiling)."""
 import numpy as np
 import pytest
 
@@ -8,7 +10,9 @@ from paper_1512_01641_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_pipeline_results_equal_plan_mine():
+@pytest.mark.parametrize("options", [None, {"tile_cols": 64, "tile_min_cells": 1 << 12, "tile_min_rows": 32}],
+                         ids=["default", "tiled"])
+def test_pipeline_results_equal_plan_mine(options):
     import torch
     from paper_1512_01641_gb300 import miner
     from paper_1512_01641_gb300.pipeline import BatchPipeline
@@ -24,7 +28,7 @@ def test_pipeline_results_equal_plan_mine():
             ref.append({"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"][:plan.n_pairs].cpu(),
                         "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(),
                         "link_s": out["link_s"][:n].cpu()})
-    pipe = BatchPipeline(params, dic.v_src, dic.v_tgt)
+    pipe = BatchPipeline(params, dic.v_src, dic.v_tgt, options=options)
     got = []
     for b in batches:
         host = [b.src.doc_sent_off, b.src.sent_tok_off, b.src.tok, b.tgt.doc_sent_off, b.tgt.sent_tok_off,
