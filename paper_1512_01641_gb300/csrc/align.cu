@@ -123,11 +123,14 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
 // loads the next one with one coalesced 256-byte read.  Diagonal cells are
 // written to the END of the pair's link window in ascending order.
 __global__ void __launch_bounds__(32 * kTailWarps)
-walk_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, AlignScratch S) {
+walk_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs, AlignScratch S) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t k = warp0; k < n_pairs; k += nwarps) {
+    // largest pairs first: their serial walks start at once and run beside
+    // the many short ones instead of after them
+    for (int64_t x = warp0; x < n_pairs; x += nwarps) {
+        const int32_t k = order[x];
         const PairGeom g = geom[k];
         const int N = g.n, M = g.m;
         const int cap = min(N, M);
@@ -137,30 +140,41 @@ walk_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, AlignScratch S) 
     }
 }
 
-// Exclusive scan of int32 counts into int64 offsets (one block; n is at most a
-// few hundred thousand, so a strided serial pass per thread is enough).
+// Exclusive scan of int32 counts into int64 offsets, out[n] = total (one
+// block; n is at most a few hundred thousand).  Tiles of 1024 consecutive
+// counts: coalesced loads, warp scans by shuffle, a scan of the 32 warp
+// totals, and a running carry from tile to tile.
 __global__ void __launch_bounds__(1024)
 scan_kernel(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out) {
-    __shared__ int64_t part[1024];
-    const int t = threadIdx.x;
-    const int64_t chunk = (n + 1023) / 1024;
-    const int64_t a = t * chunk, b = min(n, a + chunk);
-    int64_t sum = 0;
-    for (int64_t x = a; x < b; ++x) sum += in[x];
-    part[t] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        int64_t v = t >= off ? part[t - off] : 0;
+    __shared__ int64_t wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t x = base + t;
+        const int64_t v = x < n ? (int64_t)in[x] : 0;
+        int64_t s = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane == 31) wsum[w] = s;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            int64_t ws = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t y = __shfl_up_sync(kFull, ws, off);
+                if (lane >= off) ws += y;
+            }
+            wsum[lane] = ws;  // inclusive over warps
+        }
         __syncthreads();
+        if (x < n) out[x] = carry + (w > 0 ? wsum[w - 1] : 0) + s - v;
+        carry += wsum[31];
+        __syncthreads();  // wsum is rewritten by the next tile
     }
-    int64_t run = part[t] - sum;
-    for (int64_t x = a; x < b; ++x) {
-        out[x] = run;
-        run += in[x];
-    }
-    if (t == 1023) out[n] = part[1023];
+    if (t == 0) out[n] = carry;
 }
 
 // (ms, mt) of one cell by warp vote: lanes hold target positions (in chunks
@@ -377,10 +391,10 @@ cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGe
     return cudaGetLastError();
 }
 
-cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
-                        cudaStream_t st) {
+cudaError_t launch_walk(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const AlignScratch &S,
+                        int n_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    walk_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, n_pairs, S);
+    walk_kernel<<<tail_grid(n_pairs, n_sms), 32 * kTailWarps, 0, st>>>(geom, order, n_pairs, S);
     return cudaGetLastError();
 }
 

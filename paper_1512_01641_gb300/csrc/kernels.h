@@ -98,8 +98,9 @@ cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGe
                         const uint8_t *counts, int64_t counts_bytes, const AlignScratch &S, int64_t wait_limit,
                         int64_t skip_flag, int n_sms, cudaStream_t st);
 
-cudaError_t launch_walk(const PairGeom *geom, int64_t n_pairs, const AlignScratch &S, int n_sms,
-                        cudaStream_t st);
+// order: the pairs by decreasing size (a permutation of 0..n_pairs-1)
+cudaError_t launch_walk(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const AlignScratch &S,
+                        int n_sms, cudaStream_t st);
 
 cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t st);
 

@@ -669,7 +669,7 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
         return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, 2 * p->n_cells, S,
                            p->knobs.wait_limit, p->knobs.skip_flag, p->n_sms, st);
     }));
-    MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, n, S, p->n_sms, st); }));
+    MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, p->pair_order, n, S, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_diag, n, S.diag_off, st); }));
     MINE_CK(timed(p, kKLinks, st, [&] {
         return launch_link_score(p->src, p->tgt, p->dict, p->geom, n, P, S, p->knobs.link_recount ? nullptr : counts,
