@@ -104,6 +104,11 @@ __device__ __forceinline__ float similarity(int ms, int mt, const SimRow &r, con
     return rcp_approx(__fadd_rn(1.0f, ex2_approx(y)));
 }
 
+// Hint: bring the cache line holding p into L1 (no effect on results).
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // PTX acquire/release accesses for the tile flags of the cooperative fill.
 // Waits poll with relaxed loads and acquire once the value is seen: an
 // acquire at GPU scope must keep later loads off stale L1 lines, so polling

@@ -237,13 +237,17 @@ __device__ __forceinline__ float fill_strip(FillCtx &C, int s, const int64_t *__
     return fill_strip_run(C, s, hrow, tb_pair, nblk_pair, b0, ah, nb);
 }
 
-// Walk back from (N,M) to (0,0) for one pair (whole warp, same path in every
-// lane).  The 32 x 32 block of traceback codes around the current cell sits
-// in registers (lane l holds the word of row l of the block), so a step costs
-// a shuffle; leaving the block loads the next one with one coalesced 256-byte
-// read.  The t-th diagonal cell found (from the end) is written at index
-// -1-t of diag_i_end / diag_j_end, so the cells end up ascending.  Returns the
-// number of diagonal cells.
+// Walk back from (N, M) to the border along the traceback codes (UP before
+// LEFT before DIAG, as the fill recorded them), one warp per pair, and write
+// the diagonal cells to the END of the pair's link window in ascending order
+// (diag_*_end[-1] is the last); returns their number.  The 32 x 32 block of
+// codes around the current cell sits in registers (lane l holds the word of
+// row l of the block); leaving the block loads the next one with one
+// coalesced 256-byte read.  A gap step costs a shuffle; a run of diagonal
+// steps is taken at once: every lane reads the code of its own row's cell on
+// the current diagonal, and a ballot finds where the run meets a cell that is
+// not DIAG or the block's edge -- the cells the one-step walk would visit, in
+// the same order.
 __device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N, int M, int lane,
                                          int32_t *diag_i_end, int32_t *diag_j_end) {
     const int nblk = (M + 31) >> 5;
@@ -256,6 +260,13 @@ __device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N
             bs = rr >> 5;
             bj = cc >> 5;
             word = tbp[((int64_t)bs * nblk + bj) * 32 + lane];
+            // the walk leaves this block into the one above, to the left or
+            // above-left: start bringing their two 128-byte lines into L1
+            if (lane < 6) {
+                const int c = lane >> 1;
+                const int pbs = bs - (c != 1), pbj = bj - (c != 0);
+                if (pbs >= 0 && pbj >= 0) prefetch_l1(tbp + ((int64_t)pbs * nblk + pbj) * 32 + 16 * (lane & 1));
+            }
         }
         const uint64_t wr = __shfl_sync(kFull, word, rr & 31);
         const uint32_t code = (uint32_t)(wr >> (2 * (cc & 31))) & 3u;
@@ -264,13 +275,23 @@ __device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N
         } else if (code == kLeft) {
             --j;
         } else {
-            if (lane == 0) {
-                diag_i_end[-1 - n] = rr;
-                diag_j_end[-1 - n] = cc;
+            // diagonal run from (rr, cc) upwards: lane l's cell on it is
+            // (32 bs + l, cc - t) with t = rr - (32 bs + l) steps from here
+            const int top = rr & 31;
+            const int t = top - lane;
+            const int cl = cc - t;
+            bool stop = true;  // the run cannot pass this lane's cell
+            if (t >= 0 && cl >= 32 * bj) stop = ((uint32_t)(word >> (2 * (cl & 31))) & 3u) != kDiag;
+            const uint32_t below = __ballot_sync(kFull, stop) & (0xFFFFFFFFu >> (31 - top));
+            const int h = below ? 31 - __clz(below) : -1;  // the lane where the run ends (lane top is DIAG)
+            if (lane > h && lane <= top) {
+                diag_i_end[-1 - (n + t)] = rr - t;
+                diag_j_end[-1 - (n + t)] = cl;
             }
-            ++n;
-            --i;
-            --j;
+            const int len = top - h;
+            n += len;
+            i -= len;
+            j -= len;
         }
     }
     return n;
