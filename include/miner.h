@@ -162,6 +162,52 @@ int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
 int mine_link_gold_counts(mine_plan *plan, const mine_out *out, const uint8_t *gold, uint64_t *counts3,
                           miner_stream_t stream);
 
+/* ---- Bi-directional mining (Section 5.4, "BI": a second classifier mines
+ * the reverse direction and the bi-sentences of both are kept) ----
+ * The reverse direction is a second plan whose source corpus is this one's
+ * target corpus and vice versa, with a dictionary from target ids to source
+ * ids (the caller's own, or mine_dict_transpose of the forward one) and its
+ * own parameters; mine_links_combine merges the links of the two plans pair
+ * by pair. */
+
+/* Transpose of a dictionary: for every target id t, the ascending source ids
+ * v with t among tgt[off[v] .. off[v+1]-1].  off_out: v_tgt+1 int32, tgt_out:
+ * n_entries int32 (device, caller-allocated).  SYNCHRONOUS on the stream (it
+ * checks the dictionary first).  MINE_EINVAL for a NULL argument, sizes out of
+ * range, offsets that do not start at 0, decrease or do not end at
+ * n_entries, or a target id outside [0, v_tgt); the outputs are then
+ * unspecified. */
+int mine_dict_transpose(const mine_dict *dict, int32_t *off_out, int32_t *tgt_out, miner_stream_t stream);
+
+#define MINE_BI_UNION 0     /* links kept by either direction */
+#define MINE_BI_INTERSECT 1 /* links kept by both directions */
+
+/* Output of mine_links_combine (device, caller-allocated).  Links of pair k
+ * are entries link_off[k] .. link_off[k+1]-1, in forward coordinates
+ * (link_i: source sentence, link_j: target sentence), ascending in (i, j)
+ * lexicographically (a union of two monotone link lists need not be
+ * monotone).  s_fwd / s_rev: the link's similarity in each direction, NaN
+ * where that direction did not keep the link.  link_capacity must be at
+ * least mine_plan_link_capacity(fwd) + mine_plan_link_capacity(rev). */
+typedef struct {
+    int64_t *link_off; /* n_docs+1 */
+    int32_t *link_i;
+    int32_t *link_j;
+    float *s_fwd;
+    float *s_rev;
+    int64_t link_capacity;
+} mine_bi_out;
+
+/* Merge, per pair, the links of a forward plan (out_fwd, as mine_pairs or
+ * mine_align wrote it on fwd) with those of the reverse plan (out_rev on
+ * rev; its link (i', j') is the forward link (j', i')): their union or their
+ * intersection (mode, MINE_BI_*).  rev must hold the same pairs with the roles
+ * swapped, N_k(rev) = M_k(fwd) and M_k(rev) = N_k(fwd) (checked on the host:
+ * MINE_EINVAL).  Asynchronous on the stream, after both outputs are complete
+ * on it; uses a temporary of n_docs int32 from the library's pool. */
+int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, const mine_out *out_rev,
+                       int mode, mine_bi_out *out, miner_stream_t stream);
+
 /* Plan options: the tuning knobs of the planner (defaults in parentheses).
  * Setting a tiling option to a new value rebuilds the plan's work lists on
  * the host and replaces them on the device after the plan's last enqueued

@@ -144,8 +144,9 @@ walk_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order
 // block; n is at most a few hundred thousand).  Tiles of 1024 consecutive
 // counts: coalesced loads, warp scans by shuffle, a scan of the 32 warp
 // totals, and a running carry from tile to tile.
+template <typename OutT>
 __global__ void __launch_bounds__(1024)
-scan_kernel(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out) {
+scan_kernel(const int32_t *__restrict__ in, int64_t n, OutT *__restrict__ out) {
     __shared__ int64_t wsum[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int64_t carry = 0;
@@ -170,11 +171,11 @@ scan_kernel(const int32_t *__restrict__ in, int64_t n, int64_t *__restrict__ out
             wsum[lane] = ws;  // inclusive over warps
         }
         __syncthreads();
-        if (x < n) out[x] = carry + (w > 0 ? wsum[w - 1] : 0) + s - v;
+        if (x < n) out[x] = (OutT)(carry + (w > 0 ? wsum[w - 1] : 0) + s - v);
         carry += wsum[31];
         __syncthreads();  // wsum is rewritten by the next tile
     }
-    if (t == 0) out[n] = carry;
+    if (t == 0) out[n] = (OutT)carry;
 }
 
 // (ms, mt) of one cell by warp vote: lanes hold target positions (in chunks
@@ -399,7 +400,12 @@ cudaError_t launch_walk(const PairGeom *geom, const int32_t *order, int64_t n_pa
 }
 
 cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t st) {
-    scan_kernel<<<1, 1024, 0, st>>>(in, n, out);
+    scan_kernel<int64_t><<<1, 1024, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t st) {
+    scan_kernel<int32_t><<<1, 1024, 0, st>>>(in, n, out);
     return cudaGetLastError();
 }
 

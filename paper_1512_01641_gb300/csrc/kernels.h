@@ -103,6 +103,29 @@ cudaError_t launch_walk(const PairGeom *geom, const int32_t *order, int64_t n_pa
                         int n_sms, cudaStream_t st);
 
 cudaError_t launch_scan(const int32_t *in, int64_t n, int64_t *out, cudaStream_t st);
+// As launch_scan with int32 offsets (the caller knows the total fits).
+cudaError_t launch_scan32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t st);
+
+// Bi-directional mining (bi.cu).
+// Dictionary transpose: status bit 0 set for a malformed dictionary (checked
+// by launch_dict_check before any other step reads it).
+cudaError_t launch_dict_check(const int32_t *off, int32_t v_src, int64_t n_entries, const int32_t *tgt,
+                              int32_t v_tgt, uint32_t *status, cudaStream_t st);
+cudaError_t launch_dict_count(const int32_t *tgt, int64_t n_entries, int32_t *cnt, cudaStream_t st);
+cudaError_t launch_dict_scatter(const int32_t *off, int32_t v_src, const int32_t *tgt, int32_t *cursor,
+                                int32_t *tgt_out, cudaStream_t st);
+cudaError_t launch_dict_sort(const int32_t *off_out, int32_t v_tgt, int32_t *tgt_out, cudaStream_t st);
+// Link lists of a plan output (offsets per pair, i, j, s).
+struct LinkView {
+    const int64_t *off;
+    const int32_t *i, *j;
+    const float *s;
+};
+// Per pair: count (out_i == nullptr) or write the merged links of fwd and
+// rev (rev's link (i', j') is (j', i')); mode 0 union, 1 intersection.
+cudaError_t launch_links_combine(LinkView fwd, LinkView rev, int64_t n_pairs, int mode, int32_t *count,
+                                 const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_sf,
+                                 float *out_sr, cudaStream_t st);
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,

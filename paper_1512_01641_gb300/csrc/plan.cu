@@ -987,3 +987,70 @@ const char *mine_strerror(int code) {
 int mine_last_cuda_error(void) { return g_last_cuda; }
 
 }  // extern "C"
+
+// A temporary from the library's pool, returned to it (stream-ordered) when
+// the scope ends, on every path out of an entry point.
+template <typename T>
+struct PoolTemp {
+    T *p = nullptr;
+    cudaStream_t st;
+    explicit PoolTemp(cudaStream_t s) : st(s) {}
+    ~PoolTemp() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+extern "C" {
+
+int mine_dict_transpose(const mine_dict *d, int32_t *off_out, int32_t *tgt_out, miner_stream_t stream) {
+    if (!d || !off_out || !d->off || d->v_src <= 0 || d->v_tgt <= 0 || d->n_entries < 0 ||
+        d->n_entries > INT32_MAX || (d->n_entries > 0 && (!d->tgt || !tgt_out)))
+        return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int device;
+    MINE_CK(cudaGetDevice(&device));
+    PoolTemp<uint32_t> status(st);
+    PoolTemp<int32_t> cursor(st);
+    MINE_CK(dalloc(&status.p, 1, device, st));
+    MINE_CK(dalloc(&cursor.p, (size_t)d->v_tgt, device, st));
+    MINE_CK(cudaMemsetAsync(status.p, 0, sizeof(uint32_t), st));
+    MINE_CK(launch_dict_check(d->off, d->v_src, d->n_entries, d->tgt, d->v_tgt, status.p, st));
+    uint32_t bad = 0;
+    MINE_CK(cudaMemcpyAsync(&bad, status.p, sizeof bad, cudaMemcpyDeviceToHost, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    if (bad) return MINE_EINVAL;
+    // counts into off_out[0 .. v_tgt), scanned in place into offsets
+    MINE_CK(cudaMemsetAsync(off_out, 0, ((size_t)d->v_tgt + 1) * sizeof(int32_t), st));
+    MINE_CK(launch_dict_count(d->tgt, d->n_entries, off_out, st));
+    MINE_CK(launch_scan32(off_out, d->v_tgt, off_out, st));
+    MINE_CK(cudaMemcpyAsync(cursor.p, off_out, (size_t)d->v_tgt * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    MINE_CK(launch_dict_scatter(d->off, d->v_src, d->tgt, cursor.p, tgt_out, st));
+    MINE_CK(launch_dict_sort(off_out, d->v_tgt, tgt_out, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    return MINE_OK;
+}
+
+int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const mine_out *orv, int mode,
+                       mine_bi_out *o, miner_stream_t stream) {
+    if (!f || !r || !of || !orv || !o || (mode != MINE_BI_UNION && mode != MINE_BI_INTERSECT)) return MINE_EINVAL;
+    if (f->n_pairs != r->n_pairs || !of->link_off || !orv->link_off || !o->link_off) return MINE_EINVAL;
+    for (int64_t k = 0; k < f->n_pairs; ++k)
+        if (f->geom_h[k].n != r->geom_h[k].m || f->geom_h[k].m != r->geom_h[k].n) return MINE_EINVAL;
+    const int64_t need = f->link_cap + r->link_cap;
+    if (o->link_capacity < need) return MINE_EINVAL;
+    if (f->link_cap > 0 && (!of->link_i || !of->link_j || !of->link_s)) return MINE_EINVAL;
+    if (r->link_cap > 0 && (!orv->link_i || !orv->link_j || !orv->link_s)) return MINE_EINVAL;
+    if (need > 0 && (!o->link_i || !o->link_j || !o->s_fwd || !o->s_rev)) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = f->n_pairs;
+    PoolTemp<int32_t> cnt(st);
+    MINE_CK(dalloc(&cnt.p, (size_t)n, f->device, st));
+    const LinkView F{of->link_off, of->link_i, of->link_j, of->link_s};
+    const LinkView R{orv->link_off, orv->link_i, orv->link_j, orv->link_s};
+    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, st));
+    MINE_CK(launch_scan(cnt.p, n, o->link_off, st));
+    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, o->link_off, o->link_i, o->link_j, o->s_fwd, o->s_rev, st));
+    return MINE_OK;
+}
+
+}  // extern "C"

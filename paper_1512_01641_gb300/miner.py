@@ -56,6 +56,11 @@ class _Out(C.Structure):
                 ("link_s", C.c_void_p), ("pair_score", C.c_void_p), ("link_capacity", C.c_int64)]
 
 
+class _BiOut(C.Structure):
+    _fields_ = [("link_off", C.c_void_p), ("link_i", C.c_void_p), ("link_j", C.c_void_p),
+                ("s_fwd", C.c_void_p), ("s_rev", C.c_void_p), ("link_capacity", C.c_int64)]
+
+
 # Every exported symbol of include/miner.h with its ctypes signature.
 _SIGS = {
     "mine_plan_create": (C.c_int, [C.POINTER(_Corpus), C.POINTER(_Corpus), C.POINTER(_Dict),
@@ -74,6 +79,9 @@ _SIGS = {
     "mine_pairs": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_Out), C.c_void_p]),
     "mine_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mine_link_gold_counts": (C.c_int, [C.c_void_p, C.POINTER(_Out), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_dict_transpose": (C.c_int, [C.POINTER(_Dict), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_links_combine": (C.c_int, [C.c_void_p, C.POINTER(_Out), C.c_void_p, C.POINTER(_Out), C.c_int,
+                                     C.POINTER(_BiOut), C.c_void_p]),
     "mine_plan_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
     "mine_plan_get_option": (C.c_int64, [C.c_void_p, C.c_int]),
     "mine_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -167,6 +175,15 @@ class DeviceBatch:
                    up(batch.src.tok, np.int32), up(batch.tgt.doc_sent_off, np.int64),
                    up(batch.tgt.sent_tok_off, np.int64), up(batch.tgt.tok, np.int32),
                    up(batch.dic.off, np.int32), up(batch.dic.tgt, np.int32), batch.dic.v_src, batch.dic.v_tgt)
+
+    def reversed(self, dict_off=None, dict_tgt=None, stream=None) -> "DeviceBatch":
+        """The same pairs with the roles swapped (target documents become the
+        source), for mining the reverse direction; its dictionary maps this
+        batch's target ids to source ids: the given CSR (dict_off: v_tgt+1,
+        dict_tgt), or the transpose of this batch's dictionary."""
+        if dict_off is None:
+            dict_off, dict_tgt = dict_transpose(self.dict_off, self.dict_tgt, self.v_src, self.v_tgt, stream)
+        return DeviceBatch(*self.tgt, *self.src, dict_off, dict_tgt, self.v_tgt, self.v_src)
 
     def c_structs(self):
         def corpus(doc, sent, tok):
@@ -313,6 +330,75 @@ class Plan:
         p = params.c()
         _check(lib().mine_pairs(self._h, C.byref(p), C.byref(s), _stream(stream)), "mine_pairs")
         return out
+
+
+def dict_transpose(dict_off, dict_tgt, v_src: int, v_tgt: int, stream=None):
+    """mine_dict_transpose: the CSR dictionary from target ids to the sorted
+    source ids that translate to them -> (off: v_tgt+1 int32, tgt int32)."""
+    import torch
+    d = _Dict()
+    d.v_src, d.v_tgt = int(v_src), int(v_tgt)
+    d.n_entries = dict_tgt.numel()
+    d.off, d.tgt = dict_off.data_ptr(), dict_tgt.data_ptr() if dict_tgt.numel() else 0
+    off = torch.empty(int(v_tgt) + 1, dtype=torch.int32, device=dict_off.device)
+    tgt = torch.empty(max(dict_tgt.numel(), 1), dtype=torch.int32, device=dict_off.device)
+    _check(lib().mine_dict_transpose(C.byref(d), _ptr(off), _ptr(tgt), _stream(stream)), "mine_dict_transpose")
+    return off, tgt[:dict_tgt.numel()]
+
+
+BI_MODES = {"union": 0, "intersect": 1}
+
+
+def combine_links(fwd: "Plan", out_fwd, rev: "Plan", out_rev, mode: str = "union", out=None, stream=None):
+    """mine_links_combine: per pair, the union (or intersection) of the
+    forward links and the reverse plan's links mapped back to forward
+    coordinates -> dict of link_off, link_i, link_j, s_fwd, s_rev (NaN where a
+    direction did not keep the link)."""
+    import torch
+    cap = max(fwd.link_capacity + rev.link_capacity, 1)
+    if out is None:
+        out = {"link_off": torch.empty(fwd.n_pairs + 1, dtype=torch.int64, device="cuda"),
+               "link_i": torch.empty(cap, dtype=torch.int32, device="cuda"),
+               "link_j": torch.empty(cap, dtype=torch.int32, device="cuda"),
+               "s_fwd": torch.empty(cap, dtype=torch.float32, device="cuda"),
+               "s_rev": torch.empty(cap, dtype=torch.float32, device="cuda")}
+    b = _BiOut()
+    b.link_off, b.link_i, b.link_j = (out[k].data_ptr() for k in ("link_off", "link_i", "link_j"))
+    b.s_fwd, b.s_rev = out["s_fwd"].data_ptr(), out["s_rev"].data_ptr()
+    b.link_capacity = out["link_i"].numel()
+    f = Plan._out_struct(out_fwd, out_fwd["link_i"].numel())
+    r = Plan._out_struct(out_rev, out_rev["link_i"].numel())
+    _check(lib().mine_links_combine(fwd.handle, C.byref(f), rev.handle, C.byref(r), BI_MODES[mode], C.byref(b),
+                                    _stream(stream)), "mine_links_combine")
+    return out
+
+
+class BiPlan:
+    """Bi-directional mining (Section 5.4, BI): a forward plan over the batch
+    and a reverse plan over its reversed view (corpora swapped, dictionary
+    from target ids to source ids), mined with their own parameters; mine()
+    returns both directions' outputs and their per-pair combination."""
+
+    def __init__(self, dbatch: DeviceBatch, rev_dict=None, options: dict | None = None, stream=None):
+        rd = rev_dict if rev_dict is not None else (None, None)
+        self.fwd = Plan(dbatch, stream=stream, options=options)
+        self.rev = Plan(dbatch.reversed(*rd, stream=stream), stream=stream, options=options)
+        self.n_pairs = self.fwd.n_pairs
+
+    def mine(self, params_fwd: MineParams, params_rev: MineParams, mode: str = "union", stream=None):
+        of = self.fwd.mine(params_fwd, stream=stream)
+        orv = self.rev.mine(params_rev, stream=stream)
+        return of, orv, combine_links(self.fwd, of, self.rev, orv, mode, stream=stream)
+
+    def close(self):
+        self.fwd.close()
+        self.rev.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def links_per_pair(out, n_pairs):

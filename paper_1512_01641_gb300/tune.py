@@ -2,17 +2,24 @@
 
 The paper tunes the threshold and the penalty with a script that tries random
 parameter values and keeps those whose automatic alignment is most similar to
-a human one (Section 5.2).  Two tuners are provided here, both on the GPU:
+a human one (Section 5.2).  Three tuners are provided here, all on the GPU:
 
+* ``random_search``: the paper's own tuner -- settings drawn at random, each
+  scored by hard Needleman-Wunsch alignment of the training pairs against the
+  gold links, the most similar kept;
 * ``grid_search``: the exhaustive baseline -- every (gap, thr, b) setting of a
-  7 x 7 x 7 grid is scored by hard Needleman-Wunsch alignment of the training
-  pairs (micro-F1 of the links against the gold links), the best is kept;
+  7 x 7 x 7 grid is scored the same way, the best is kept;
 * ``adam_tune``: gradient descent on the soft-alignment loss (softnw_fwd /
   softnw_bwd through ``miner.SoftAligner``) over all seven parameters.
 
-Both are then evaluated identically: hard alignment of held-out pairs,
-micro-F1 of the kept links against the gold links.  Counts are computed once
-per batch (mine_count) and reused by every evaluation and every step.
+The similarity of an automatic and a human alignment is read as
+2 * matched / (automatic links + human links), where matched counts the links
+that a Needleman-Wunsch alignment of the two link lists pairs up; both lists
+are monotone (they lie on alignment paths), so matched is the number of
+common links and the similarity is the links' micro-F1.  All tuners are then
+evaluated identically: hard alignment of held-out pairs, micro-F1 of the kept
+links against the gold links.  Counts are computed once per batch
+(mine_count) and reused by every evaluation and every step.
 """
 from __future__ import annotations
 
@@ -30,6 +37,9 @@ GRID = {
     "b": [-6.0, -5.0, -4.0, -3.0, -2.0, -1.0, 0.0],
 }
 THETA0 = np.array([4.0, 4.0, -2.0, 1.0, -3.0, 0.3, 0.5])  # w0..w3, b, gap, thr
+# ranges of the random search: those the grid spans (uniform draws)
+RANDOM_RANGES = {"b": (-6.0, 0.0), "gap": (0.05, 0.8), "thr": (0.2, 0.8)}
+_THETA_INDEX = {"b": 4, "gap": 5, "thr": 6}
 
 
 class TuneData:
@@ -85,6 +95,43 @@ def grid_search(train: TuneData, held_out: TuneData, theta0=THETA0, grid=GRID) -
     return TuneResult("grid", best.tolist(), best_f1, ev, secs, {"settings": n})
 
 
+def random_draws(trials: int, seed: int = 0, theta0=THETA0, ranges=RANDOM_RANGES) -> list:
+    """The settings random_search tries: theta0 with each parameter of ranges
+    (b, gap, thr, in that order) drawn uniformly from its range."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(trials):
+        th = np.array(theta0, np.float64)
+        for k in ("b", "gap", "thr"):
+            if k in ranges:
+                lo, hi = ranges[k]
+                th[_THETA_INDEX[k]] = rng.uniform(lo, hi)
+        out.append(th)
+    return out
+
+
+def random_search(train: TuneData, held_out: TuneData, trials: int = 343, seed: int = 0, theta0=THETA0,
+                  ranges=RANDOM_RANGES) -> TuneResult:
+    """The paper's tuner (Section 5.2): naive random selection of parameter
+    values, keeping the setting whose hard alignment of the training pairs is
+    most similar to the gold alignment (micro-F1, see the module docstring).
+    The default budget equals the grid's 343 settings; ranges may name a
+    subset of b, gap, thr (the paper tunes thr and gap)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best, best_f1 = None, -1.0
+    for th in random_draws(trials, seed, theta0, ranges):
+        f = train.f1(miner.params_from_theta(th))["f1"]
+        if f > best_f1:
+            best, best_f1 = th, f
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    ev = held_out.f1(miner.params_from_theta(best))
+    return TuneResult("random", best.tolist(), best_f1, ev, secs,
+                      {"trials": trials, "seed": seed, "ranges": {k: list(v) for k, v in ranges.items()}})
+
+
 def adam_tune(train: TuneData, held_out: TuneData, steps: int = 200, lr: float = 0.05, gamma: float = 0.1,
               tau: float = 0.05, betas=(0.9, 0.999), theta0=THETA0, batch_pairs: int | None = 1024,
               seed: int = 0) -> TuneResult:
@@ -128,13 +175,15 @@ def adam_tune(train: TuneData, held_out: TuneData, steps: int = 200, lr: float =
                        "loss_first": losses[0], "loss_last": losses[-1]})
 
 
-def compare(train_batch, eval_batch, steps=200, grid=GRID, gamma=0.1) -> dict:
-    """Grid search vs Adam on the same GPU, both evaluated on held-out pairs."""
+def compare(train_batch, eval_batch, steps=200, grid=GRID, gamma=0.1, random_trials=343) -> dict:
+    """Grid search vs the paper's random search vs Adam on the same GPU, all
+    evaluated on held-out pairs."""
     train, held = TuneData(train_batch), TuneData(eval_batch)
     base = held.f1(miner.params_from_theta(THETA0))
     g = grid_search(train, held, grid=grid)
+    r = random_search(train, held, trials=random_trials)
     a = adam_tune(train, held, steps=steps, gamma=gamma)
-    return {"baseline_eval": base, "grid": g.as_dict(), "adam": a.as_dict(),
+    return {"baseline_eval": base, "grid": g.as_dict(), "random": r.as_dict(), "adam": a.as_dict(),
             "f1_gap_points": 100 * (a.eval["f1"] - g.eval["f1"]),
             "speedup_vs_grid": g.seconds / a.seconds if a.seconds > 0 else None,
             "train_pairs": train_batch.n_pairs, "eval_pairs": eval_batch.n_pairs}

@@ -342,3 +342,121 @@ def test_soft_loss_gradient_central_differences(gamma):
         tm[k] -= h
         fd = (softgrad.loss_value(pairs, tp, gamma, 0.05) - softgrad.loss_value(pairs, tm, gamma, 0.05)) / (2 * h)
         assert g[k] == pytest.approx(fd, rel=1e-4, abs=1e-7), k
+
+
+# --- the tuning objective (Section 5.2): similarity of automatic and human alignments ---
+
+def _lcs_brute(a, b):
+    """Longest common subsequence by enumerating every subsequence of a."""
+    import itertools
+    best = 0
+    for r in range(len(a) + 1):
+        for idx in itertools.combinations(range(len(a)), r):
+            sub = [a[x] for x in idx]
+            it = iter(b)
+            if all(any(y == x for y in it) for x in sub):
+                best = max(best, r)
+    return best
+
+
+def test_nw_similarity_hand_cases():
+    from oracle import evaluate
+    assert evaluate.nw_matched([(0, 0), (1, 1), (2, 2)], [(0, 0), (2, 2)]) == 2
+    assert evaluate.nw_matched([], [(0, 0)]) == 0
+    # order matters (an alignment of sequences, not a set overlap)
+    assert evaluate.nw_matched([(0, 0), (1, 1)], [(1, 1), (0, 0)]) == 1
+    r = evaluate.similarity([[(0, 0), (1, 1), (2, 2)]], [[(0, 0), (2, 2)]])
+    assert (r["matched"], r["auto"], r["human"]) == (2, 3, 2)
+    assert r["similarity"] == pytest.approx(0.8)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_nw_similarity_equals_lcs_brute_force(seed):
+    from oracle import evaluate
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        a = [tuple(x) for x in rng.integers(0, 3, size=(int(rng.integers(0, 7)), 2))]
+        b = [tuple(x) for x in rng.integers(0, 3, size=(int(rng.integers(0, 7)), 2))]
+        assert evaluate.nw_matched(a, b) == _lcs_brute(a, b)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nw_similarity_of_monotone_alignments_is_their_intersection(seed):
+    # two link lists taken from monotone paths: the NW alignment pairs up
+    # exactly the common links, so the similarity is the links' micro-F1
+    from oracle import evaluate
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(30):
+        n, m = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+
+        def monotone():
+            k = int(rng.integers(0, min(n, m) + 1))
+            i = np.sort(rng.choice(n, k, replace=False))
+            j = np.sort(rng.choice(m, k, replace=False))
+            return [(int(x), int(y)) for x, y in zip(i, j)]
+        a, b = monotone(), monotone()
+        assert evaluate.nw_matched(a, b) == len(set(a) & set(b))
+
+
+# --- bi-directional mining (Section 5.4, BI) ---
+
+def _random_dict(seed, v_src=60, v_tgt=40, kmax=4):
+    rng = np.random.default_rng(seed)
+    lists = [sorted(rng.choice(v_tgt, int(rng.integers(0, kmax + 1)), replace=False).tolist()) for _ in range(v_src)]
+    off = np.zeros(v_src + 1, np.int32)
+    off[1:] = np.cumsum([len(x) for x in lists])
+    return synth.Dictionary(v_src, v_tgt, off, np.array([t for x in lists for t in x], np.int32))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_dictionary_transpose_is_the_inverse_relation(seed):
+    from oracle import bi
+    d = _random_dict(seed)
+    r = bi.transpose_dictionary(d)
+    assert (r.v_src, r.v_tgt) == (d.v_tgt, d.v_src) and len(r.tgt) == len(d.tgt)
+    for t in range(d.v_tgt):
+        lst = r.tgt[r.off[t]:r.off[t + 1]].tolist()
+        assert lst == sorted(set(lst))
+        assert set(lst) == {v for v in range(d.v_src) if t in d.tgt[d.off[v]:d.off[v + 1]]}
+    rr = bi.transpose_dictionary(r)
+    assert np.array_equal(rr.off, d.off) and np.array_equal(rr.tgt, d.tgt)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_reverse_counts_with_the_transposed_dictionary_are_swapped(seed):
+    # ms of the reverse direction counts target positions whose token has a
+    # (reverse) translation in the source sentence: that is the forward mt,
+    # and the reverse mt is the forward ms
+    from oracle import bi
+    rng = np.random.default_rng(10 + seed)
+    d = _random_dict(20 + seed)
+    r = bi.transpose_dictionary(d)
+    for _ in range(50):
+        src = np.sort(rng.integers(0, d.v_src, int(rng.integers(1, 12))))
+        tgt = np.sort(rng.integers(0, d.v_tgt, int(rng.integers(1, 12))))
+        ms, mt = oracle.counts(src, tgt, d)
+        assert oracle.counts(tgt, src, r) == (mt, ms)
+
+
+def test_reverse_mining_of_the_transposed_problem_has_the_same_optimum():
+    # with the transposed dictionary and the two overlap weights exchanged the
+    # reverse similarity matrix is the transpose of the forward one, so every
+    # pair's optimum H(N, M) is unchanged
+    from oracle import bi
+    b = synth.make_batch(71, 6, v_src=3000, v_tgt=3000, size_median=20, size_hi=40)
+    w, bias, gap, thr = np.array([4.0, 3.0, -2.0, 1.0]), -3.0, 0.3, 0.5
+    f = oracle.mine(b, w, bias, gap, thr)
+    r = oracle.mine(bi.reversed_batch(b), w[[1, 0, 2, 3]], bias, gap, thr)
+    assert np.allclose(f["score"], r["score"], rtol=0, atol=1e-12)
+
+
+def test_combine_links_hand_case():
+    from oracle import bi
+    fwd = [[(0, 0, 0.9), (2, 1, 0.8)]]
+    rev = [[(1, 2, 0.7), (3, 3, 0.6)]]  # reverse coordinates: (j, i)
+    u = bi.combine(fwd, rev, "union")[0]
+    assert [(i, j) for i, j, _, _ in u] == [(0, 0), (2, 1), (3, 3)]
+    assert u[1][2:] == (0.8, 0.7)
+    assert math.isnan(u[0][3]) and math.isnan(u[2][2])
+    x = bi.combine(fwd, rev, "intersect")[0]
+    assert [(i, j) for i, j, _, _ in x] == [(2, 1)]
