@@ -142,12 +142,16 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         }
     }
     rc = 0;
+    // the cell of step u is column j = jl + u + c0 of this lane's row; it
+    // exists when 0 <= jl + u < width (width 0 for a row below the pair)
+    const int jl = col_base - lane - C.c0;
+    const uint32_t width = C.rv ? (uint32_t)(C.c1 - C.c0) : 0u;
+    float *const hrow_at = hrow_w + C.c0 + jl;  // lane 31 stores column j at hrow_at[u]
 #pragma unroll
     for (int u = 0; u < 32; ++u) {
         float a_up = __shfl_up_sync(kFull, a_down, 1);
         const float h0 = __shfl_sync(kFull, hv, u);
         if (lane == 0) a_up = h0;
-        const int j = col_base + u - lane;
         const float sv = (u >= lane) ? cur[u] : prev[u];
         // branch-free step: computed in every lane, committed where the cell
         // exists (the skew leaves lanes outside the pair at both ends).  Only
@@ -157,7 +161,7 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         // its last, or below the last row).  Nor do the code bits: those of
         // an invalid cell land in a word that is never stored (before the
         // first block) or at a cell the walk never visits.
-        const bool valid = C.rv && j >= C.c0 && j < C.c1;
+        const bool valid = (uint32_t)(jl + u) < width;
         const float d = fmaxf(fmaxf(sv, b), a_up);
         const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : 0u);
         rc |= (uint64_t)code << (2 * u);
@@ -165,7 +169,7 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         const float nb2 = __fsub_rn(e, a_up);
         a_down = __fsub_rn(e, b);
         b = valid ? nb2 : b;
-        if (valid && lane == 31) __stcg(hrow_w + j, a_down);
+        if (valid && lane == 31) __stcg(hrow_at + u, a_down);
     }
     // the word of block jb-1 is complete: its columns came at steps u >= lane
     // of iteration jb-1 and u < lane of iteration jb
