@@ -37,7 +37,8 @@ METRIC = "DP cell-updates/s (batched hard-NW mining)"
 UNIT = "cell-updates/s"
 N_SMS = 152
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes issue per clock
-# algorithmic lane-operations per cell, see the design doc (roofline model)
+# algorithmic lane-operations per cell of the roofline model when the path is
+# timed from precomputed counts (similarity and DP only)
 OPS_SIM = 11   # 4 quotients, 4 multiply-adds, exp, add, reciprocal
 OPS_DP = 8     # 3 candidates, 2 max, 2 compare/select, 1 pack
 
@@ -428,7 +429,9 @@ def main():
     pairs_s = plan.n_pairs * world * args.steps / secs
     launches = sum(n for _, n in kt.values())
 
-    # roofline of the dominant kernel (ALU issue bound)
+    # roofline of the dominant kernel: ALU issue bound (integer compares,
+    # hashing and bit-sliced counting for the counts; FP adds and selects for
+    # the DP -- no dense contraction anywhere)
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(kt[dom][1], 1)
     n_cells = plan.n_cells
