@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--tune-steps", type=int, default=200)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-bi", action="store_true", help="skip the bi-directional mining record")
+    ap.add_argument("--no-anchors", action="store_true", help="skip the anchor-token record")
+    ap.add_argument("--anchor-pairs", type=int, default=10_000)
     ap.add_argument("--soft-step", action="store_true",
                     help="only time one soft-NW forward+backward on a 4,096-pair tuning minibatch (profiling)")
     return ap.parse_args()
@@ -297,6 +299,37 @@ def run_bi(args, db, plan, params, options):
     return rec
 
 
+def run_anchors(args):
+    """Anchor tokens (Section 5.3) on planted Wikipedia-shaped pairs: the GPU
+    time of extending the corpora and the dictionary, and the default
+    classifier's links against the gold links without and with anchors."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    v_anchor = 100_000
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 60))
+    dic = synth.make_dictionary(rng, 50_000, 50_000)
+    b = synth.tune_batch(args.anchor_pairs, seed=synth.SEED_BASE + 61, dic=dic)
+    sa, ta = synth.make_anchors(b, synth.SEED_BASE + 62, v_anchor=v_anchor)
+    db = miner.DeviceBatch.from_batch(b)
+    dev = [(torch.from_numpy(a.sent_off).cuda(), torch.from_numpy(a.ids).cuda()) for a in (sa, ta)]
+    miner.add_anchors(db, *dev, v_anchor)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ext = miner.add_anchors(db, *dev, v_anchor)
+    torch.cuda.synchronize()
+    extend_ms = (time.perf_counter() - t0) * 1e3
+
+    def evaluate(batch):
+        with miner.Plan(batch) as plan:
+            out = plan.mine(miner.MineParams())
+            gold = torch.from_numpy(miner.gold_cells(b, plan)).cuda()
+            tp, nl, ng = (int(x) for x in plan.link_gold_counts(out, gold).cpu().tolist())
+        p, r = tp / max(nl, 1), tp / max(ng, 1)
+        return {"precision": p, "recall": r, "f1": 2 * p * r / (p + r) if p + r else 0.0, "links": nl, "gold": ng}
+    return {"pairs": b.n_pairs, "v_anchor": v_anchor, "anchor_tokens": int(len(sa.ids) + len(ta.ids)),
+            "extend_ms": extend_ms, "words": evaluate(db), "with_anchors": evaluate(ext)}
+
+
 def _pinned_inputs(batch):
     import torch
     host = [batch.src.doc_sent_off, batch.src.sent_tok_off, batch.src.tok, batch.tgt.doc_sent_off,
@@ -447,6 +480,10 @@ def main():
                 "ops_per_launch": ops, "ms_per_launch": dom_ms,
                 "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lane-ops/clk x {sm_max:.0f} MHz (max SM clock)"}
 
+    anchors_rec = None
+    if rank == 0 and not args.no_anchors:
+        anchors_rec = run_anchors(args)
+
     bi_rec = None
     if not args.no_bi:
         bi_rec = run_bi(args, db, plan, params, dict(tuned["best"]) if tuned else {})
@@ -487,7 +524,7 @@ def main():
                 "kernel_ms": {k: v[0] / max(args.steps, 1) for k, v in kt.items() if v[1]},
                 "direct_launch_ms_per_step": 1000 * secs_direct / args.steps,
                 "graph": {"captures": plan.get_option("graph_captures")},
-                "autotune": tuned, "tune": tune_rec, "bi": bi_rec,
+                "autotune": tuned, "tune": tune_rec, "bi": bi_rec, "anchors": anchors_rec,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()

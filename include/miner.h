@@ -179,6 +179,36 @@ int mine_link_gold_counts(mine_plan *plan, const mine_out *out, const uint8_t *g
  * unspecified. */
 int mine_dict_transpose(const mine_dict *dict, int32_t *off_out, int32_t *tgt_out, miner_stream_t stream);
 
+/* ---- Anchors (Section 5.3: names, dates, numbers and references that two
+ * Wikipedia sentences share mark them as likely translations) ----
+ * An anchor is an id of its own vocabulary [0, v_anchor), the same in both
+ * languages.  Reading: it takes part in the overlap counts of Section 4 as a
+ * word that translates to itself -- anchor a of a sentence becomes token
+ * v_words + a of its corpus (v_words: that corpus's vocabulary size), and the
+ * dictionary gains the entries v_src + a -> {v_tgt + a}.  The extended
+ * corpora and dictionary are then mined like any others. */
+
+/* The corpus with every sentence's anchors appended to its tokens (as
+ * v_words + a; anchors sort after every word, so sorted anchors keep the
+ * sentence sorted).  anchor_off: n_sents+1 int64, anchor_ids: n_anchor_tok
+ * int32 (device; per sentence sorted and distinct -- mine_plan_create rejects
+ * the extended corpus otherwise).  Outputs (device, caller-allocated):
+ * sent_tok_off_out n_sents+1 int64, tok_out n_tok + n_anchor_tok int32; the
+ * document offsets are unchanged.  SYNCHRONOUS on the stream (it checks the
+ * anchors first).  MINE_EINVAL for a NULL argument, v_words + v_anchor beyond
+ * int32, anchor offsets that do not start at 0, decrease or do not end at
+ * n_anchor_tok, or an anchor id outside [0, v_anchor). */
+int mine_corpus_add_anchors(const mine_corpus *words, int32_t v_words, const int64_t *anchor_off,
+                            const int32_t *anchor_ids, int64_t n_anchor_tok, int32_t v_anchor,
+                            int64_t *sent_tok_off_out, int32_t *tok_out, miner_stream_t stream);
+
+/* The dictionary with the identity entries of v_anchor anchors appended:
+ * off_out v_src + v_anchor + 1 int32, tgt_out n_entries + v_anchor int32
+ * (device, caller-allocated).  Asynchronous.  MINE_EINVAL for a NULL
+ * argument or sizes beyond int32. */
+int mine_dict_add_anchors(const mine_dict *dict, int32_t v_anchor, int32_t *off_out, int32_t *tgt_out,
+                          miner_stream_t stream);
+
 #define MINE_BI_UNION 0     /* links kept by either direction */
 #define MINE_BI_INTERSECT 1 /* links kept by both directions */
 

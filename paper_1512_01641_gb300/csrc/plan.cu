@@ -1030,6 +1030,41 @@ int mine_dict_transpose(const mine_dict *d, int32_t *off_out, int32_t *tgt_out, 
     return MINE_OK;
 }
 
+int mine_corpus_add_anchors(const mine_corpus *w, int32_t v_words, const int64_t *anchor_off,
+                            const int32_t *anchor_ids, int64_t n_anchor_tok, int32_t v_anchor,
+                            int64_t *sent_tok_off_out, int32_t *tok_out, miner_stream_t stream) {
+    if (!w || !anchor_off || !sent_tok_off_out || !w->sent_tok_off || w->n_sents < 0 || w->n_tok < 0 ||
+        n_anchor_tok < 0 || v_words <= 0 || v_anchor <= 0 || (int64_t)v_words + v_anchor > INT32_MAX ||
+        (n_anchor_tok > 0 && !anchor_ids) || (w->n_tok > 0 && !w->tok) || (w->n_tok + n_anchor_tok > 0 && !tok_out))
+        return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int device;
+    MINE_CK(cudaGetDevice(&device));
+    PoolTemp<uint32_t> status(st);
+    MINE_CK(dalloc(&status.p, 1, device, st));
+    MINE_CK(cudaMemsetAsync(status.p, 0, sizeof(uint32_t), st));
+    MINE_CK(launch_anchor_check(anchor_off, w->n_sents, anchor_ids, n_anchor_tok, v_anchor, status.p, st));
+    uint32_t bad = 0;
+    MINE_CK(cudaMemcpyAsync(&bad, status.p, sizeof bad, cudaMemcpyDeviceToHost, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    if (bad) return MINE_EINVAL;
+    MINE_CK(launch_anchor_merge(w->sent_tok_off, w->tok, anchor_off, anchor_ids, w->n_sents, v_words,
+                                sent_tok_off_out, tok_out, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    return MINE_OK;
+}
+
+int mine_dict_add_anchors(const mine_dict *d, int32_t v_anchor, int32_t *off_out, int32_t *tgt_out,
+                          miner_stream_t stream) {
+    if (!d || !off_out || !tgt_out || !d->off || d->v_src <= 0 || d->v_tgt <= 0 || d->n_entries < 0 ||
+        v_anchor <= 0 || (d->n_entries > 0 && !d->tgt) || (int64_t)d->v_src + v_anchor > INT32_MAX ||
+        (int64_t)d->v_tgt + v_anchor > INT32_MAX || d->n_entries + v_anchor > INT32_MAX)
+        return MINE_EINVAL;
+    MINE_CK(launch_anchor_dict(d->off, d->tgt, d->v_src, d->v_tgt, d->n_entries, v_anchor, off_out, tgt_out,
+                               (cudaStream_t)stream));
+    return MINE_OK;
+}
+
 int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const mine_out *orv, int mode,
                        mine_bi_out *o, miner_stream_t stream) {
     if (!f || !r || !of || !orv || !o || (mode != MINE_BI_UNION && mode != MINE_BI_INTERSECT)) return MINE_EINVAL;

@@ -80,6 +80,9 @@ _SIGS = {
     "mine_plan_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mine_link_gold_counts": (C.c_int, [C.c_void_p, C.POINTER(_Out), C.c_void_p, C.c_void_p, C.c_void_p]),
     "mine_dict_transpose": (C.c_int, [C.POINTER(_Dict), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_corpus_add_anchors": (C.c_int, [C.POINTER(_Corpus), C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_dict_add_anchors": (C.c_int, [C.POINTER(_Dict), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mine_links_combine": (C.c_int, [C.c_void_p, C.POINTER(_Out), C.c_void_p, C.POINTER(_Out), C.c_int,
                                      C.POINTER(_BiOut), C.c_void_p]),
     "mine_plan_set_option": (C.c_int, [C.c_void_p, C.c_int, C.c_int64]),
@@ -344,6 +347,32 @@ def dict_transpose(dict_off, dict_tgt, v_src: int, v_tgt: int, stream=None):
     tgt = torch.empty(max(dict_tgt.numel(), 1), dtype=torch.int32, device=dict_off.device)
     _check(lib().mine_dict_transpose(C.byref(d), _ptr(off), _ptr(tgt), _stream(stream)), "mine_dict_transpose")
     return off, tgt[:dict_tgt.numel()]
+
+
+def add_anchors(dbatch: DeviceBatch, src_anchors, tgt_anchors, v_anchor: int, stream=None) -> DeviceBatch:
+    """Anchors (Section 5.3): the batch with every sentence's anchor ids
+    (src_anchors / tgt_anchors: (sent_off int64, ids int32) device tensors,
+    per sentence sorted and distinct, ids in [0, v_anchor)) among its tokens
+    and the anchors' identity entries in the dictionary
+    (mine_corpus_add_anchors, mine_dict_add_anchors)."""
+    import torch
+    L = lib()
+    cs, ct, d = dbatch.c_structs()
+
+    def corpus(c, words, anc, v_words):
+        aoff, ids = anc
+        off = torch.empty(words[1].numel(), dtype=torch.int64, device=words[1].device)
+        tok = torch.empty(max(words[2].numel() + ids.numel(), 1), dtype=torch.int32, device=words[1].device)
+        _check(L.mine_corpus_add_anchors(C.byref(c), int(v_words), _ptr(aoff), _ptr(ids), ids.numel(), int(v_anchor),
+                                         _ptr(off), _ptr(tok), _stream(stream)), "mine_corpus_add_anchors")
+        return words[0], off, tok[:words[2].numel() + ids.numel()]
+    src = corpus(cs, dbatch.src, src_anchors, dbatch.v_src)
+    tgt = corpus(ct, dbatch.tgt, tgt_anchors, dbatch.v_tgt)
+    off = torch.empty(dbatch.v_src + v_anchor + 1, dtype=torch.int32, device=dbatch.dict_off.device)
+    tgt_d = torch.empty(dbatch.dict_tgt.numel() + v_anchor, dtype=torch.int32, device=dbatch.dict_off.device)
+    _check(L.mine_dict_add_anchors(C.byref(d), int(v_anchor), _ptr(off), _ptr(tgt_d), _stream(stream)),
+           "mine_dict_add_anchors")
+    return DeviceBatch(*src, *tgt, off, tgt_d, dbatch.v_src + v_anchor, dbatch.v_tgt + v_anchor)
 
 
 BI_MODES = {"union": 0, "intersect": 1}

@@ -396,3 +396,43 @@ def from_lists(src_docs, tgt_docs, dic_lists, v_tgt=None) -> Batch:
     n = len(src_docs)
     return Batch(corpus(src_docs), corpus(tgt_docs), dic, np.zeros(n, bool),
                  [np.zeros((0, 2), np.int32) for _ in range(n)])
+
+
+@dataclass
+class Anchors:
+    """Per-sentence anchor ids (CSR over the sentences of one corpus): the
+    language-independent names, dates, numbers and reference keys a sentence
+    carries, ids in [0, v_anchor), sorted and distinct per sentence."""
+    sent_off: np.ndarray  # int64, n_sents+1
+    ids: np.ndarray       # int32
+
+
+def make_anchors(batch: Batch, seed: int, v_anchor: int = 100_000, p_anchor: float = 0.3,
+                 p_keep: float = 0.9, max_per: int = 2) -> tuple:
+    """Anchors for both corpora of a batch: a source sentence carries 1..max_per
+    random anchors with probability p_anchor; the target sentence planted from
+    it (its gold link) carries each of them with probability p_keep; every
+    other target sentence carries random anchors like a source sentence.
+    Returns (source Anchors, target Anchors)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def draw(n_sents):
+        has = rng.random(n_sents) < p_anchor
+        cnt = np.where(has, rng.integers(1, max_per + 1, n_sents), 0)
+        return [sorted(set(rng.integers(0, v_anchor, int(c)).tolist())) for c in cnt]
+
+    n_src = int(batch.src.sent_tok_off.size - 1)
+    n_tgt = int(batch.tgt.sent_tok_off.size - 1)
+    src = draw(n_src)
+    tgt = draw(n_tgt)
+    for k, g in enumerate(batch.gold):
+        s0, t0 = int(batch.src.doc_sent_off[k]), int(batch.tgt.doc_sent_off[k])
+        for i, j in np.asarray(g).reshape(-1, 2).tolist():
+            kept = [a for a in src[s0 + i] if rng.random() < p_keep]
+            tgt[t0 + j] = sorted(kept)
+
+    def csr(lists):
+        off = _csr(np.asarray([len(x) for x in lists], np.int64))
+        ids = np.asarray([a for x in lists for a in x], np.int32)
+        return Anchors(off, ids)
+    return csr(src), csr(tgt)

@@ -460,3 +460,46 @@ def test_combine_links_hand_case():
     assert math.isnan(u[0][3]) and math.isnan(u[2][2])
     x = bi.combine(fwd, rev, "intersect")[0]
     assert [(i, j) for i, j, _, _ in x] == [(2, 1)]
+
+
+# --- anchors (Section 5.3): shared names, dates, numbers, references ---
+
+@pytest.mark.parametrize("seed", range(3))
+def test_anchor_extension_adds_shared_anchor_positions_to_the_counts(seed):
+    # closed form: with anchors as self-translating tokens, ms gains the
+    # source anchor positions whose anchor the target sentence carries and mt
+    # the target anchor positions whose anchor the source sentence carries;
+    # nothing else changes (anchor ids never meet word ids)
+    from oracle import anchors
+    b = synth.make_batch(300 + seed, 6, v_src=2000, v_tgt=2000, planted_frac=0.5, size_median=12, size_hi=30)
+    sa, ta = synth.make_anchors(b, 400 + seed, v_anchor=40, p_anchor=0.7)
+    e = anchors.extend_batch(b, sa, ta, 40)
+    rng = np.random.default_rng(seed)
+    n_s, n_t = len(b.src.sent_tok_off) - 1, len(b.tgt.sent_tok_off) - 1
+    for _ in range(200):
+        i, j = int(rng.integers(n_s)), int(rng.integers(n_t))
+        ms, mt = oracle.counts(b.src.sentence(i), b.tgt.sentence(j), b.dic)
+        xs, xt = anchors.shared_positions(sa.ids[sa.sent_off[i]:sa.sent_off[i + 1]],
+                                          ta.ids[ta.sent_off[j]:ta.sent_off[j + 1]])
+        assert oracle.counts(e.src.sentence(i), e.tgt.sentence(j), e.dic) == (ms + xs, mt + xt)
+        assert len(e.src.sentence(i)) == len(b.src.sentence(i)) + sa.sent_off[i + 1] - sa.sent_off[i]
+
+
+def test_anchor_dictionary_entries_are_identities():
+    from oracle import anchors
+    d = _random_dict(7)
+    e = anchors.extend_dictionary(d, 5)
+    assert (e.v_src, e.v_tgt) == (d.v_src + 5, d.v_tgt + 5)
+    assert np.array_equal(e.off[:d.v_src + 1], d.off) and np.array_equal(e.tgt[:len(d.tgt)], d.tgt)
+    for a in range(5):
+        assert e.tgt[e.off[d.v_src + a]:e.off[d.v_src + a + 1]].tolist() == [d.v_tgt + a]
+
+
+def test_planted_anchors_follow_the_gold_links():
+    b = synth.make_batch(310, 8, planted_frac=1.0, size_median=15, size_hi=40)
+    sa, ta = synth.make_anchors(b, 311, p_keep=1.0)
+    for k, g in enumerate(b.gold):
+        s0, t0 = b.src.doc_sent_off[k], b.tgt.doc_sent_off[k]
+        for i, j in g.tolist():
+            assert (ta.ids[ta.sent_off[t0 + j]:ta.sent_off[t0 + j + 1]].tolist() ==
+                    sa.ids[sa.sent_off[s0 + i]:sa.sent_off[s0 + i + 1]].tolist())
