@@ -1,7 +1,7 @@
 """FP64 / exact oracle of the tuning objective (test infrastructure only).
 
-Section 5.2 tunes the threshold and the gap penalty by naive random selection
-of parameter values, keeping those whose automatic alignment of sample
+Section 5.2 tunes the threshold and the gap penalty by drawing parameter
+values at random and keeping those whose automatic alignment of sample
 article pairs is most similar to a human alignment of them; the similarity is
 a percentage, and the comparison of the two alignments is made with a
 Needleman-Wunsch alignment.

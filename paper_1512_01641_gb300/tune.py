@@ -112,8 +112,8 @@ def random_draws(trials: int, seed: int = 0, theta0=THETA0, ranges=RANDOM_RANGES
 
 def random_search(train: TuneData, held_out: TuneData, trials: int = 343, seed: int = 0, theta0=THETA0,
                   ranges=RANDOM_RANGES) -> TuneResult:
-    """The paper's tuner (Section 5.2): naive random selection of parameter
-    values, keeping the setting whose hard alignment of the training pairs is
+    """The paper's tuner (Section 5.2): parameter settings drawn at random,
+    keeping the setting whose hard alignment of the training pairs is
     most similar to the gold alignment (micro-F1, see the module docstring).
     The default budget equals the grid's 343 settings; ranges may name a
     subset of b, gap, thr (the paper tunes thr and gap)."""
