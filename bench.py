@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--long-n", type=int, default=5000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-stream-steps", type=int, default=16)
     ap.add_argument("--cpu-pairs", type=int, default=8000, help="pairs in the oracle's timed sample")
     ap.add_argument("--no-tune", action="store_true", help="skip the tuning comparison")
