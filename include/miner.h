@@ -195,9 +195,9 @@ int mine_dict_transpose(const mine_dict *dict, int32_t *off_out, int32_t *tgt_ou
  * the extended corpus otherwise).  Outputs (device, caller-allocated):
  * sent_tok_off_out n_sents+1 int64, tok_out n_tok + n_anchor_tok int32; the
  * document offsets are unchanged.  SYNCHRONOUS on the stream (it checks the
- * anchors first).  MINE_EINVAL for a NULL argument, v_words + v_anchor beyond
- * int32, anchor offsets that do not start at 0, decrease or do not end at
- * n_anchor_tok, or an anchor id outside [0, v_anchor). */
+ * offsets first).  MINE_EINVAL for a NULL argument, v_words + v_anchor beyond
+ * int32, word or anchor offsets that do not start at 0, decrease or do not
+ * end at n_tok / n_anchor_tok, or an anchor id outside [0, v_anchor). */
 int mine_corpus_add_anchors(const mine_corpus *words, int32_t v_words, const int64_t *anchor_off,
                             const int32_t *anchor_ids, int64_t n_anchor_tok, int32_t v_anchor,
                             int64_t *sent_tok_off_out, int32_t *tok_out, miner_stream_t stream);

@@ -9,15 +9,18 @@
 namespace gbm {
 namespace {
 
-// Anchor offsets start at 0, never decrease and end at n_anchor_tok; ids lie
-// in [0, v_anchor).  Any violation sets status bit 0.
-__global__ void anchor_check_kernel(const int64_t *__restrict__ aoff, int64_t n_sents, const int32_t *__restrict__ ids,
-                                    int64_t n_anchor_tok, int32_t v_anchor, uint32_t *status) {
+// Word and anchor offsets start at 0, never decrease and end at n_tok and
+// n_anchor_tok; anchor ids lie in [0, v_anchor).  Any violation sets status
+// bit 0 (the merge indexes both token arrays through these offsets).
+__global__ void anchor_check_kernel(const int64_t *__restrict__ woff, int64_t n_tok, const int64_t *__restrict__ aoff,
+                                    int64_t n_sents, const int32_t *__restrict__ ids, int64_t n_anchor_tok,
+                                    int32_t v_anchor, uint32_t *status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t s = t0; s < n_sents; s += stride)
-        if (aoff[s + 1] < aoff[s]) atomicOr(status, 1u);
-    if (t0 == 0 && (aoff[0] != 0 || aoff[n_sents] != n_anchor_tok)) atomicOr(status, 1u);
+        if (aoff[s + 1] < aoff[s] || woff[s + 1] < woff[s]) atomicOr(status, 1u);
+    if (t0 == 0 && (aoff[0] != 0 || aoff[n_sents] != n_anchor_tok || woff[0] != 0 || woff[n_sents] != n_tok))
+        atomicOr(status, 1u);
     for (int64_t x = t0; x < n_anchor_tok; x += stride)
         if (ids[x] < 0 || ids[x] >= v_anchor) atomicOr(status, 1u);
 }
@@ -62,10 +65,11 @@ int grid_of(int64_t n, int per_block) {
 
 }  // namespace
 
-cudaError_t launch_anchor_check(const int64_t *aoff, int64_t n_sents, const int32_t *ids, int64_t n_anchor_tok,
-                                int32_t v_anchor, uint32_t *status, cudaStream_t st) {
+cudaError_t launch_anchor_check(const int64_t *woff, int64_t n_tok, const int64_t *aoff, int64_t n_sents,
+                                const int32_t *ids, int64_t n_anchor_tok, int32_t v_anchor, uint32_t *status,
+                                cudaStream_t st) {
     anchor_check_kernel<<<grid_of(n_sents > n_anchor_tok ? n_sents : n_anchor_tok, 256), 256, 0, st>>>(
-        aoff, n_sents, ids, n_anchor_tok, v_anchor, status);
+        woff, n_tok, aoff, n_sents, ids, n_anchor_tok, v_anchor, status);
     return cudaGetLastError();
 }
 

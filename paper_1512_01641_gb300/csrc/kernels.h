@@ -115,9 +115,11 @@ cudaError_t launch_dict_count(const int32_t *tgt, int64_t n_entries, int32_t *cn
 cudaError_t launch_dict_scatter(const int32_t *off, int32_t v_src, const int32_t *tgt, int32_t *cursor,
                                 int32_t *tgt_out, cudaStream_t st);
 cudaError_t launch_dict_sort(const int32_t *off_out, int32_t v_tgt, int32_t *tgt_out, cudaStream_t st);
-// Anchor tokens (anchors.cu): status bit 0 set for malformed anchor lists.
-cudaError_t launch_anchor_check(const int64_t *aoff, int64_t n_sents, const int32_t *ids, int64_t n_anchor_tok,
-                                int32_t v_anchor, uint32_t *status, cudaStream_t st);
+// Anchor tokens (anchors.cu): status bit 0 set for malformed word offsets or
+// anchor lists.
+cudaError_t launch_anchor_check(const int64_t *woff, int64_t n_tok, const int64_t *aoff, int64_t n_sents,
+                                const int32_t *ids, int64_t n_anchor_tok, int32_t v_anchor, uint32_t *status,
+                                cudaStream_t st);
 cudaError_t launch_anchor_merge(const int64_t *woff, const int32_t *words, const int64_t *aoff, const int32_t *ids,
                                 int64_t n_sents, int32_t v_words, int64_t *out_off, int32_t *out, cudaStream_t st);
 cudaError_t launch_anchor_dict(const int32_t *off, const int32_t *tgt, int32_t v_src, int32_t v_tgt,

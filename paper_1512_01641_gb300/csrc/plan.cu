@@ -1043,7 +1043,8 @@ int mine_corpus_add_anchors(const mine_corpus *w, int32_t v_words, const int64_t
     PoolTemp<uint32_t> status(st);
     MINE_CK(dalloc(&status.p, 1, device, st));
     MINE_CK(cudaMemsetAsync(status.p, 0, sizeof(uint32_t), st));
-    MINE_CK(launch_anchor_check(anchor_off, w->n_sents, anchor_ids, n_anchor_tok, v_anchor, status.p, st));
+    MINE_CK(launch_anchor_check(w->sent_tok_off, w->n_tok, anchor_off, w->n_sents, anchor_ids, n_anchor_tok, v_anchor,
+                                status.p, st));
     uint32_t bad = 0;
     MINE_CK(cudaMemcpyAsync(&bad, status.p, sizeof bad, cudaMemcpyDeviceToHost, st));
     MINE_CK(cudaStreamSynchronize(st));

@@ -86,17 +86,20 @@ def test_anchors_mark_parallel_sentences():
     assert fp1 / max(tp1 + fp1, 1) <= fp0 / max(tp0 + fp0, 1) + 0.01
 
 
-@pytest.mark.parametrize("bad", ["id_out_of_range", "offsets_end"])
+@pytest.mark.parametrize("bad", ["id_out_of_range", "offsets_end", "word_offsets_decrease"])
 def test_add_anchors_rejects_malformed_anchor_lists(bad):
+    # the checks run before anything is read through the offsets
     import torch
     from paper_1512_01641_gb300 import miner
     b, sa, ta = _batch_and_anchors(350, 4)
     ids = sa.ids.copy()
     off = sa.sent_off.copy()
+    db = miner.DeviceBatch.from_batch(b)
     if bad == "id_out_of_range":
         ids[0] = V_ANCHOR
-    else:
+    elif bad == "offsets_end":
         off[-1] -= 1
+    else:
+        db.src[1][3] = db.src[1][2] - 1
     with pytest.raises(miner.MinerError):
-        miner.add_anchors(miner.DeviceBatch.from_batch(b), (torch.from_numpy(off).cuda(), torch.from_numpy(ids).cuda()),
-                          _dev_anchors(ta), V_ANCHOR)
+        miner.add_anchors(db, (torch.from_numpy(off).cuda(), torch.from_numpy(ids).cuda()), _dev_anchors(ta), V_ANCHOR)
