@@ -234,7 +234,9 @@ typedef struct {
  * intersection (mode, MINE_BI_*).  rev must hold the same pairs with the roles
  * swapped, N_k(rev) = M_k(fwd) and M_k(rev) = N_k(fwd) (checked on the host:
  * MINE_EINVAL).  Asynchronous on the stream, after both outputs are complete
- * on it; uses a temporary of n_docs int32 from the library's pool. */
+ * on it; uses a temporary of n_docs int32 from the library's pool.  Every
+ * access stays inside the buffers' declared capacities even for outputs that
+ * did not come from mining these plans (the links are then unspecified). */
 int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, const mine_out *out_rev,
                        int mode, mine_bi_out *out, miner_stream_t stream);
 

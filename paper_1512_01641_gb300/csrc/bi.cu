@@ -60,17 +60,21 @@ __global__ void dict_sort_kernel(const int32_t *__restrict__ off_out, int32_t v_
 
 // One thread per pair: merge the forward links (i, j) and the reverse links
 // (i', j') -> (j', i'), both ascending in i and in j, into one list ascending
-// in (i, j); a link in both lists appears once with both similarities.
+// in (i, j); a link in both lists appears once with both similarities.  Every
+// range is clamped to its buffer's capacity and no write goes past the
+// output's, so offsets that did not come from mining these plans cannot move
+// an access out of bounds.
 template <bool WRITE>
 __global__ void links_combine_kernel(LinkView fwd, LinkView rev, int64_t n_pairs, int mode, int32_t *count,
-                                     const int64_t *__restrict__ out_off, int32_t *__restrict__ out_i,
+                                     int64_t out_cap, const int64_t *__restrict__ out_off, int32_t *__restrict__ out_i,
                                      int32_t *__restrict__ out_j, float *__restrict__ out_sf,
                                      float *__restrict__ out_sr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const float nan = __int_as_float(0x7fc00000);
+    auto clamp = [](int64_t x, int64_t hi) { return x < 0 ? 0 : (x > hi ? hi : x); };
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_pairs; k += stride) {
-        int64_t a = fwd.off[k], c = rev.off[k];
-        const int64_t ae = fwd.off[k + 1], ce = rev.off[k + 1];
+        int64_t a = clamp(fwd.off[k], fwd.cap), c = clamp(rev.off[k], rev.cap);
+        const int64_t ae = clamp(fwd.off[k + 1], fwd.cap), ce = clamp(rev.off[k + 1], rev.cap);
         int64_t o = WRITE ? out_off[k] : 0;
         int32_t n = 0;
         while (a < ae || c < ce) {
@@ -78,14 +82,14 @@ __global__ void links_combine_kernel(LinkView fwd, LinkView rev, int64_t n_pairs
             const int64_t rk = c < ce ? ((int64_t)rev.j[c] << 32) | (uint32_t)rev.i[c] : INT64_MAX;
             const bool in_f = fk <= rk, in_r = rk <= fk;
             if (mode == 0 || (in_f && in_r)) {
-                if (WRITE) {
+                if (WRITE && o < out_cap) {
                     const int64_t key = in_f ? fk : rk;
                     out_i[o] = (int32_t)(key >> 32);
                     out_j[o] = (int32_t)(key & 0xffffffff);
                     out_sf[o] = in_f ? fwd.s[a] : nan;
                     out_sr[o] = in_r ? rev.s[c] : nan;
                     ++o;
-                } else {
+                } else if (!WRITE) {
                     ++n;
                 }
             }
@@ -129,15 +133,15 @@ cudaError_t launch_dict_sort(const int32_t *off_out, int32_t v_tgt, int32_t *tgt
 }
 
 cudaError_t launch_links_combine(LinkView fwd, LinkView rev, int64_t n_pairs, int mode, int32_t *count,
-                                 const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_sf,
-                                 float *out_sr, cudaStream_t st) {
+                                 int64_t out_cap, const int64_t *out_off, int32_t *out_i, int32_t *out_j,
+                                 float *out_sf, float *out_sr, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
     if (out_i)
-        links_combine_kernel<true><<<grid_for(n_pairs, 128), 128, 0, st>>>(fwd, rev, n_pairs, mode, count, out_off,
-                                                                          out_i, out_j, out_sf, out_sr);
+        links_combine_kernel<true><<<grid_for(n_pairs, 128), 128, 0, st>>>(fwd, rev, n_pairs, mode, count, out_cap,
+                                                                          out_off, out_i, out_j, out_sf, out_sr);
     else
-        links_combine_kernel<false><<<grid_for(n_pairs, 128), 128, 0, st>>>(fwd, rev, n_pairs, mode, count, out_off,
-                                                                           out_i, out_j, out_sf, out_sr);
+        links_combine_kernel<false><<<grid_for(n_pairs, 128), 128, 0, st>>>(fwd, rev, n_pairs, mode, count, out_cap,
+                                                                           out_off, out_i, out_j, out_sf, out_sr);
     return cudaGetLastError();
 }
 

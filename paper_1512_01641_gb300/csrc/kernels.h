@@ -130,12 +130,14 @@ struct LinkView {
     const int64_t *off;
     const int32_t *i, *j;
     const float *s;
+    int64_t cap;  // entries of i, j, s
 };
 // Per pair: count (out_i == nullptr) or write the merged links of fwd and
-// rev (rev's link (i', j') is (j', i')); mode 0 union, 1 intersection.
+// rev (rev's link (i', j') is (j', i')); mode 0 union, 1 intersection;
+// out_cap: entries of the output arrays.
 cudaError_t launch_links_combine(LinkView fwd, LinkView rev, int64_t n_pairs, int mode, int32_t *count,
-                                 const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_sf,
-                                 float *out_sr, cudaStream_t st);
+                                 int64_t out_cap, const int64_t *out_off, int32_t *out_i, int32_t *out_j,
+                                 float *out_sf, float *out_sr, cudaStream_t st);
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,

@@ -1070,6 +1070,7 @@ int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const min
                        mine_bi_out *o, miner_stream_t stream) {
     if (!f || !r || !of || !orv || !o || (mode != MINE_BI_UNION && mode != MINE_BI_INTERSECT)) return MINE_EINVAL;
     if (f->n_pairs != r->n_pairs || !of->link_off || !orv->link_off || !o->link_off) return MINE_EINVAL;
+    if (of->link_capacity < 0 || orv->link_capacity < 0) return MINE_EINVAL;
     for (int64_t k = 0; k < f->n_pairs; ++k)
         if (f->geom_h[k].n != r->geom_h[k].m || f->geom_h[k].m != r->geom_h[k].n) return MINE_EINVAL;
     const int64_t need = f->link_cap + r->link_cap;
@@ -1081,11 +1082,12 @@ int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const min
     const int64_t n = f->n_pairs;
     PoolTemp<int32_t> cnt(st);
     MINE_CK(dalloc(&cnt.p, (size_t)n, f->device, st));
-    const LinkView F{of->link_off, of->link_i, of->link_j, of->link_s};
-    const LinkView R{orv->link_off, orv->link_i, orv->link_j, orv->link_s};
-    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, st));
+    const LinkView F{of->link_off, of->link_i, of->link_j, of->link_s, of->link_capacity};
+    const LinkView R{orv->link_off, orv->link_i, orv->link_j, orv->link_s, orv->link_capacity};
+    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, 0, nullptr, nullptr, nullptr, nullptr, nullptr, st));
     MINE_CK(launch_scan(cnt.p, n, o->link_off, st));
-    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, o->link_off, o->link_i, o->link_j, o->s_fwd, o->s_rev, st));
+    MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, o->link_capacity, o->link_off, o->link_i, o->link_j, o->s_fwd,
+                                 o->s_rev, st));
     return MINE_OK;
 }
 
