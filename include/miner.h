@@ -204,8 +204,11 @@ int mine_corpus_add_anchors(const mine_corpus *words, int32_t v_words, const int
 
 /* The dictionary with the identity entries of v_anchor anchors appended:
  * off_out v_src + v_anchor + 1 int32, tgt_out n_entries + v_anchor int32
- * (device, caller-allocated).  Asynchronous.  MINE_EINVAL for a NULL
- * argument or sizes beyond int32. */
+ * (device, caller-allocated).  SYNCHRONOUS on the stream (it checks the
+ * dictionary first, as mine_dict_transpose does).  MINE_EINVAL, with nothing
+ * written, for a NULL argument, sizes beyond int32, or offsets that do not
+ * start at 0, decrease or do not end at n_entries, or a target id outside
+ * [0, v_tgt). */
 int mine_dict_add_anchors(const mine_dict *dict, int32_t v_anchor, int32_t *off_out, int32_t *tgt_out,
                           miner_stream_t stream);
 
@@ -267,6 +270,11 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
                                      mean per warp is split over warps, one strip each,
                                      in a wavefront (1); 2 every pair of two or more
                                      strips is split.  Same results in every mode. */
+#define MINE_OPT_FAULT_SKIP_SOFT 11 /* fault injection for tests: the forward progress counter
+                                       with this index (strips of split pairs, in the soft work
+                                       list's order) is never published, so the strips that wait
+                                       on it give up after MINE_OPT_WAIT_LIMIT polls and
+                                       mine_plan_check reports MINE_ETIMEOUT (-1: off) */
 int mine_plan_set_option(mine_plan *plan, int option, int64_t value);
 /* Current value of an option, or MINE_EINVAL for an unknown option. */
 int64_t mine_plan_get_option(const mine_plan *plan, int option);
@@ -358,7 +366,11 @@ int softnw_bwd(mine_plan *plan, const mine_params *params, const softnw_opts *op
  * before any stream capture.  Every call uses the same array, so calls whose
  * kernels overlap on the GPU (other streams, other threads) race and corrupt
  * each other's results; serialise them.  Nothing needs to be zero beforehand:
- * each call overwrites every scratch word it reads. */
+ * each call overwrites every scratch word it reads.
+ * A device-side failure has no plan to report it through: if a bounded wait
+ * for the staged counts gives up, the kernel writes *n_links = -1 and
+ * *pair_score = NaN, and the links are then invalid (the call itself has
+ * already returned MINE_OK; read n_links before using the links). */
 #define MINE_NOALLOC_MAX_SIDE 2048
 int mine_align_pair_noalloc(const int64_t *src_sent_off, const int64_t *tgt_sent_off, int32_t n, int32_t m,
                             const uint8_t *counts, const mine_params *params, int32_t *link_i,

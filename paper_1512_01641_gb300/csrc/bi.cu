@@ -82,7 +82,7 @@ __global__ void links_combine_kernel(LinkView fwd, LinkView rev, int64_t n_pairs
             const int64_t rk = c < ce ? ((int64_t)rev.j[c] << 32) | (uint32_t)rev.i[c] : INT64_MAX;
             const bool in_f = fk <= rk, in_r = rk <= fk;
             if (mode == 0 || (in_f && in_r)) {
-                if (WRITE && o < out_cap) {
+                if (WRITE && o >= 0 && o < out_cap) {
                     const int64_t key = in_f ? fk : rk;
                     out_i[o] = (int32_t)(key >> 32);
                     out_j[o] = (int32_t)(key & 0xffffffff);

@@ -160,6 +160,7 @@ struct SoftArgs {
     int64_t wait_limit;  // bounded spins of a strip wait (split pairs)
     uint32_t *status;    // plan status word (timeout bit)
     int split;           // 0: one warp per pair, 1: split long pairs, 2: split every pair of >= 2 strips
+    int64_t skip_ctr;    // fault injection: this forward progress counter is never published (-1: off)
 };
 constexpr int kSoftChunk = 4096;  // cells per chunk of the per-cell kernels
 constexpr int kSoftSlots = 8;     // per chunk: loss sum, seven gradient sums
@@ -202,6 +203,10 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
                                  const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
                                  const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float dloss,
                                  float *grad, float *hvp, int n_sms, cudaStream_t st);
+
+// Records e as this thread's last CUDA error (what mine_last_cuda_error
+// returns) for entry points outside the plan's translation unit.
+void record_cuda_error(int e);
 
 // Kernel kinds of the per-kernel timing hook (order of MINE_KERNEL_KINDS).
 enum KernelKind { kKCount = 0, kKFill, kKWalk, kKLinks, kKScan, kKScore, kKSoftFwd, kKSoftBwd, kKinds };

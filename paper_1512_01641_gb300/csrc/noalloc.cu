@@ -38,7 +38,10 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
     __shared__ SimCol colv[32];
     __shared__ __align__(16) unsigned char stage[2][32][kStageBytes];
     __shared__ uint64_t stage_bar[2];
+    __shared__ uint32_t status;  // timeout bit of the staging waits
     const int lane = threadIdx.x;
+    if (lane == 0) status = 0u;
+    __syncwarp();
     const int nstrips = (N + 31) >> 5, nblk = (M + 31) >> 5;
     const int cap = min(N, M);
     uint64_t *tb = reinterpret_cast<uint64_t *>(scratch);
@@ -58,7 +61,7 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
         C.counts_bytes = 2 * (int64_t)N * M;
         C.stage = stage;
         C.stage_bar = stage_bar;
-        C.status = nullptr;
+        C.status = &status;
         fill_stage_init(C);
         C.N = N;
         C.M = M;
@@ -86,9 +89,15 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
     int kept;
     pair_sum_warp(diag_s + base, nd, P.thr, lane, sum, kept);
     copy_kept_warp(diag_i + base, diag_j + base, diag_s + base, nd, P.thr, lane, link_i, link_j, link_s);
+    __syncwarp();
     if (lane == 0) {
-        *n_links = kept;
-        *pair_score = (float)(sum - (double)P.gap * (double)(N + M - 2 * nd));
+        if (status != 0u) {  // a staging wait gave up: the results are invalid
+            *n_links = -1;
+            *pair_score = __int_as_float(0x7fc00000);
+        } else {
+            *n_links = kept;
+            *pair_score = (float)(sum - (double)P.gap * (double)(N + M - 2 * nd));
+        }
     }
 }
 
@@ -114,8 +123,6 @@ cudaError_t scratch_address(void **out) {
     return cudaSuccess;
 }
 
-thread_local int g_noalloc_last_cuda = 0;
-
 }  // namespace
 }  // namespace gbm
 
@@ -132,7 +139,7 @@ extern "C" int mine_align_pair_noalloc(const int64_t *src_sent_off, const int64_
     void *scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) {
-        g_noalloc_last_cuda = (int)e;
+        record_cuda_error((int)e);
         return MINE_ECUDA;
     }
     align_pair_static_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(src_sent_off, tgt_sent_off, n, m, counts,
@@ -140,7 +147,7 @@ extern "C" int mine_align_pair_noalloc(const int64_t *src_sent_off, const int64_
                                                                  link_i, link_j, link_s, n_links, pair_score);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
-        g_noalloc_last_cuda = (int)e;
+        record_cuda_error((int)e);
         return MINE_ECUDA;
     }
     return MINE_OK;

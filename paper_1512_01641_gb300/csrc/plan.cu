@@ -114,6 +114,8 @@ cudaError_t dalloc(T **p, size_t n, int device, cudaStream_t st) {
 
 }  // namespace
 
+void record_cuda_error(int e) { g_last_cuda = e; }
+
 cudaError_t launch_validate_corpus(const DevCorpus &c, int64_t n_sents, int64_t n_tok, int32_t vocab,
                                    uint32_t *status, int32_t *max_len, cudaStream_t st) {
     int64_t blocks = std::min<int64_t>((n_sents + 255) / 256, 4096);
@@ -144,6 +146,7 @@ struct PlanKnobs {
     int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
     int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
     int soft_split = 1;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs split over warps
+    int64_t skip_soft = -1;            // fault injection: soft progress counter never published (tests)
 };
 
 struct mine_plan {
@@ -454,6 +457,9 @@ static int knob_apply(PlanKnobs &k, int option, int64_t value, int *effect) {
         case MINE_OPT_SOFT_SPLIT:
             if (value < 0 || value > 2) return MINE_EINVAL;
             k.soft_split = (int)value;
+            return MINE_OK;
+        case MINE_OPT_FAULT_SKIP_SOFT:
+            k.skip_soft = value < 0 ? -1 : value;
             return MINE_OK;
         default:
             return MINE_EINVAL;
@@ -815,6 +821,7 @@ static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, con
     A.wait_limit = p->knobs.wait_limit;
     A.status = p->S.status;
     A.split = p->knobs.soft_split;
+    A.skip_ctr = p->knobs.skip_soft;
     int64_t cells = p->n_cells;
     order = p->pair_order;
     n = p->n_pairs;
@@ -947,6 +954,7 @@ int64_t mine_plan_get_option(const mine_plan *p, int option) {
         case MINE_OPT_FAULT_SKIP_FLAG: return p->knobs.skip_flag;
         case MINE_OPT_N_TILE_FLAGS: return p->n_flags;
         case MINE_OPT_SOFT_SPLIT: return p->knobs.soft_split;
+        case MINE_OPT_FAULT_SKIP_SOFT: return p->knobs.skip_soft;
         default: return MINE_EINVAL;
     }
 }
@@ -1061,8 +1069,20 @@ int mine_dict_add_anchors(const mine_dict *d, int32_t v_anchor, int32_t *off_out
         v_anchor <= 0 || (d->n_entries > 0 && !d->tgt) || (int64_t)d->v_src + v_anchor > INT32_MAX ||
         (int64_t)d->v_tgt + v_anchor > INT32_MAX || d->n_entries + v_anchor > INT32_MAX)
         return MINE_EINVAL;
-    MINE_CK(launch_anchor_dict(d->off, d->tgt, d->v_src, d->v_tgt, d->n_entries, v_anchor, off_out, tgt_out,
-                               (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    int device;
+    MINE_CK(cudaGetDevice(&device));
+    // the offsets are copied and shifted as they are: check the dictionary
+    // before anything is written
+    PoolTemp<uint32_t> status(st);
+    MINE_CK(dalloc(&status.p, 1, device, st));
+    MINE_CK(cudaMemsetAsync(status.p, 0, sizeof(uint32_t), st));
+    MINE_CK(launch_dict_check(d->off, d->v_src, d->n_entries, d->tgt, d->v_tgt, status.p, st));
+    uint32_t bad = 0;
+    MINE_CK(cudaMemcpyAsync(&bad, status.p, sizeof bad, cudaMemcpyDeviceToHost, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    if (bad) return MINE_EINVAL;
+    MINE_CK(launch_anchor_dict(d->off, d->tgt, d->v_src, d->v_tgt, d->n_entries, v_anchor, off_out, tgt_out, st));
     return MINE_OK;
 }
 

@@ -455,7 +455,8 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
             if (I.kind == 1) {
                 soft_fwd_strip<false, false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
                                              nullptr, sbuf, s + 1 == S ? vlast : nullptr,
-                                             s > 0 ? p1 + s - 1 : nullptr, p1 + s);
+                                             s > 0 ? p1 + s - 1 : nullptr,
+                                             (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
             } else {
                 soft_fwd_strip<false, true>(C, s, top(s), nullptr, nullptr, nullptr, sbuf, nullptr,
                                             s > 0 ? p1 + s - 1 : nullptr, nullptr);
@@ -509,7 +510,7 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
                 if (s + 1 < S)  // the last strip's checkpoint is not needed
                     soft_fwd_strip<true, false>(C, s, topv(s), topt(s), ckv + (int64_t)s * C.M,
                                                 ckt + (int64_t)s * C.M, sbuf, nullptr, s > 0 ? p1 + s - 1 : nullptr,
-                                                p1 + s);
+                                                (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
             } else {
                 soft_fwd_strip<true, true>(C, s, topv(s), topt(s), nullptr, nullptr, sbuf, nullptr,
                                            s > 0 ? p1 + s - 1 : nullptr, nullptr);

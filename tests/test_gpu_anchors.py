@@ -103,3 +103,30 @@ def test_add_anchors_rejects_malformed_anchor_lists(bad):
         db.src[1][3] = db.src[1][2] - 1
     with pytest.raises(miner.MinerError):
         miner.add_anchors(db, (torch.from_numpy(off).cuda(), torch.from_numpy(ids).cuda()), _dev_anchors(ta), V_ANCHOR)
+
+
+@pytest.mark.parametrize("bad", ["offsets_end", "offsets_decrease", "target_out_of_range"])
+def test_dict_add_anchors_rejects_malformed_dictionaries(bad):
+    # the dictionary is checked before its offsets are copied and shifted:
+    # a malformed one is rejected with nothing written to the outputs
+    import ctypes as C
+    import torch
+    from paper_1512_01641_gb300 import miner
+    b, _, _ = _batch_and_anchors(351, 4)
+    db = miner.DeviceBatch.from_batch(b)
+    off = db.dict_off.clone()
+    tgt = db.dict_tgt.clone()
+    if bad == "offsets_end":
+        off[-1] -= 1
+    elif bad == "offsets_decrease":
+        off[5] = off[4] - 1
+    else:
+        tgt[0] = db.v_tgt
+    d = miner._Dict(db.v_src, db.v_tgt, tgt.numel(), off.data_ptr(), tgt.data_ptr())
+    off_out = torch.full((db.v_src + V_ANCHOR + 1,), -5, dtype=torch.int32, device="cuda")
+    tgt_out = torch.full((tgt.numel() + V_ANCHOR,), -5, dtype=torch.int32, device="cuda")
+    rc = miner.lib().mine_dict_add_anchors(C.byref(d), V_ANCHOR, C.c_void_p(off_out.data_ptr()),
+                                           C.c_void_p(tgt_out.data_ptr()), None)
+    assert rc == miner.MINE_EINVAL
+    torch.cuda.synchronize()
+    assert bool((off_out == -5).all()) and bool((tgt_out == -5).all())

@@ -262,3 +262,64 @@ def test_soft_full_size_4096_pairs_sampled(gamma):
         Eg = exp[off[k]:off[k + 1]].cpu().numpy().reshape(E.shape)
         assert np.abs(Eg - E).max() <= etol, (k, np.abs(Eg - E).max())
     plan.close()
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.1])
+def test_multi_strip_backward_vs_oracle(gamma):
+    """The strip-recompute backward on pairs of two to four 32-row strips
+    (ragged last strips and ragged column blocks): the 7 gradients and H u of
+    every cell against the FP64 oracle's double backward, with the strips on
+    one warp (split mode 0) and every strip on its own warp (split mode 2)."""
+    pytest.importorskip("torch")
+    import torch
+    from oracle import softgrad
+    from paper_1512_01641_gb300 import miner
+    ns, ms = [40, 70, 97], [45, 33, 64]
+    batch = synth.make_batch(310, 3, v_src=500, v_tgt=500, planted_frac=0.0, src_sizes=ns, tgt_sizes=ms)
+    # planted-like gold on the diagonal band, so the loss has both kinds of cells
+    batch.gold = [np.array([(i, int(i * m / n)) for i in range(n)], np.int32) for n, m in zip(ns, ms)]
+    plan = miner.Plan(miner.DeviceBatch.from_batch(batch))
+    counts = plan.count()
+    gold = torch.from_numpy(miner.gold_cells(batch, plan)).cuda()
+    _, pairs = _oracle_pairs(batch)
+    L, grad = softgrad.loss_and_grad(pairs, THETA, gamma, TAU)
+    n_cells = plan.n_cells
+    hu_o = [softgrad.hvp_cells(*pr, THETA, gamma, TAU, n_cells)[2] for pr in pairs]
+    off = plan.cell_offsets
+    for split in (0, 2):
+        loss, _, _, g, hu = _soft_all(plan, counts, gold, gamma, split)
+        assert float(loss[0]) == pytest.approx(L, rel=1e-4), split
+        g = g.astype(np.float64)
+        assert np.abs(g - grad).max() <= 1e-3 * np.abs(grad).max(), (split, g, grad)
+        for k, h in enumerate(hu_o):
+            got = hu[off[k]:off[k + 1]].reshape(h.shape)
+            assert np.abs(got - h).max() <= 1e-4 * np.abs(h).max(), (split, k, np.abs(got - h).max())
+    plan.close()
+
+
+def test_soft_split_wait_reports_timeout_and_recovers():
+    """A strip's forward progress counter that nothing publishes (fault
+    injection) in a pair split over warps: the strips that wait on it give up
+    after a short bounded poll, mine_plan_check reports MINE_ETIMEOUT, the
+    context stays usable, and the next normal call is correct."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    batch = _batch(311, 1, 100, v=500)
+    plan = miner.Plan(miner.DeviceBatch.from_batch(batch))
+    counts = plan.count()
+    gold = torch.from_numpy(miner.gold_cells(batch, plan)).cuda()
+    ref = _soft_all(plan, counts, gold, 0.1, 2)
+    plan.set_option("wait_limit", 2000)
+    plan.set_option("fault_skip_soft", 0)
+    al = miner.SoftAligner(plan, counts, gold, 0.1, TAU)
+    al.forward(miner.params_from_theta(THETA))
+    with pytest.raises(miner.MinerError) as e:
+        plan.check()
+    assert e.value.code == miner.MINE_ETIMEOUT
+    plan.set_option("fault_skip_soft", -1)
+    plan.set_option("wait_limit", 1 << 24)
+    got = _soft_all(plan, counts, gold, 0.1, 2)
+    for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
+        assert np.array_equal(a, b), name
+    assert plan.get_option("fault_skip_soft") == -1
+    plan.close()

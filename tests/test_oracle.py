@@ -344,6 +344,26 @@ def test_soft_loss_gradient_central_differences(gamma):
         assert g[k] == pytest.approx(fd, rel=1e-4, abs=1e-7), k
 
 
+def test_soft_loss_hand_worked():
+    """The oracle's loss (gate, clamp, BCE mean over cells) against a 1x1 and a
+    1x2 pair worked out in closed form by path enumeration
+    (tests/golden/soft_loss_hand.py holds the derivation); the oracle's soft
+    value and expected alignment of the same similarities too."""
+    pytest.importorskip("torch")
+    from oracle import softgrad
+    d = _load("soft_loss_hand.json")
+    pairs = [(np.array(p["ms"]), np.array(p["mt"]), p["ls"], p["lt"], np.array(p["gold"], float)) for p in d["pairs"]]
+    L = softgrad.loss_value(pairs, d["theta"], d["gamma"], d["tau"], d["eps"])
+    assert L == pytest.approx(d["loss"], rel=1e-10)
+    assert L != pytest.approx(d["loss"] * 3 / 2, rel=1e-3)  # a mean over pairs would differ
+    for p in d["pairs"]:
+        V, E, _ = oracle.soft_nw(np.array(p["s"]), d["theta"][5], d["gamma"])
+        assert V[-1, -1] == pytest.approx(p["V"], rel=1e-12)
+        assert np.allclose(E, np.array(p["E"]), rtol=1e-10, atol=1e-15)
+    # the clamp acts on the second pair's unmatched cell
+    assert d["pairs"][1]["P"][0][1] == d["eps"]
+
+
 # --- the tuning objective (Section 5.2): similarity of automatic and human alignments ---
 
 def _lcs_brute(a, b):
