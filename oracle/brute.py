@@ -73,3 +73,11 @@ def soft(s, p, gamma):
         for j in range(M):
             E[i][j] /= Z
     return mx + gamma * math.log(Z), E
+
+
+def unconstrained_choices(N: int, M: int):
+    """Every row-by-row choice of the unconstrained aligner's move set: each
+    source row unmatched (None) or matched to any target column, in any
+    order -- (M + 1) ** N of them."""
+    import itertools
+    return itertools.product([None] + list(range(M)), repeat=N)

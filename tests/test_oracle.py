@@ -523,3 +523,92 @@ def test_planted_anchors_follow_the_gold_links():
         for i, j in g.tolist():
             assert (ta.ids[ta.sent_off[t0 + j]:ta.sent_off[t0 + j + 1]].tolist() ==
                     sa.ids[sa.sent_off[s0 + i]:sa.sent_off[s0 + i + 1]].tolist())
+
+
+# --- the unconstrained (Yalign A*) aligner of Section 5.1, Figures 3 and 5 ---
+
+def _score_choice(s, p, choice):
+    """Score of a row-by-row choice, written out for the brute force: a match
+    ahead of the pointer skips the columns between (p each), a match at or
+    behind it is a move back (p), an unmatched row costs p, and so does every
+    target sentence after the final pointer."""
+    N, M = s.shape
+    ptr, tot = 0, 0.0
+    for i in range(N):
+        j = choice[i]
+        if j is None:
+            tot -= p
+        elif j + 1 > ptr:
+            tot += s[i, j] - p * (j - ptr)
+            ptr = j + 1
+        else:
+            tot += s[i, j] - p
+            ptr = j + 1
+    return tot - p * (M - ptr)
+
+
+@pytest.mark.parametrize("name", ["fig3_unconstrained.json", "fig5_unconstrained.json"])
+def test_unconstrained_figures(name):
+    from oracle import unconstrained
+    g = _load(name)
+    s = _identity_sim(g["rows"], g["cols"])
+    score, links = unconstrained.align(s, g["gap"])
+    assert score == g["score"]
+    assert [list(x) for x in links] == g["links"]
+    if "alignment_cols" in g:  # the alignment printed under Figure 3
+        last = links[-1][1]
+        cols = [g["cols"][j] for _, j in links] + g["cols"][last + 1:]
+        rows = [g["rows"][i] for i, _ in links] + ["-"] * (len(g["cols"]) - last - 1)
+        assert cols == g["alignment_cols"] and rows == g["alignment_rows"]
+    if "marked_matches" in g:
+        assert set(map(tuple, g["marked_matches"])) <= set(links)
+        H, _, _ = oracle.nw(s, g["gap"])
+        assert H[-1, -1] == g["nw_score"] < score
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_unconstrained_brute_force(seed):
+    """The DP's optimum and path against every row-by-row choice (brute force)."""
+    from oracle import unconstrained
+    rng = np.random.default_rng(600 + seed)
+    N, M = int(rng.integers(1, 5)), int(rng.integers(1, 5))
+    s = rng.random((N, M))
+    p = float(rng.choice([0.05, 0.2, 0.4, 0.8]))
+    scores = [_score_choice(s, p, ch) for ch in brute.unconstrained_choices(N, M)]
+    best = max(scores)
+    score, links = unconstrained.align(s, p)
+    assert score == pytest.approx(best, abs=1e-12)
+    choice = [None] * N
+    for i, j in links:
+        choice[i] = j
+    assert _score_choice(s, p, choice) == pytest.approx(best, abs=1e-12)
+    assert unconstrained.path_score(s, p, choice) == pytest.approx(best, abs=1e-12)
+
+
+def test_unconstrained_without_the_move_back_is_nw():
+    """Forbidding the move back leaves exactly Needleman-Wunsch: same optimum
+    as the oracle's NW fill, and never better than the unconstrained one."""
+    from oracle import unconstrained
+    rng = np.random.default_rng(610)
+    for _ in range(20):
+        N, M = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+        s = rng.random((N, M))
+        p = float(rng.choice([0.05, 0.3, 0.7]))
+        H, _, diag = oracle.nw(s, p)
+        score_nw, links = unconstrained.align(s, p, back=False)
+        assert score_nw == pytest.approx(H[-1, -1], abs=1e-12)
+        assert all(j2 > j1 for (_, j1), (_, j2) in zip(links, links[1:]))
+        assert unconstrained.align(s, p)[0] >= score_nw - 1e-12
+
+
+def test_unconstrained_single_column_closed_form():
+    """M = 1: every row takes the column (matching again is a move back at
+    cost p, never worse than leaving the row unmatched), so the optimum is
+    s_0 + sum_{i>0} (s_i - p)."""
+    from oracle import unconstrained
+    rng = np.random.default_rng(611)
+    s = rng.random((7, 1))
+    p = 0.3
+    score, links = unconstrained.align(s, p)
+    assert score == pytest.approx(s[0, 0] + sum(s[i, 0] - p for i in range(1, 7)), abs=1e-12)
+    assert links == [(i, 0) for i in range(7)]
