@@ -35,8 +35,11 @@ from paper_1512_01641_gb300 import synth  # noqa: E402
 
 METRIC = "DP cell-updates/s (batched hard-NW mining)"
 UNIT = "cell-updates/s"
-N_SMS = 152
-LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes issue per clock
+LANES_PER_SM = 128  # issue model: 4 sub-partitions x one 32-lane warp instruction per clock
+PEAKS = os.path.join(HERE, "MEASURED_PEAKS.json")
+TUNE_DICT_DROP = 0.3   # share of dictionary entries the miner does not know (tuning and BI records)
+TUNE_THETA0 = [4.0, 4.0, -2.0, 1.0, -6.0, 0.8, 0.8]  # poor start: b, gap, thr at the grid's far corner
+HBM_FALLBACK_GBS = 6800.0  # one earlier GB300 copy measurement, used only without MEASURED_PEAKS.json
 # algorithmic lane-operations per cell of the roofline model when the path is
 # timed from precomputed counts (similarity and DP only)
 OPS_SIM = 11   # 4 quotients, 4 multiply-adds, exp, add, reciprocal
@@ -86,7 +89,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-bi", action="store_true", help="skip the bi-directional mining record")
     ap.add_argument("--no-anchors", action="store_true", help="skip the anchor-token record")
+    ap.add_argument("--bi-pairs", type=int, default=10_000)
     ap.add_argument("--anchor-pairs", type=int, default=10_000)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-pair, 10,000-pair, NW-only and soft-NW records")
     ap.add_argument("--soft-step", action="store_true",
                     help="only time one soft-NW forward+backward on a 4,096-pair tuning minibatch (profiling)")
     return ap.parse_args()
@@ -127,6 +133,181 @@ def merge_compare_ops(batch):
         (np.diff(batch.tgt.doc_sent_off) > 0)
     M = np.diff(batch.tgt.doc_sent_off)
     return int((tr_doc * M + tl_doc * n_src).sum())
+
+
+def sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def algorithmic_bytes(batch, n_links):
+    """Bytes the method itself must move per step: the inputs once (corpora
+    CSR and dictionary), the 2-bit traceback mask of every cell written once,
+    the outputs once (12 bytes per link, a score and a link offset per pair).
+    The count buffer between the count and fill kernels is a design choice,
+    not counted."""
+    src, tgt, dic = batch.src, batch.tgt, batch.dic
+    inp = sum(a.nbytes for a in (src.doc_sent_off, src.sent_tok_off, src.tok, tgt.doc_sent_off,
+                                 tgt.sent_tok_off, tgt.tok, dic.off, dic.tgt))
+    cells = batch.cells()
+    return inp + cells // 4 + 12 * n_links + 12 * batch.n_pairs
+
+
+def timed_steps(fn, steps, warmup):
+    """CUDA-event time (s) of `steps` calls of fn after `warmup` calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1000.0
+
+
+def oracle_rate(batch, n_pairs=None, seed=0):
+    """The FP64 oracle's cell-updates/s on (a sample of) a batch, all host cores."""
+    import oracle
+    pick = np.arange(batch.n_pairs)
+    if n_pairs is not None and n_pairs < batch.n_pairs:
+        pick = np.sort(np.random.default_rng(seed).choice(batch.n_pairs, n_pairs, replace=False))
+    sub = batch.subset(pick)
+    t0 = time.perf_counter()
+    r = oracle.mine(sub, [4, 4, -2, 1], -3.0, 0.3, 0.5, n_threads=os.cpu_count() or 1)
+    dt = time.perf_counter() - t0
+    return {"value": sub.cells() / dt, "unit": UNIT, "cores": int(r["threads"]), "kind": "oracle",
+            "sample": f"{len(pick)} pairs, {sub.cells()} cells, {dt:.2f} s"}
+
+
+def config_records(args, params):
+    """The other configurations of the benchmark spec, each with the oracle beside it:
+    one 40 x 45 pair (latency of one call), 10,000 Wikipedia-shaped pairs
+    (throughput), the NW-only rate of the bench batch's counts, and the soft
+    alignment of 4,096 planted pairs at three temperatures."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    rec = {}
+    # single pair, 40 x 45: the latency of one mine_pairs call (graph replay)
+    b1 = synth.single_pair()
+    with miner.Plan(miner.DeviceBatch.from_batch(b1)) as plan:
+        out = plan.mine(params)
+        for _ in range(10):
+            plan.mine(params, out)
+        torch.cuda.synchronize()
+        lat = []
+        for _ in range(200):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.mine(params, out)
+            b.record()
+            torch.cuda.synchronize()
+            lat.append(a.elapsed_time(b))
+        host = []
+        for _ in range(50):
+            t0 = time.perf_counter()
+            plan.mine(params, out)
+            n = int(out["link_off"][-1].item())
+            out["link_i"][:n].cpu()
+            host.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    import oracle
+    for _ in range(20):
+        oracle.mine(b1, [4, 4, -2, 1], -3.0, 0.3, 0.5, n_threads=1)
+    o1 = (time.perf_counter() - t0) / 20
+    rec["single_pair_40x45"] = {"device_ms_median": float(np.median(lat)), "device_ms_p99": float(np.percentile(lat, 99)),
+                                "call_and_readback_ms_median": 1000 * float(np.median(host)),
+                                "cells": b1.cells(), "oracle_ms_one_core": 1000 * o1,
+                                "timing": "CUDA events around each of 200 mine_pairs calls (graph replay)"}
+    # 10,000 Wikipedia-shaped pairs
+    b2 = synth.wiki_batch()
+    with miner.Plan(miner.DeviceBatch.from_batch(b2)) as plan:
+        out = plan.new_output()
+        secs = timed_steps(lambda: plan.mine(params, out), args.steps, args.warmup)
+        rec["wiki_10000"] = {"value": plan.n_cells * args.steps / secs, "unit": UNIT,
+                             "pairs_per_s": plan.n_pairs * args.steps / secs, "ms_per_step": 1000 * secs / args.steps,
+                             "cells": plan.n_cells, "oracle": oracle_rate(b2, 2000)}
+    # the unconstrained (Yalign A*) aligner against Needleman-Wunsch on the
+    # same 10,000 pairs: links, micro precision / recall against the planted
+    # gold links, target sentences aligned more than once, and time
+    with miner.Plan(miner.DeviceBatch.from_batch(b2)) as plan:
+        counts = plan.count()
+        gold = torch.from_numpy(miner.gold_cells(b2, plan)).cuda()
+        res = {}
+        for name in ("nw", "unconstrained"):
+            run = (lambda: plan.align(params, counts)) if name == "nw" else \
+                (lambda: plan.align_unconstrained(params, counts))
+            o = run()
+            secs = timed_steps(run, 3, 1)
+            tp, nl, ng = (int(x) for x in plan.link_gold_counts(o, gold).cpu().tolist())
+            links = miner.links_per_pair(o, b2.n_pairs)
+            rep = sum(len(l) - len({j for _, j, _ in l}) for l in links)
+            prec, rec_ = tp / max(nl, 1), tp / max(ng, 1)
+            res[name] = {"links": nl, "correct": tp, "gold": ng, "precision": prec, "recall": rec_,
+                         "f1": 2 * prec * rec_ / max(prec + rec_, 1e-12), "repeated_targets": rep,
+                         "ms": 1000 * secs / 3}
+        rec["unconstrained_vs_nw"] = {"pairs": b2.n_pairs, **res,
+                                      "note": "same counts and classifier; the unconstrained aligner may move back "
+                                              "into the target sequence (one gap penalty), so a target sentence "
+                                              "can be aligned twice"}
+    # soft alignment of 4,096 planted pairs of ~100 x 100 sentences
+    b4 = synth.soft_batch()
+    with miner.Plan(miner.DeviceBatch.from_batch(b4)) as plan:
+        counts = plan.count()
+        gold = torch.from_numpy(miner.gold_cells(b4, plan)).cuda()
+        p = miner.params_from_theta([4.0, 4.0, -2.0, 1.0, -3.0, 0.3, 0.5])
+        soft = {}
+        for g in (1.0, 0.1, 0.01):
+            al = miner.SoftAligner(plan, counts, gold, g, 0.05)
+            tf = timed_steps(lambda: al.forward(p), args.steps, max(args.warmup, 2))
+            tb = timed_steps(lambda: al.backward(p), args.steps, max(args.warmup, 2))
+            soft[str(g)] = {"forward_ms": 1000 * tf / args.steps, "backward_ms": 1000 * tb / args.steps,
+                            "cells_per_s_fwd_bwd": plan.n_cells * args.steps / (tf + tb)}
+        plan.check()
+        rec["soft_4096"] = {"pairs": plan.n_pairs, "cells": plan.n_cells, "tau": 0.05, "gamma": soft}
+    return rec
+
+
+def near_tie_record(batch, out_all, pick, ref, p_gap):
+    """GPU paths (threshold off) against the oracle's (ref: oracle.mine of the
+    pairs `pick`, the CPU sample) : identical diagonal sets, or a near tie (the
+    GPU path re-scored in FP64 by the oracle within 1e-4 of the optimum), or a
+    violation."""
+    import oracle
+    from paper_1512_01641_gb300 import miner
+    links = miner.links_per_pair(out_all, batch.n_pairs)
+    score = out_all["pair_score"].cpu().numpy()
+    sub = batch.subset(pick)
+    diff = []
+    max_rel = 0.0
+    for x, k in enumerate(pick):
+        h = ref["score"][x]
+        max_rel = max(max_rel, abs(float(score[k]) - h) / max(1.0, abs(h)))
+        if [(i, j) for i, j, _ in links[k]] != [(i, j) for i, j, _ in ref["diag"][x]]:
+            diff.append(x)
+    ties = viol = 0
+    if diff:
+        rs = oracle.mine(sub.subset(diff), [4, 4, -2, 1], -3.0, p_gap, -1.0, want_sim=True)
+        for y, x in enumerate(diff):
+            got = oracle.path_score(rs["sim"][y], p_gap, [(i, j) for i, j, _ in links[pick[x]]])
+            if got >= rs["score"][y] - 1e-4:
+                ties += 1
+            else:
+                viol += 1
+    return {"pairs_compared": len(pick), "paths_identical": len(pick) - len(diff), "near_ties": ties,
+            "violations": viol, "max_pair_score_rel_err": max_rel,
+            "rule": "GPU path (threshold off) vs oracle path; a differing path counts as a near tie when its FP64 "
+                    "score is within 1e-4 of the optimum, else as a violation"}
 
 
 class Clocks:
@@ -186,7 +367,7 @@ def cpu_baseline(batch, n_pairs, seed=0):
     dt = time.perf_counter() - t0
     return {"value": cells / dt, "unit": UNIT, "cores": int(r["threads"]), "kind": "oracle",
             "sample": f"{len(pick)} random pairs of the workload (long pairs excluded), {cells} cells, "
-                      f"{dt:.1f} s", "seconds": dt, "cells": cells}
+                      f"{dt:.1f} s", "seconds": dt, "cells": cells}, pick, r
 
 
 def run_reference(args):
@@ -252,25 +433,46 @@ def run_tune(args):
     """Soft-NW gradient tuning (Adam) vs the 7^3 grid search and the paper's
     random search (343 draws), same GPU, evaluated by hard-NW micro-F1 on
     held-out planted pairs."""
+    import dataclasses
     from paper_1512_01641_gb300 import tune
     rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
     dic = synth.make_dictionary(rng, 50_000, 50_000)
     tr = synth.tune_batch(args.tune_pairs, seed=synth.SEED_BASE + 4, dic=dic)
     ev = synth.tune_batch(args.tune_eval, seed=synth.SEED_BASE + 5, dic=dic)
-    r = tune.compare(tr, ev, steps=args.tune_steps)
+    # the planted data come from the full dictionary; the miner knows 70 % of
+    # its entries, and every tuner starts from a poor setting
+    thin = synth.thin_dictionary(dic, TUNE_DICT_DROP, synth.SEED_BASE + 41)
+    tr, ev = dataclasses.replace(tr, dic=thin), dataclasses.replace(ev, dic=thin)
+    r = tune.compare(tr, ev, steps=args.tune_steps, theta0=TUNE_THETA0)
     r["train_cells"] = tr.cells()
+    r["mining_dictionary"] = f"{100 * (1 - TUNE_DICT_DROP):.0f} % of the planting dictionary's entries"
     return r
 
 
-def run_bi(args, db, plan, params, options):
-    """Bi-directional mining (Section 5.4, BI) of the same batch: the reverse
-    direction by a plan over the reversed batch (dictionary transposed on the
-    GPU), mined with the mirrored classifier (the two overlap weights
-    exchanged), then the per-pair union of the links.  Device-timed like the
-    main line: K steps of forward mining + reverse mining + combination."""
+def run_bi(args, params, options):
+    """Bi-directional mining (Section 5.4, BI) of 10,000 Wikipedia-shaped pairs
+    (half planted): each direction has its own incomplete dictionary -- the
+    forward one and the transpose of the planting dictionary, each missing an
+    independent 30 % of its entries, as two separately trained phrase tables
+    would -- and the reverse direction the mirrored classifier (the two
+    overlap weights exchanged).  Links of each direction, their union and
+    intersection against the gold links; device-timed steps of forward mining
+    + reverse mining + union."""
+    import dataclasses
     import torch
     from paper_1512_01641_gb300 import miner
-    rev = miner.Plan(db.reversed(), options=options)
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 50))
+    dic = synth.make_dictionary(rng, 50_000, 50_000)
+    b = synth.make_batch(synth.SEED_BASE + 51, args.bi_pairs, dic=dic)
+    fwd_dic = synth.thin_dictionary(dic, TUNE_DICT_DROP, synth.SEED_BASE + 52)
+    t_off, t_tgt = miner.dict_transpose(torch.from_numpy(dic.off).cuda(), torch.from_numpy(dic.tgt).cuda(),
+                                        dic.v_src, dic.v_tgt)
+    rev_full = synth.Dictionary(dic.v_tgt, dic.v_src, t_off.cpu().numpy(), t_tgt.cpu().numpy())
+    rev_dic = synth.thin_dictionary(rev_full, TUNE_DICT_DROP, synth.SEED_BASE + 53)
+    db = miner.DeviceBatch.from_batch(dataclasses.replace(b, dic=fwd_dic))
+    plan = miner.Plan(db, options=options)
+    rev = miner.Plan(db.reversed(torch.from_numpy(rev_dic.off).cuda(), torch.from_numpy(rev_dic.tgt).cuda()),
+                     options=options)
     w = params.w
     prev = miner.MineParams(w=(w[1], w[0], w[2], w[3]), b=params.b, gap=params.gap, thr=params.thr)
     of, orv = plan.new_output(), rev.new_output()
@@ -290,12 +492,29 @@ def run_bi(args, db, plan, params, options):
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1000.0 / args.steps
     x = miner.combine_links(plan, of, rev, orv, "intersect")
+    gold = [set(map(tuple, g.tolist())) for g in b.gold]
+
+    def quality(links):
+        tp = sum(len(l & g) for l, g in zip(links, gold))
+        nl, ng = sum(len(l) for l in links), sum(len(g) for g in gold)
+        p_, r_ = tp / max(nl, 1), tp / max(ng, 1)
+        return {"links": nl, "correct": tp, "precision": p_, "recall": r_,
+                "f1": 2 * p_ * r_ / max(p_ + r_, 1e-12)}
+
+    def pair_sets(o, swap=False):
+        off = o["link_off"].cpu().numpy()
+        li, lj = o["link_i"].cpu().numpy(), o["link_j"].cpu().numpy()
+        return [set(zip(lj[off[k]:off[k + 1]].tolist(), li[off[k]:off[k + 1]].tolist())) if swap else
+                set(zip(li[off[k]:off[k + 1]].tolist(), lj[off[k]:off[k + 1]].tolist())) for k in range(b.n_pairs)]
     rec = {"metric": "DP cell-updates/s (bi-directional mining: both directions + union)",
-           "value": 2 * plan.n_cells / secs, "ms_per_step": secs * 1e3,
-           "links_fwd": int(of["link_off"][-1]), "links_rev": int(orv["link_off"][-1]),
-           "links_union": int(u["link_off"][-1]), "links_intersect": int(x["link_off"][-1]),
-           "reverse_classifier": "mirrored (w1, w0, w2, w3), same b, gap, thr; transposed dictionary"}
+           "value": 2 * plan.n_cells / secs, "ms_per_step": secs * 1e3, "pairs": b.n_pairs,
+           "forward": quality(pair_sets(of)), "reverse": quality(pair_sets(orv, swap=True)),
+           "union": quality(pair_sets(u)), "intersection": quality(pair_sets(x)),
+           "dictionaries": f"forward and reverse each keep an independent {100 * (1 - TUNE_DICT_DROP):.0f} % of "
+                           "the planting dictionary's entries",
+           "reverse_classifier": "mirrored (w1, w0, w2, w3), same b, gap, thr"}
     rev.close()
+    plan.close()
     return rec
 
 
@@ -474,11 +693,29 @@ def main():
         ops = (OPS_SIM + OPS_DP) * n_cells
     achieved = ops / (dom_ms / 1000.0) / 1e12
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = N_SMS * LANES_PER_SM * sm_max * 1e6 / 1e12
+    n_sms = sm_count()
+    peak = n_sms * LANES_PER_SM * sm_max * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": traffic_per_launch(dom, n_cells),
                 "ops_per_launch": ops, "ms_per_launch": dom_ms,
-                "peak_basis": f"{N_SMS} SMs x {LANES_PER_SM} lane-ops/clk x {sm_max:.0f} MHz (max SM clock)"}
+                "peak_basis": f"model, not a measurement: {n_sms} SMs (read from the device) x {LANES_PER_SM} "
+                              f"lane-ops/clk (one warp instruction per sub-partition per clock) x {sm_max:.0f} MHz"}
+    n_links = int(out["link_off"][-1].item())
+    hbm_gbs, hbm_src = hbm_peak()
+    alg = algorithmic_bytes(batch, n_links)
+    hbm = {"algorithmic_bytes_per_step": alg, "achieved_gbs": alg / (secs / args.steps) / 1e9, "peak_gbs": hbm_gbs,
+           "peak_source": hbm_src, "frac": alg / (secs / args.steps) / 1e9 / hbm_gbs,
+           "count_kernel_dram_bytes_per_launch": traffic_per_launch("count", n_cells)}
+
+    # NW only: fill, walk, link scoring and compaction from the batch's cached counts
+    nw_only = None
+    if not args.no_configs:
+        counts = plan.count()
+        out_nw = plan.new_output()
+        t_nw = timed_steps(lambda: plan.align(params, counts, out_nw), args.steps, 1)
+        nw_only = {"value": n_cells * args.steps / t_nw, "unit": UNIT, "ms_per_step": 1000 * t_nw / args.steps,
+                   "what": "mine_align from cached counts (fill, traceback, link scoring, compaction)"}
+        del counts, out_nw
 
     anchors_rec = None
     if rank == 0 and not args.no_anchors:
@@ -486,7 +723,7 @@ def main():
 
     bi_rec = None
     if not args.no_bi:
-        bi_rec = run_bi(args, db, plan, params, dict(tuned["best"]) if tuned else {})
+        bi_rec = run_bi(args, params, dict(tuned["best"]) if tuned else {})
 
     e2e = None
     if not args.no_e2e:
@@ -504,9 +741,16 @@ def main():
                               "includes": "one batch at a time, nothing overlapped"}}
         plan = plan_keep
 
-    cpu = None
+    cpu = ties = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(batch, args.cpu_pairs)
+        cpu, pick, ref = cpu_baseline(batch, args.cpu_pairs)
+        out_all = plan.mine(miner.MineParams(thr=-1.0))
+        ties = near_tie_record(batch, out_all, pick, ref, params.gap)
+        del out_all
+
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = config_records(args, params)
 
     tune_rec = None
     if rank == 0 and not args.no_tune:
@@ -525,7 +769,8 @@ def main():
                 "direct_launch_ms_per_step": 1000 * secs_direct / args.steps,
                 "graph": {"captures": plan.get_option("graph_captures")},
                 "autotune": tuned, "tune": tune_rec, "bi": bi_rec, "anchors": anchors_rec,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+                "roofline": roofline, "hbm": hbm, "nw_only": nw_only, "near_ties": ties, "configs": configs,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "sm_count": sm_count()}
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -342,6 +342,33 @@ int softnw_fwd(mine_plan *plan, const mine_params *params, const softnw_opts *op
 int softnw_bwd(mine_plan *plan, const mine_params *params, const softnw_opts *opts, const uint8_t *counts,
                const uint8_t *gold, void *ws, float dloss, float *grad, float *hvp, miner_stream_t stream);
 
+/* ---- Unconstrained alignment: the A* aligner of Yalign, the baseline that
+ * Section 5.1 contrasts with Needleman-Wunsch (Figures 3 and 5 against 4 and
+ * 6): with NW's similarities and gap penalty A* finds NW's alignment only if
+ * its path may not go back up or left in the S matrix, and Yalign's may, so
+ * a sentence can be aligned twice.  The paper gives no cost model for the
+ * move back; reading used: source sentences are taken in order, each is
+ * unmatched (-gap), matched ahead of the target pointer (the NW diagonal,
+ * -gap for every target sentence skipped), or matched at or behind it (a
+ * move back into the target sequence, -gap); target sentences after the
+ * final pointer cost gap each.  Without the move back this is exactly NW.
+ * Ties prefer unmatched, then ahead, then back; the nearest predecessor.
+ * Scores in FP64 on the GPU (a comparison baseline, not the mining path). */
+
+/* Bytes of the caller-provided workspace of mine_align_unconstrained. */
+int64_t mine_unconstrained_workspace_size(const mine_plan *plan);
+/* Links the output must hold: the sum over pairs of N_k (one per source
+ * sentence at most; target sentences may repeat). */
+int64_t mine_unconstrained_link_capacity(const mine_plan *plan);
+/* Unconstrained alignment of every pair from counts (as mine_count) and the
+ * classifier of params: out receives per pair the matched cells with s >= thr
+ * in source order (target indices need not increase) and the score in
+ * pair_score.  ws: mine_unconstrained_workspace_size bytes of device memory.
+ * Asynchronous.  MINE_EINVAL for a NULL argument or an output of less than
+ * mine_unconstrained_link_capacity links. */
+int mine_align_unconstrained(mine_plan *plan, const mine_params *params, const uint8_t *counts, void *ws,
+                             mine_out *out, miner_stream_t stream);
+
 /* Allocation-free alignment of ONE document pair (the paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory when they call -- a serving loop with a fixed memory budget,

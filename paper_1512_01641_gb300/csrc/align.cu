@@ -49,8 +49,8 @@ __device__ bool wait_flag(const int32_t *f, int64_t limit) {
 __global__ void __launch_bounds__(32 * kFillWarps, 3)
 fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             const FillItem *__restrict__ items, int64_t n_items, DevParams P,
-            const uint8_t *__restrict__ counts, int64_t counts_bytes, AlignScratch S, int64_t wait_limit,
-            int64_t skip_flag) {
+            const uint8_t *__restrict__ counts, int64_t counts_bytes, bool blocked, AlignScratch S,
+            int64_t wait_limit, int64_t skip_flag) {
     __shared__ SimCol colv_all[kFillWarps][32];
     __shared__ __align__(16) unsigned char stage_all[kFillWarps][2][32][kStageBytes];
     __shared__ uint64_t bar_all[kFillWarps][2];
@@ -66,6 +66,7 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
     C.stage = stage_all[warp];
     C.stage_bar = bar_all[warp];
     C.status = S.status;
+    C.blocked = blocked;
     fill_stage_init(C);
     for (;;) {
         int64_t it = 0;
@@ -89,7 +90,7 @@ fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             // before the wait for them
             FillAhead ah;
             int nb;
-            fill_strip_prepare(C, s, src.sent + sbase, g.cell_off, ah, nb);
+            fill_strip_prepare(C, s, src.sent + sbase, g.cell_off, ah, nb, g.tb_off);
             if (tiled) {
                 if (lane == 0) {
                     bool ok = true;
@@ -228,7 +229,7 @@ __device__ __forceinline__ int64_t owner_pair(const int64_t *__restrict__ diag_o
 
 __global__ void __launch_bounds__(32 * kTailWarps)
 link_score_cached_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, int64_t n_pairs,
-                         DevParams P, AlignScratch S, const uint8_t *__restrict__ counts) {
+                         DevParams P, AlignScratch S, const uint8_t *__restrict__ counts, bool blocked) {
     const int64_t total = S.diag_off[n_pairs];
     const SimConst K = sim_const(P);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -239,7 +240,10 @@ link_score_cached_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restric
         const int rr = S.diag_i[at], cc = S.diag_j[at];
         const int64_t sb = src.doc[k] + rr, tbs = tgt.doc[k] + cc;
         const int ls = (int)(src.sent[sb + 1] - src.sent[sb]), lt = (int)(tgt.sent[tbs + 1] - tgt.sent[tbs]);
-        const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)rr * g.m + cc];
+        const int64_t cell = blocked ? 32 * g.tb_off + 1024 * ((int64_t)(rr >> 5) * ((g.m + 31) >> 5) + (cc >> 5)) +
+                                           32 * (rr & 31) + (cc & 31)
+                                     : g.cell_off + (int64_t)rr * g.m + cc;
+        const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[cell];
         S.diag_s[at] = similarity(q.x, q.y, sim_row(ls, P), sim_col(lt, P), K);
     }
 }
@@ -376,8 +380,8 @@ int tail_grid(int64_t warps_wanted, int n_sms) {
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, int64_t counts_bytes, const AlignScratch &S, int64_t wait_limit,
-                        int64_t skip_flag, int n_sms, cudaStream_t st) {
+                        const uint8_t *counts, int64_t counts_bytes, bool blocked, const AlignScratch &S,
+                        int64_t wait_limit, int64_t skip_flag, int n_sms, cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fill_kernel, 32 * kFillWarps, 0);
@@ -388,7 +392,7 @@ cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGe
     e = cudaMemsetAsync(S.queue, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     fill_kernel<<<(unsigned)blocks, 32 * kFillWarps, 0, st>>>(src, tgt, geom, items, n_items, P, counts,
-                                                               counts_bytes, S, wait_limit, skip_flag);
+                                                               counts_bytes, blocked, S, wait_limit, skip_flag);
     return cudaGetLastError();
 }
 
@@ -411,10 +415,12 @@ cudaError_t launch_scan32(const int32_t *in, int64_t n, int32_t *out, cudaStream
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                              const AlignScratch &S, const uint8_t *counts, int n_sms, cudaStream_t st) {
+                              const AlignScratch &S, const uint8_t *counts, bool blocked, int n_sms,
+                              cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
     if (counts)
-        link_score_cached_kernel<<<n_sms * 8, 32 * kTailWarps, 0, st>>>(src, tgt, geom, n_pairs, P, S, counts);
+        link_score_cached_kernel<<<n_sms * 8, 32 * kTailWarps, 0, st>>>(src, tgt, geom, n_pairs, P, S, counts,
+                                                                         blocked);
     else
         link_score_kernel<<<n_sms * 16, 32 * kTailWarps, 0, st>>>(src, tgt, dict, geom, n_pairs, P, S);
     return cudaGetLastError();

@@ -11,7 +11,10 @@ namespace gbm {
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int32_t kEmpty = -1;
 
-// Traceback direction codes, 2 bits per cell.
+// Traceback directions.  The fill stores, per cell, whether the UP and the
+// LEFT candidate equal the cell's value (one bit each: per row and 32-column
+// block a 64-bit word, UP bits low, LEFT bits high); the walk takes UP if
+// set, else LEFT if set, else DIAG.
 constexpr uint32_t kDiag = 0, kUp = 1, kLeft = 2;
 
 struct DevParams {
@@ -95,6 +98,24 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // is exact.  Same value as (float)x, which is a quarter-rate conversion.
 __device__ __forceinline__ float small_int_float(int x) {
     return __fsub_rn(__int_as_float(0x4B000000 | x), 8388608.0f);
+}
+// all-ones if a == b, else 0
+__device__ __forceinline__ uint32_t eq_mask(float a, float b) {
+    uint32_t m;
+    asm("set.eq.u32.f32 %0, %1, %2;" : "=r"(m) : "f"(a), "f"(b));
+    return m;
+}
+// Similarity of a cell from its two count bytes as one 16-bit word (ms in
+// the low byte): each byte goes straight into the mantissa of 2^23 by a byte
+// permute, the same floats small_int_float makes.
+__device__ __forceinline__ float similarity_q16(uint32_t q16, const SimRow &r, const SimCol &c, const SimConst &k) {
+    const float fs = __fsub_rn(__int_as_float(__byte_perm(q16, 0x4B000000u, 0x7540)), 8388608.0f);
+    const float ft = __fsub_rn(__int_as_float(__byte_perm(q16, 0x4B000000u, 0x7541)), 8388608.0f);
+    const float q = fminf(__fmul_rn(r.len, c.rlen), __fmul_rn(c.len, r.rlen));
+    float y = __fmaf_rn(k.c1, q, k.c0);
+    y = __fmaf_rn(c.b, ft, y);
+    y = __fmaf_rn(r.a, fs, y);
+    return rcp_approx(__fadd_rn(1.0f, ex2_approx(y)));
 }
 __device__ __forceinline__ float similarity(int ms, int mt, const SimRow &r, const SimCol &c, const SimConst &k) {
     const float q = fminf(__fmul_rn(r.len, c.rlen), __fmul_rn(c.len, r.rlen));

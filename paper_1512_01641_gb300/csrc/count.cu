@@ -18,6 +18,7 @@
 // definitions read: a source position counts once however many of its
 // translations hit; a target position counts once however many source tokens
 // translate to it.
+#include <algorithm>
 #include <cstddef>
 
 #include "kernels.h"
@@ -564,6 +565,417 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tile kernel: the same strip table, with the per-block work spread evenly
+// over the CTA's four warps and no shared atomics outside the column pass.
+//
+// Once per strip (row group) the table of the strip's translations is built
+// from a fixed-width copy of the dictionary (dict4: the 1..4 translations of
+// a source id in one 16-byte load, -1 padded), every thread holding all of
+// its positions' loads in flight at once.  Each source position keeps a
+// record of its translations' table slots (four 16-bit slots, padding = a
+// slot whose column mask is always 0).  Per 32 x 32 block:
+//   column pass (all threads, token by token): each target token looks
+//     itself up; a hit replaces the token by RT[t] (the rows whose
+//     translation sets contain t) and sets the token's column bit in the
+//     slot's column mask CM[slot] (the columns whose sentence contains t);
+//   quarter passes: warp w takes the w-th quarter of every column's tokens
+//     (lane = column: their row masks into bit-sliced counters, mt) and of
+//     every row's positions (lane = row: h = OR of CM over the position's
+//     slots, into bit-sliced counters, ms);
+//   combine: every warp adds the four quarters (bit-sliced, 4 planes each)
+//     and expands one quarter of the bytes: columns 8w..8w+7 of ms (lane =
+//     row), rows 8w..8w+7 of mt (lane = column, through a transpose tile);
+//   output: lane = row interleaves (ms, mt) pairs by byte permutes and
+//     writes 16 bytes: straight into the blocked layout (one 2 KB tile per
+//     32 x 32 block, row r at byte 64 r) or, row-major, through a tile.
+// The counts are the same integers as the other count kernels compute.
+constexpr int kTileWarps = 4;
+constexpr int kTileThreads = 32 * kTileWarps;
+constexpr int kTileSlots = 1 << kStripLogSlots;  // 2048
+constexpr int kTileZero = kTileSlots;            // CM index that stays 0
+constexpr int kTilePosRounds = (kPosCap + kTileThreads - 1) / kTileThreads;
+constexpr int kTileTokRounds = (kTokCap + kTileThreads - 1) / kTileThreads;
+
+struct alignas(16) TileSmem {
+    uint64_t bar;                   // completion barrier of the staged target tokens
+    int32_t n_ent;                  // translation entries of the row group
+    int32_t tsh;                    // staged block: index in tg of its first token | bulk << 30
+    int2 ent[kTileSlots];           // hash table: (target id, row mask of the rows translating to it)
+    uint32_t cm[kTileSlots + 4];    // column masks of the current block; cm[kTileZero] stays 0
+    uint2 prec[kPosCap];            // per source position: byte offsets into cm of its translations' slots
+    uint32_t tg[kTokCap + 8];       // staged target tokens, replaced in place by their row masks
+    uint32_t part[kTileWarps][8][32];  // per warp: 4 ms planes, 4 mt planes; then the output tile
+    uint8_t mt_t[32][36];           // mt bytes [column][row]
+    uint8_t colid[kTokCap];
+    uint8_t rowid[kPosCap];
+    int32_t ctpre[33];              // per column of the staged block: first token index; [32] = total
+};
+static_assert(offsetof(TileSmem, tg) % 16 == 0 && offsetof(TileSmem, ent) % 16 == 0 &&
+                  offsetof(TileSmem, cm) % 16 == 0 && 4 * (kTileSlots + 3) < 65536,
+              "tile kernel shared layout");
+
+// Insert t into the interleaved table (linear probing): its slot, or -1 if
+// the table is full.
+__device__ __forceinline__ int ent_insert(int2 *ent, int32_t t) {
+    uint32_t h = hash_slot(t, kStripLogSlots);
+    for (int n = 0; n < kTileSlots; ++n) {
+        const int32_t old = atomicCAS(&ent[h].x, kEmpty, t);
+        if (old == kEmpty || old == t) return (int)h;
+        h = (h + 1) & (kTileSlots - 1);
+    }
+    return -1;
+}
+
+// Continue a lookup of t at slot h (after a first probe that found neither t
+// nor an empty slot): the slot's entry, key kEmpty if t is absent.
+__device__ __forceinline__ int ent_find_from(const int2 *ent, int32_t t, uint32_t h, uint32_t &rm) {
+    for (int n = 1; n < kTileSlots; ++n) {
+        const int2 e = ent[h];
+        if (e.x == t) {
+            rm = (uint32_t)e.y;
+            return (int)h;
+        }
+        if (e.x == kEmpty) return -1;
+        h = (h + 1) & (kTileSlots - 1);
+    }
+    return -1;
+}
+static_assert(kEntCap * 100 <= kTileSlots * 71, "entry cap bounds the tile table's load");
+
+// Sum of four 4-plane bit-sliced counters (each lane: 32 counters of at most
+// 8) into 5 planes: ripple adds with three-input XOR / majority.
+__device__ __forceinline__ void add4x4(const uint32_t (&a)[4], const uint32_t (&b)[4], const uint32_t (&c)[4],
+                                       const uint32_t (&d)[4], uint32_t (&r)[5]) {
+    uint32_t x[5], y[5];
+    uint32_t cx = 0u, cy = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        x[k] = a[k] ^ b[k] ^ cx;
+        cx = (a[k] & b[k]) | (cx & (a[k] ^ b[k]));
+        y[k] = c[k] ^ d[k] ^ cy;
+        cy = (c[k] & d[k]) | (cy & (c[k] ^ d[k]));
+    }
+    x[4] = cx;
+    y[4] = cy;
+    uint32_t cz = 0u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        r[k] = x[k] ^ y[k] ^ cz;
+        cz = (x[k] & y[k]) | (cz & (x[k] ^ y[k]));
+    }
+}
+
+// Bytes of the counters for bit positions 4m .. 4m+3 (byte r <- position 4m+r).
+__device__ __forceinline__ uint32_t nibble_bytes(const uint32_t (&p)[5], int m) {
+    uint32_t w = 0u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) w |= (((p[k] >> (4 * m)) & 0xFu) * (0x00204081u << k)) & (0x01010101u << k);
+    return w;
+}
+
+// Fixed-width dictionary: entry v holds the translations of source id v, -1
+// padded (every list has at most four entries).
+__global__ void dict4_kernel(DevDict d, int32_t v_src, int4 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < v_src; v += stride) {
+        const int32_t e0 = d.off[v], n = d.off[v + 1] - e0;
+        int4 q = make_int4(-1, -1, -1, -1);
+        if (n > 0) q.x = d.tgt[e0];
+        if (n > 1) q.y = d.tgt[e0 + 1];
+        if (n > 2) q.z = d.tgt[e0 + 2];
+        if (n > 3) q.w = d.tgt[e0 + 3];
+        out[v] = q;
+    }
+}
+
+template <bool BLOCKED>
+__global__ void __launch_bounds__(kTileThreads, 5)
+count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, const PairGeom *__restrict__ geom,
+                  const CountStripItem *__restrict__ items, int64_t n_items, int32_t *queue, bool bulk_ok,
+                  uint8_t *__restrict__ counts, uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) mbar_init(&sm.bar);
+    for (int x = tid; x < (kTileSlots + 4) / 4; x += kTileThreads)
+        reinterpret_cast<uint4 *>(sm.cm)[x] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    uint32_t phase = 0;
+    __shared__ int32_t item_sh;
+
+    for (;;) {
+        __syncthreads();  // everyone has read the previous item's index
+        if (tid == 0) item_sh = atomicAdd(queue, 1);
+        __syncthreads();
+        const int64_t it = item_sh;
+        if (it >= n_items) break;
+        const CountStripItem item = items[it];
+        const PairGeom g = geom[item.pair];
+        const int r0 = item.strip * 32;
+        const int rend = min(item.r_hi, g.n - r0);
+        const int64_t ssent0 = src.doc[item.pair] + r0;
+        const int64_t tdoc = tgt.doc[item.pair];
+        const int nblk = (g.m + 31) >> 5;
+        int group = 32;
+        for (int g_lo = item.r_lo; g_lo < rend;) {
+            const int g_hi = min(g_lo + group, rend);
+            const bool rv = lane >= g_lo && lane < g_hi;
+            const int my_len = rv ? (int)(src.sent[ssent0 + lane + 1] - src.sent[ssent0 + lane]) : 0;
+            int n_pos;
+            const int prow = warp_excl_scan(my_len, lane, n_pos);
+            const int64_t ptok0 = src.sent[ssent0 + g_lo];
+            // the group's positions, all loads in flight at once
+            const int prounds = (n_pos + kTileThreads - 1) / kTileThreads;  // the same in every thread
+            int32_t v[kTilePosRounds];
+#pragma unroll
+            for (int k = 0; k < kTilePosRounds; ++k) {
+                const int p = tid + kTileThreads * k;
+                v[k] = p < n_pos ? src.tok[ptok0 + p] : -1;
+            }
+            int4 d4[kTilePosRounds];
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < kTilePosRounds; ++k) {
+                d4[k] = v[k] >= 0 ? __ldg(dict4 + v[k]) : make_int4(-1, -1, -1, -1);
+            }
+#pragma unroll
+            for (int k = 0; k < kTilePosRounds; ++k) {
+                cnt += (d4[k].x >= 0) + (d4[k].y >= 0) + (d4[k].z >= 0) + (d4[k].w >= 0);
+            }
+            for (int x = tid; x < kTileSlots / 2; x += kTileThreads)
+                reinterpret_cast<int4 *>(sm.ent)[x] = make_int4(kEmpty, 0, kEmpty, 0);
+            // row of every position: warp w writes positions 8w .. 8w+7 of each row
+            for (int t = 8 * warp; t < min(8 * warp + 8, my_len); ++t) sm.rowid[prow + t] = (uint8_t)lane;
+            if (tid == 0) sm.n_ent = 0;
+            __syncthreads();
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(kFull, cnt, off);
+            if (lane == 0 && cnt) atomicAdd(&sm.n_ent, cnt);
+            __syncthreads();
+            if (sm.n_ent > kEntCap) {
+                __syncthreads();  // everyone has read n_ent before the rebuild resets it
+                if (group == 1) {
+                    if (tid == 0) atomicOr(status, kStTableFull);
+                    break;
+                }
+                group >>= 1;
+                continue;
+            }
+            // inserts: row masks and the positions' slot records
+#pragma unroll
+            for (int k = 0; k < kTilePosRounds; ++k) {
+                if (k >= prounds) break;
+                const int p = tid + kTileThreads * k;
+                if (p < n_pos) {
+                    const uint32_t rbit = 1u << sm.rowid[p];
+                    const int32_t tt[4] = {d4[k].x, d4[k].y, d4[k].z, d4[k].w};
+                    uint32_t sl[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        sl[u] = 4u * kTileZero;
+                        if (tt[u] >= 0) {
+                            const int h = ent_insert(sm.ent, tt[u]);
+                            if (h < 0) {
+                                atomicOr(status, kStTableFull);
+                            } else {
+                                atomicOr(reinterpret_cast<uint32_t *>(&sm.ent[h].y), rbit);
+                                sl[u] = 4u * (uint32_t)h;
+                            }
+                        }
+                    }
+                    sm.prec[p] = make_uint2(sl[0] | (sl[1] << 16), sl[2] | (sl[3] << 16));
+                }
+            }
+
+            // stage block jb's target tokens (warp 3)
+            int64_t nx_lo = 0, nx_hi = 0;
+            auto offsets = [&](int jb) {
+                const int c = 32 * jb + lane;
+                if (jb < nblk && c < g.m) {
+                    nx_lo = tgt.sent[tdoc + c];
+                    nx_hi = tgt.sent[tdoc + c + 1];
+                } else {
+                    nx_lo = nx_hi = 0;
+                }
+            };
+            auto stage_block = [&](int jb) {
+                const int nc = min(32, g.m - 32 * jb);
+                const int my_lt = lane < nc ? (int)(nx_hi - nx_lo) : 0;
+                const int64_t ttok0 = __shfl_sync(kFull, nx_lo, 0);
+                int n_tok;
+                const int tpre = warp_excl_scan(my_lt, lane, n_tok);
+                sm.ctpre[lane] = tpre;
+                if (lane == 0) sm.ctpre[32] = n_tok;
+                for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
+                bool bulk_b;
+                const int sh = stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.tg, &sm.bar, bulk_ok, lane, bulk_b);
+                if (lane == 0) sm.tsh = sh | (bulk_b ? 1 << 30 : 0);
+            };
+            if (warp == 3) {
+                offsets(0);
+                stage_block(0);
+                offsets(1);
+            }
+            fence_proxy_async();
+            __syncthreads();  // table, position records and block 0's staging complete
+
+            const int lq0 = (warp * my_len) >> 2, lq1 = ((warp + 1) * my_len) >> 2;  // this warp's quarter of the row
+            for (int jb = 0; jb < nblk; ++jb) {
+                const int c0 = jb * 32;
+                const int nc = min(32, g.m - c0);
+                const int tshw = sm.tsh;
+                stage_wait_own((tshw >> 30) & 1, &sm.bar, phase, status);
+                const int n_tok = sm.ctpre[32];
+                uint32_t *tg = sm.tg + (tshw & ((1 << 30) - 1));
+                // column pass
+                const int trounds = (n_tok + kTileThreads - 1) / kTileThreads;  // the same in every thread
+                uint32_t hit[kTileTokRounds];
+                {
+                    int32_t tk[kTileTokRounds];
+                    uint32_t hs[kTileTokRounds];
+                    int32_t k0[kTileTokRounds];
+#pragma unroll
+                    for (int k = 0; k < kTileTokRounds; ++k) {
+                        if (k >= trounds) break;
+                        const int x = tid + kTileThreads * k;
+                        tk[k] = x < n_tok ? (int32_t)tg[x] : kEmpty;
+                        hs[k] = hash_slot(tk[k], kStripLogSlots);
+                        k0[k] = x < n_tok ? sm.ent[hs[k]].x : kEmpty;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kTileTokRounds; ++k) {
+                        hit[k] = kTileZero;
+                        if (k >= trounds) break;
+                        const int x = tid + kTileThreads * k;
+                        if (x < n_tok) {
+                            int slot = -1;
+                            uint32_t rm = 0u;
+                            if (k0[k] == tk[k]) {
+                                slot = (int)hs[k];
+                                rm = (uint32_t)sm.ent[slot].y;
+                            } else if (k0[k] != kEmpty) {
+                                slot = ent_find_from(sm.ent, tk[k], (hs[k] + 1) & (kTileSlots - 1), rm);
+                            }
+                            if (slot >= 0) {
+                                atomicOr(&sm.cm[slot], 1u << sm.colid[x]);
+                                hit[k] = (uint32_t)slot;
+                            }
+                            tg[x] = rm;
+                        }
+                    }
+                }
+                __syncthreads();
+                // quarter passes
+                {
+                    BitCounter<4> mtq, msq;
+                    mtq.clear();
+                    msq.clear();
+                    if (lane < nc) {
+                        const int t0 = sm.ctpre[lane];
+                        const int t1 = lane < 31 ? sm.ctpre[lane + 1] : n_tok;
+                        const int L = t1 - t0;
+                        acc_words(mtq, tg + t0 + ((warp * L) >> 2), (((warp + 1) * L) >> 2) - ((warp * L) >> 2));
+                    }
+                    int p = prow + lq0;
+                    const int pe = prow + lq1;
+                    const unsigned char *cmb = reinterpret_cast<const unsigned char *>(sm.cm);
+                    auto cmw = [&](uint32_t off) { return *reinterpret_cast<const uint32_t *>(cmb + off); };
+                    for (; p + 2 <= pe; p += 2) {
+                        const uint2 a = sm.prec[p], b = sm.prec[p + 1];
+                        const uint32_t ha = cmw(a.x & 0xFFFFu) | cmw(a.x >> 16) | cmw(a.y & 0xFFFFu) | cmw(a.y >> 16);
+                        const uint32_t hb = cmw(b.x & 0xFFFFu) | cmw(b.x >> 16) | cmw(b.y & 0xFFFFu) | cmw(b.y >> 16);
+                        msq.add(ha);
+                        msq.add(hb);
+                    }
+                    if (p < pe) {
+                        const uint2 a = sm.prec[p];
+                        msq.add(cmw(a.x & 0xFFFFu) | cmw(a.x >> 16) | cmw(a.y & 0xFFFFu) | cmw(a.y >> 16));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        sm.part[warp][k][lane] = msq.p[k];
+                        sm.part[warp][4 + k][lane] = mtq.p[k];
+                    }
+                }
+                fence_proxy_async();  // this block's accesses to tg come before the next block's copy into it
+                __syncthreads();
+                // column masks back to zero (every hit slot; repeats are harmless)
+#pragma unroll
+                for (int k = 0; k < kTileTokRounds; ++k) {
+                    if (k >= trounds) break;
+                    if (tid + kTileThreads * k < n_tok) sm.cm[hit[k]] = 0u;
+                }
+                // the next block's tokens go out now (tg, ctpre, colid are free)
+                if (warp == 3 && jb + 1 < nblk) {
+                    stage_block(jb + 1);
+                    offsets(jb + 2);
+                }
+                // combine the quarters; expand this warp's quarter of the bytes
+                uint32_t msw0, msw1;
+                {
+                    uint32_t q[4][4];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) q[w][k] = sm.part[w][k][lane];
+                    uint32_t ms5[5];
+                    add4x4(q[0], q[1], q[2], q[3], ms5);
+                    msw0 = nibble_bytes(ms5, 2 * warp);
+                    msw1 = nibble_bytes(ms5, 2 * warp + 1);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) q[w][k] = sm.part[w][4 + k][lane];
+                    uint32_t mt5[5];
+                    add4x4(q[0], q[1], q[2], q[3], mt5);
+                    *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * warp]) = nibble_bytes(mt5, 2 * warp);
+                    *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * warp + 4]) = nibble_bytes(mt5, 2 * warp + 1);
+                }
+                __syncthreads();
+                // interleave (ms, mt) for row `lane`, columns 8w .. 8w+7
+                {
+                    const int c = 8 * warp;
+                    const uint32_t mA = (uint32_t)sm.mt_t[c][lane] | ((uint32_t)sm.mt_t[c + 1][lane] << 8) |
+                                        ((uint32_t)sm.mt_t[c + 2][lane] << 16) | ((uint32_t)sm.mt_t[c + 3][lane] << 24);
+                    const uint32_t mB = (uint32_t)sm.mt_t[c + 4][lane] | ((uint32_t)sm.mt_t[c + 5][lane] << 8) |
+                                        ((uint32_t)sm.mt_t[c + 6][lane] << 16) | ((uint32_t)sm.mt_t[c + 7][lane] << 24);
+                    const uint4 o = make_uint4(__byte_perm(msw0, mA, 0x5140), __byte_perm(msw0, mA, 0x7362),
+                                               __byte_perm(msw1, mB, 0x5140), __byte_perm(msw1, mB, 0x7362));
+                    if (BLOCKED) {
+                        if (rv) {
+                            uint8_t *tile = counts + g.tb_off * 64 + ((int64_t)item.strip * nblk + jb) * 2048;
+                            *reinterpret_cast<uint4 *>(tile + 64 * lane + 16 * warp) = o;
+                        }
+                    } else {
+                        uint32_t *ot = &sm.part[0][0][0];  // [32][17] words: the block's rows, interleaved
+                        ot[17 * lane + 4 * warp] = o.x;
+                        ot[17 * lane + 4 * warp + 1] = o.y;
+                        ot[17 * lane + 4 * warp + 2] = o.z;
+                        ot[17 * lane + 4 * warp + 3] = o.w;
+                    }
+                }
+                if (!BLOCKED) {
+                    __syncthreads();
+                    const uint32_t *ot = &sm.part[0][0][0];
+                    uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m + c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int i = 8 * warp + q;
+                        if (i >= g_lo && i < g_hi && lane < nc) {
+                            const uint32_t wd = ot[17 * i + (lane >> 1)];
+                            reinterpret_cast<uint16_t *>(out_strip + 2 * (int64_t)i * g.m)[lane] =
+                                (uint16_t)(lane & 1 ? wd >> 16 : wd & 0xFFFFu);
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // the last block is done before the next group's build
+            g_lo = g_hi;
+        }
+    }
+}
+
 template <int LOG_SLOTS, int K>
 cudaError_t launch_strip_t(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                            const PairGeom *geom, const CountStripItem *items, int64_t n_items, bool bulk_ok,
@@ -614,6 +1026,31 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
                    ? launch_strip_t<11, 5>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st)
                    : launch_strip_t<11, 8>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dict4(const DevDict &dict, int32_t v_src, int4 *dict4, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((v_src + 255) / 256, 4096);
+    dict4_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(dict, v_src, dict4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_tiles(const DevCorpus &src, const DevCorpus &tgt, const int4 *dict4, const PairGeom *geom,
+                               const CountStripItem *items, int64_t n_items, int32_t *queue, bool bulk_ok,
+                               bool blocked, uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    const size_t smem = sizeof(TileSmem);
+    auto kern = blocked ? count_tile_kernel<true> : count_tile_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(n_items < cap ? n_items : cap);
+    e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kTileThreads, smem, st>>>(src, tgt, dict4, geom, items, n_items, queue, bulk_ok, counts, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_count(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,

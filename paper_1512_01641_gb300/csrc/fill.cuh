@@ -30,6 +30,8 @@ struct FillCtx {
     uint32_t stage_phase;       // bit b: parity of buffer b's next completion
     int stage_off0, stage_off1; // byte offset of the segment in the lane's staged row, per buffer
     uint32_t *status;           // timeout bit (may be null)
+    bool blocked;               // counts in the blocked layout: row_byte is the strip's first tile,
+                                // block b of the pair at row_byte + 2048 b, row r at byte 64 r
 };
 
 // Per-warp setup of the staging barriers (lane 0 initialises, all lanes
@@ -55,6 +57,14 @@ __device__ __forceinline__ void fill_stage(FillCtx &C, int jb, int nb) {
     const int col_base = C.c0 + 32 * jb;
     const int ncol = min(32, C.c1 - col_base);
     uint64_t *bar = C.stage_bar + buf;
+    if (C.blocked) {
+        // the block's 32 rows are one aligned 2 KB tile: one copy for the warp
+        if (C.lane == 0)
+            bulk_copy_g2s(C.stage[buf], C.counts + C.row_byte + 2048 * (int64_t)(col_base >> 5), 2048u, bar);
+        else
+            mbar_arrive(bar);
+        return;
+    }
     unsigned char *dst = C.stage[buf][C.lane];
     int off = 0;
     if (C.rv) {
@@ -82,6 +92,7 @@ __device__ __forceinline__ const unsigned char *fill_stage_wait(FillCtx &C, int 
     if (!mbar_wait(C.stage_bar + buf, (C.stage_phase >> buf) & 1u, kStageWaitLimit) && C.status)
         atomicOr(C.status, kStTimeout);
     C.stage_phase ^= 1u << buf;
+    if (C.blocked) return &C.stage[buf][0][0] + 64 * C.lane;
     return C.stage[buf][C.lane] + (buf ? C.stage_off1 : C.stage_off0);
 }
 
@@ -137,11 +148,11 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const int c = (x - lane) & 31;
-            const uchar2 q = *reinterpret_cast<const uchar2 *>(st + 2 * c);
-            cur[x] = similarity(q.x, q.y, C.row, C.colv[c], C.k);
+            const uint32_t q16 = *reinterpret_cast<const uint16_t *>(st + 2 * c);
+            cur[x] = similarity_q16(q16, C.row, C.colv[c], C.k);
         }
     }
-    rc = 0;
+    uint32_t rup = 0u, rleft = 0u;
     // the cell of step u is column j = jl + u + c0 of this lane's row; it
     // exists when 0 <= jl + u < width (width 0 for a row below the pair)
     const int jl = col_base - lane - C.c0;
@@ -163,20 +174,21 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
         // first block) or at a cell the walk never visits.
         const bool valid = (uint32_t)(jl + u) < width;
         const float d = fmaxf(fmaxf(sv, b), a_up);
-        const uint32_t code = (d == a_up) ? kUp : ((d == b) ? kLeft : 0u);
-        rc |= (uint64_t)code << (2 * u);
+        rup |= eq_mask(d, a_up) & (1u << u);
+        rleft |= eq_mask(d, b) & (1u << u);
         const float e = __fsub_rn(d, C.two_p);
         const float nb2 = __fsub_rn(e, a_up);
         a_down = __fsub_rn(e, b);
         b = valid ? nb2 : b;
         if (valid && lane == 31) __stcg(hrow_at + u, a_down);
     }
+    rc = ((uint64_t)rleft << 32) | rup;
     // the word of block jb-1 is complete: its columns came at steps u >= lane
     // of iteration jb-1 and u < lane of iteration jb
     if (jb > 0) {
-        const int sh = 2 * lane;
-        const uint64_t w = (rp >> sh) | (sh ? (rc << (64 - sh)) : 0ull);
-        tb_strip[(int64_t)((C.c0 >> 5) + jb - 1) * 32 + lane] = w;
+        const uint32_t wu = __funnelshift_r((uint32_t)rp, rup, lane);
+        const uint32_t wl = __funnelshift_r((uint32_t)(rp >> 32), rleft, lane);
+        tb_strip[(int64_t)((C.c0 >> 5) + jb - 1) * 32 + lane] = ((uint64_t)wl << 32) | wu;
     }
 }
 
@@ -187,13 +199,14 @@ __device__ __forceinline__ void fill_block(FillCtx &C, int jb, int nb, bool firs
 // bytes -- so that a tile can start these loads before it waits for its
 // neighbours.  nb receives the number of 32-column blocks.
 __device__ __forceinline__ void fill_strip_prepare(FillCtx &C, int s, const int64_t *__restrict__ ssent,
-                                                   int64_t cell_off, FillAhead &ah, int &nb) {
+                                                   int64_t cell_off, FillAhead &ah, int &nb, int64_t tb_off = 0) {
     const int lane = C.lane;
     C.r = 32 * s + lane;
     C.rv = C.r < C.N;
     const int ls = C.rv ? (int)(ssent[C.r + 1] - ssent[C.r]) : 1;
     C.row = sim_row(ls, C.P);
-    C.row_byte = 2 * (cell_off + (int64_t)C.r * C.M);
+    C.row_byte = C.blocked ? 64 * tb_off + 2048 * (int64_t)s * ((C.M + 31) >> 5)
+                           : 2 * (cell_off + (int64_t)C.r * C.M);
     nb = (C.c1 - C.c0 + 31) >> 5;
     fill_ahead_lt(C, 0, nb, ah);
     fill_stage(C, 0, nb);
@@ -273,10 +286,9 @@ __device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N
             }
         }
         const uint64_t wr = __shfl_sync(kFull, word, rr & 31);
-        const uint32_t code = (uint32_t)(wr >> (2 * (cc & 31))) & 3u;
-        if (code == kUp) {
+        if ((wr >> (cc & 31)) & 1u) {  // UP
             --i;
-        } else if (code == kLeft) {
+        } else if ((wr >> (32 + (cc & 31))) & 1u) {  // LEFT
             --j;
         } else {
             // diagonal run from (rr, cc) upwards: lane l's cell on it is
@@ -285,7 +297,7 @@ __device__ __forceinline__ int walk_pair(const uint64_t *__restrict__ tbp, int N
             const int t = top - lane;
             const int cl = cc - t;
             bool stop = true;  // the run cannot pass this lane's cell
-            if (t >= 0 && cl >= 32 * bj) stop = ((uint32_t)(word >> (2 * (cl & 31))) & 3u) != kDiag;
+            if (t >= 0 && cl >= 32 * bj) stop = (((word >> (cl & 31)) | (word >> (32 + (cl & 31)))) & 1u) != 0;
             const uint32_t below = __ballot_sync(kFull, stop) & (0xFFFFFFFFu >> (31 - top));
             const int h = below ? 31 - __clz(below) : -1;  // the lane where the run ends (lane top is DIAG)
             if (lane > h && lane <= top) {

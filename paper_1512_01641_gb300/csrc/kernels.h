@@ -58,7 +58,7 @@ struct FillItem {
 
 // Plan-owned scratch of the alignment kernels.
 struct AlignScratch {
-    uint64_t *tb;      // traceback words: [strip][column block][row in strip], 2 bits per cell
+    uint64_t *tb;      // traceback words: [strip][column block][row in strip]: UP bits low, LEFT bits high
     float *hrow;       // boundary row per pair (UP candidates of the next strip)
     float *vcol;       // boundary column per pair (LEFT candidates of the next chunk)
     int32_t *flags;    // tile completion flags
@@ -86,6 +86,18 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
                                 int log_slots, int planes, bool bulk_ok, uint8_t *counts, uint32_t *status,
                                 int n_sms, cudaStream_t st);
 
+// Fixed-width copy of a dictionary whose lists hold at most four targets.
+cudaError_t launch_dict4(const DevDict &dict, int32_t v_src, int4 *dict4, cudaStream_t st);
+// Tile count kernel (sentences of at most 31 tokens, dictionary fan-out at
+// most 4): blocked = true writes the blocked layout (pair k's 32 x 32 block
+// (s, b) is the 2048-byte tile at byte 64 * tb_off + 2048 * (s * nblk + b),
+// row r at byte 64 r of it, (ms, mt) per cell), false the row-major layout.
+// queue: one int32 of device scratch (reset by the launch).
+cudaError_t launch_count_tiles(const DevCorpus &src, const DevCorpus &tgt, const int4 *dict4, const PairGeom *geom,
+                               const CountStripItem *items, int64_t n_items, int32_t *queue, bool bulk_ok,
+                               bool blocked, uint8_t *counts, uint32_t *status, int n_sms, cudaStream_t st);
+constexpr int kTileMaxFanout = 4;
+
 constexpr int kStripLogSlots = 11;  // row-table slots of the strip count kernel (2^11)
 constexpr int kStripMaxFanout = 46; // dictionary fan-out up to which one row always fits the row table
 
@@ -95,8 +107,8 @@ cudaError_t launch_score(const DevCorpus &src, const DevCorpus &tgt, const PairG
 
 cudaError_t launch_fill(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                         const FillItem *items, int64_t n_items, const DevParams &P,
-                        const uint8_t *counts, int64_t counts_bytes, const AlignScratch &S, int64_t wait_limit,
-                        int64_t skip_flag, int n_sms, cudaStream_t st);
+                        const uint8_t *counts, int64_t counts_bytes, bool blocked, const AlignScratch &S,
+                        int64_t wait_limit, int64_t skip_flag, int n_sms, cudaStream_t st);
 
 // order: the pairs by decreasing size (a permutation of 0..n_pairs-1)
 cudaError_t launch_walk(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const AlignScratch &S,
@@ -141,7 +153,8 @@ cudaError_t launch_links_combine(LinkView fwd, LinkView rev, int64_t n_pairs, in
 
 cudaError_t launch_link_score(const DevCorpus &src, const DevCorpus &tgt, const DevDict &dict,
                               const PairGeom *geom, int64_t n_pairs, const DevParams &P,
-                              const AlignScratch &S, const uint8_t *counts, int n_sms, cudaStream_t st);
+                              const AlignScratch &S, const uint8_t *counts, bool blocked, int n_sms,
+                              cudaStream_t st);
 
 cudaError_t launch_pair_sum(const PairGeom *geom, int64_t n_pairs, const DevParams &P,
                             const AlignScratch &S, float *pair_score, int n_sms, cudaStream_t st);
@@ -203,6 +216,27 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
                                  const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
                                  const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float dloss,
                                  float *grad, float *hvp, int n_sms, cudaStream_t st);
+
+// Unconstrained (Yalign A*) alignment: the caller's workspace, carved up.
+struct UcScratch {
+    const int64_t *a_off;     // per pair: first double of its two DP rows (2 (M+1))
+    const int64_t *prev_off;  // per pair: first int of its predecessor pointers (N (M+1))
+    const int64_t *link_off;  // per pair: first slot of its window of N matched cells
+    double *A;
+    int32_t *prev;
+    int32_t *li, *lj;
+    float *ls;
+    int32_t *n_match;         // per pair: matched cells (at the end of the window)
+};
+// Scores, matches and per-pair kept-link counts (kept), then the compaction
+// of the kept links (s >= thr) at out_off.
+cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
+                                 int64_t n_pairs, const DevParams &P, const uint8_t *counts, const UcScratch &W,
+                                 float *pair_score, const int64_t *out_off_scan_in, int32_t *kept, int n_sms,
+                                 cudaStream_t st);
+cudaError_t launch_unconstrained_copy(const PairGeom *geom, int64_t n_pairs, float thr, const UcScratch &W,
+                                      const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_s, int n_sms,
+                                      cudaStream_t st);
 
 // Records e as this thread's last CUDA error (what mine_last_cuda_error
 // returns) for entry points outside the plan's translation unit.

@@ -62,6 +62,7 @@ align_pair_static_kernel(const int64_t *__restrict__ ssent, const int64_t *__res
         C.stage = stage;
         C.stage_bar = stage_bar;
         C.status = &status;
+        C.blocked = false;
         fill_stage_init(C);
         C.N = N;
         C.M = M;

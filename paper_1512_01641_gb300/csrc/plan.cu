@@ -166,6 +166,12 @@ struct mine_plan {
     CountStripItem *strip_items = nullptr;
     int64_t n_strip_items = 0;
     bool use_strips = false;  // strip count kernel (else the per-block kernel)
+    bool use_tiles = false;   // tile count kernel (sentences <= 31 tokens, fan-out <= 4); mine_pairs
+                              // then keeps its counts in the blocked layout
+    int4 *dict4 = nullptr;    // fixed-width dictionary of the tile kernel
+    int32_t *count_queue = nullptr;
+    int32_t v_src = 0;
+    int64_t counts_bytes = 0;  // plan-owned count buffer (blocked layout when use_tiles)
     bool bulk_ok = false;     // token arrays 16-byte aligned: bulk-copy staging
     FillItem *fill_items = nullptr;
     uint8_t *counts = nullptr;
@@ -190,6 +196,7 @@ struct mine_plan {
     mine_out graph_out{};
     mine_params graph_params{};
     int64_t graph_captures = 0;
+    std::vector<int64_t> uc_off_h;  // per-pair workspace offsets of the unconstrained aligner
 };
 
 // Launch f() on stream st; with timing enabled, bracket it by two events.
@@ -253,7 +260,8 @@ static void plan_free(mine_plan *p) {
     drain_pending(p);
     drop_graph(p);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-    void *bufs[] = {p->geom, p->pair_order, p->count_items, p->strip_items, p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
+    void *bufs[] = {p->geom, p->pair_order, p->count_items, p->strip_items, p->dict4, p->count_queue,
+                    p->fill_items, p->counts, p->S.tb, p->S.hrow, p->S.vcol,
                     p->S.flags, p->S.queue, p->S.status, p->S.diag_i, p->S.diag_j, p->S.diag_s, p->S.n_diag,
                     p->S.diag_off, p->S.n_links, p->stats};
     // back to the pool after the work last enqueued on the plan (the
@@ -558,7 +566,7 @@ int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt
     PLAN_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice, st));
 
     // scratch
-    PLAN_CK(dalloc(&p->counts, 2 * p->n_cells, p->device, st));
+    p->v_src = dict->v_src;
     PLAN_CK(dalloc(&p->S.tb, tbw, p->device, st));
     PLAN_CK(dalloc(&p->S.hrow, hrow, p->device, st));
     PLAN_CK(dalloc(&p->S.vcol, vcol, p->device, st));
@@ -584,6 +592,13 @@ int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt
     // overfill the row table); it needs sentences of at most 31 tokens (5
     // counter planes) and a dictionary fan-out small enough for one row to fit
     p->use_strips = std::max(stats[0], stats[1]) <= 31 && stats[3] <= kStripMaxFanout;
+    p->use_tiles = p->use_strips && stats[3] <= kTileMaxFanout;
+    p->counts_bytes = p->use_tiles ? 64 * tbw : 2 * p->n_cells;
+    PLAN_CK(dalloc(&p->counts, p->counts_bytes, p->device, st));
+    if (p->use_tiles) {
+        PLAN_CK(dalloc(&p->dict4, (size_t)p->v_src, p->device, st));
+        PLAN_CK(dalloc(&p->count_queue, 1, p->device, st));
+    }
     if (p->use_strips) {
         std::vector<CountStripItem> sitems;
         sitems.reserve((size_t)p->soft_strips);
@@ -629,12 +644,20 @@ int mine_plan_cell_offsets(const mine_plan *p, int64_t *host_out) {
     return MINE_OK;
 }
 
-int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
-    if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
+}  // extern "C"
+
+// Counts of every cell into `counts`: row-major (the layout of mine_count) or,
+// with the tile kernel, blocked (mine_pairs' own buffer).
+static int count_into(mine_plan *p, uint8_t *counts, bool blocked, cudaStream_t st) {
     if (p->n_cells == 0) return MINE_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    DoneMark mark{p, st};
-    if (p->use_strips) {
+    if (p->use_tiles) {
+        MINE_CK(timed(p, kKCount, st, [&] {
+            cudaError_t e = launch_dict4(p->dict, p->v_src, p->dict4, st);
+            if (e != cudaSuccess) return e;
+            return launch_count_tiles(p->src, p->tgt, p->dict4, p->geom, p->strip_items, p->n_strip_items,
+                                      p->count_queue, p->bulk_ok, blocked, counts, p->S.status, p->n_sms, st);
+        }));
+    } else if (p->use_strips) {
         MINE_CK(timed(p, kKCount, st, [&] {
             return launch_count_strips(p->src, p->tgt, p->dict, p->geom, p->strip_items, p->n_strip_items,
                                        kStripLogSlots, p->planes, p->bulk_ok, counts, p->S.status, p->n_sms, st);
@@ -648,6 +671,16 @@ int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
     return MINE_OK;
 }
 
+extern "C" {
+
+int mine_count(mine_plan *p, uint8_t *counts, miner_stream_t stream) {
+    if (!p || (!counts && p->n_cells > 0)) return MINE_EINVAL;
+    if (p->n_cells == 0) return MINE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
+    return count_into(p, counts, false, st);
+}
+
 int mine_score(mine_plan *p, const mine_params *params, const uint8_t *counts, float *s, float *feat,
                miner_stream_t stream) {
     if (!p || !params || ((!counts || !s) && p->n_cells > 0)) return MINE_EINVAL;
@@ -659,27 +692,39 @@ int mine_score(mine_plan *p, const mine_params *params, const uint8_t *counts, f
     return MINE_OK;
 }
 
-int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, mine_out *out,
-               miner_stream_t stream) {
+}  // extern "C"
+
+static int align_from(mine_plan *p, const mine_params *params, const uint8_t *counts, bool blocked, mine_out *out,
+                      cudaStream_t st);
+
+extern "C" int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, mine_out *out,
+                          miner_stream_t stream) {
     if (!p || !params || !out || !out->link_off || (!out->pair_score && p->n_pairs > 0)) return MINE_EINVAL;
     if (out->link_capacity < p->link_cap) return MINE_EINVAL;
     if (p->link_cap > 0 && (!out->link_i || !out->link_j || !out->link_s)) return MINE_EINVAL;
     if (p->n_cells > 0 && !counts) return MINE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     DoneMark mark{p, st};
+    return align_from(p, params, counts, false, out, st);
+}
+
+// Fill, walk, link scoring and compaction from counts in either layout.
+static int align_from(mine_plan *p, const mine_params *params, const uint8_t *counts, bool blocked, mine_out *out,
+                      cudaStream_t st) {
     const DevParams P = to_dev(*params);
     const AlignScratch &S = p->S;
     const int64_t n = p->n_pairs;
     if (p->n_flags > 0) MINE_CK(cudaMemsetAsync(S.flags, 0, p->n_flags * sizeof(int32_t), st));
     MINE_CK(timed(p, kKFill, st, [&] {
-        return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts, 2 * p->n_cells, S,
-                           p->knobs.wait_limit, p->knobs.skip_flag, p->n_sms, st);
+        return launch_fill(p->src, p->tgt, p->geom, p->fill_items, p->n_fill_items, P, counts,
+                           blocked ? p->counts_bytes : 2 * p->n_cells, blocked, S, p->knobs.wait_limit,
+                           p->knobs.skip_flag, p->n_sms, st);
     }));
     MINE_CK(timed(p, kKWalk, st, [&] { return launch_walk(p->geom, p->pair_order, n, S, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_diag, n, S.diag_off, st); }));
     MINE_CK(timed(p, kKLinks, st, [&] {
         return launch_link_score(p->src, p->tgt, p->dict, p->geom, n, P, S, p->knobs.link_recount ? nullptr : counts,
-                                 p->n_sms, st);
+                                 blocked, p->n_sms, st);
     }));
     MINE_CK(timed(p, kKLinks, st, [&] { return launch_pair_sum(p->geom, n, P, S, out->pair_score, p->n_sms, st); }));
     MINE_CK(timed(p, kKScan, st, [&] { return launch_scan(S.n_links, n, out->link_off, st); }));
@@ -690,10 +735,15 @@ int mine_align(mine_plan *p, const mine_params *params, const uint8_t *counts, m
 }
 
 static int enqueue_pairs(mine_plan *p, const mine_params *params, mine_out *out, cudaStream_t st) {
-    int r = mine_count(p, p->counts, (miner_stream_t)st);
+    if (!out->link_off || (!out->pair_score && p->n_pairs > 0) || out->link_capacity < p->link_cap ||
+        (p->link_cap > 0 && (!out->link_i || !out->link_j || !out->link_s)))
+        return MINE_EINVAL;
+    int r = count_into(p, p->counts, p->use_tiles, st);
     if (r != MINE_OK) return r;
-    return mine_align(p, params, p->counts, out, (miner_stream_t)st);
+    return align_from(p, params, p->counts, p->use_tiles, out, st);
 }
+
+extern "C" {
 
 int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_stream_t stream) {
     if (!p || !params || !out) return MINE_EINVAL;
@@ -1108,6 +1158,99 @@ int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const min
     MINE_CK(launch_scan(cnt.p, n, o->link_off, st));
     MINE_CK(launch_links_combine(F, R, n, mode, cnt.p, o->link_capacity, o->link_off, o->link_i, o->link_j, o->s_fwd,
                                  o->s_rev, st));
+    return MINE_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------- unconstrained alignment
+namespace {
+
+struct UcLayout {
+    int64_t offs, n_match, kept, A, prev, li, lj, ls, total;
+    int64_t a_total, prev_total, link_total;
+};
+
+UcLayout uc_layout(const mine_plan *p) {
+    UcLayout L{};
+    const int64_t n = p->n_pairs;
+    for (const PairGeom &g : p->geom_h) {
+        L.a_total += 2 * ((int64_t)g.m + 1);
+        L.prev_total += (int64_t)g.n * ((int64_t)g.m + 1);
+        L.link_total += g.n;
+    }
+    auto up = [](int64_t x) { return (x + 255) / 256 * 256; };
+    int64_t o = 0;
+    L.offs = o;
+    o = up(o + 3 * std::max<int64_t>(n, 1) * 8);
+    L.n_match = o;
+    o = up(o + std::max<int64_t>(n, 1) * 4);
+    L.kept = o;
+    o = up(o + std::max<int64_t>(n, 1) * 4);
+    L.A = o;
+    o = up(o + std::max<int64_t>(L.a_total, 1) * 8);
+    L.prev = o;
+    o = up(o + std::max<int64_t>(L.prev_total, 1) * 4);
+    L.li = o;
+    o = up(o + std::max<int64_t>(L.link_total, 1) * 4);
+    L.lj = o;
+    o = up(o + std::max<int64_t>(L.link_total, 1) * 4);
+    L.ls = o;
+    o = up(o + std::max<int64_t>(L.link_total, 1) * 4);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t mine_unconstrained_workspace_size(const mine_plan *p) { return p ? uc_layout(p).total : 0; }
+
+int64_t mine_unconstrained_link_capacity(const mine_plan *p) { return p ? uc_layout(p).link_total : 0; }
+
+int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint8_t *counts, void *ws, mine_out *out,
+                             miner_stream_t stream) {
+    if (!p || !params || !out || !ws || !out->link_off || (!out->pair_score && p->n_pairs > 0)) return MINE_EINVAL;
+    const UcLayout L = uc_layout(p);
+    if (out->link_capacity < L.link_total) return MINE_EINVAL;
+    if (L.link_total > 0 && (!out->link_i || !out->link_j || !out->link_s)) return MINE_EINVAL;
+    if (p->n_cells > 0 && !counts) return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    DoneMark mark{p, st};
+    const int64_t n = p->n_pairs;
+    if (p->uc_off_h.empty() && n > 0) {
+        p->uc_off_h.resize(3 * (size_t)n);
+        int64_t a = 0, pv = 0, lk = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            const PairGeom &g = p->geom_h[k];
+            p->uc_off_h[k] = a;
+            p->uc_off_h[n + k] = pv;
+            p->uc_off_h[2 * n + k] = lk;
+            a += 2 * ((int64_t)g.m + 1);
+            pv += (int64_t)g.n * ((int64_t)g.m + 1);
+            lk += g.n;
+        }
+    }
+    char *b = static_cast<char *>(ws);
+    if (n > 0) MINE_CK(cudaMemcpyAsync(b + L.offs, p->uc_off_h.data(), 3 * n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    UcScratch W;
+    W.a_off = reinterpret_cast<const int64_t *>(b + L.offs);
+    W.prev_off = W.a_off + n;
+    W.link_off = W.a_off + 2 * n;
+    W.n_match = reinterpret_cast<int32_t *>(b + L.n_match);
+    W.A = reinterpret_cast<double *>(b + L.A);
+    W.prev = reinterpret_cast<int32_t *>(b + L.prev);
+    W.li = reinterpret_cast<int32_t *>(b + L.li);
+    W.lj = reinterpret_cast<int32_t *>(b + L.lj);
+    W.ls = reinterpret_cast<float *>(b + L.ls);
+    int32_t *kept = reinterpret_cast<int32_t *>(b + L.kept);
+    const DevParams P = to_dev(*params);
+    MINE_CK(launch_unconstrained(p->src, p->tgt, p->geom, p->pair_order, n, P, counts, W, out->pair_score, nullptr,
+                                 kept, p->n_sms, st));
+    MINE_CK(launch_scan(kept, n, out->link_off, st));
+    MINE_CK(launch_unconstrained_copy(p->geom, n, P.thr, W, out->link_off, out->link_i, out->link_j, out->link_s,
+                                      p->n_sms, st));
     return MINE_OK;
 }
 

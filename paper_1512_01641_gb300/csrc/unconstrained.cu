@@ -1,0 +1,254 @@
+// Unconstrained sentence alignment: the A* aligner Yalign used, which Section
+// 5.1 contrasts with Needleman-Wunsch (Figures 3 and 5 against 4 and 6).
+//
+// Source sentences (rows) are taken in order.  After row i-1 the target
+// pointer is c (the last matched target sentence, 1-based; 0 before any
+// match).  Row i is
+//   unmatched:                    A(i, c)  = A(i-1, c) - p
+//   matched ahead (c' > c):       A(i, c') = A(i-1, c) + s(i, c') - p (c' - c - 1)
+//   matched back (c' <= c):       A(i, c') = A(i-1, c) + s(i, c') - p
+// and the target sentences after the final pointer cost p each.  Without
+// the move back these are exactly the Needleman-Wunsch alignments; the move
+// back is what lets a target sentence be used twice (the paper's
+// repetitions).  Per row, the best forward predecessor of c' is a prefix
+// maximum of A(i-1, c) + p c over c < c', the best move back a suffix maximum
+// of A(i-1, c) over c >= c': one warp per pair sweeps each row twice with
+// warp scans.  Exact ties prefer unmatched, then a forward match, then a move
+// back; among predecessors the nearest pointer; at the end the smallest final
+// pointer.  Scores are FP64 (a comparison baseline, off the mining path).
+#include <cmath>
+
+#include "kernels.h"
+
+namespace gbm {
+namespace {
+
+constexpr int kUcWarps = 4;
+
+struct MaxArg {
+    double v;
+    int a;
+};
+
+// Inclusive warp scan of (value, index) maxima in lane order: ties keep the
+// larger index (PREFER_HIGH) or the smaller one.
+template <bool UP, bool PREFER_HIGH>
+__device__ __forceinline__ MaxArg warp_max_scan(MaxArg x, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double v = UP ? __shfl_up_sync(kFull, x.v, off) : __shfl_down_sync(kFull, x.v, off);
+        const int a = UP ? __shfl_up_sync(kFull, x.a, off) : __shfl_down_sync(kFull, x.a, off);
+        const bool in = UP ? lane >= off : lane + off < 32;
+        if (in) {
+            const bool take = v > x.v || (v == x.v && (PREFER_HIGH ? a > x.a : a < x.a));
+            if (take) x = {v, a};
+        }
+    }
+    return x;
+}
+
+__device__ __forceinline__ bool better(double v, int a, const MaxArg &b, bool prefer_high) {
+    return v > b.v || (v == b.v && (prefer_high ? a > b.a : a < b.a));
+}
+
+__global__ void __launch_bounds__(32 * kUcWarps)
+unconstrained_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
+                     int64_t n_pairs, DevParams P, const uint8_t *__restrict__ counts, UcScratch W, float *pair_score) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double p = (double)P.gap;
+    const double NEG = -INFINITY;
+    const SimConst K = sim_const(P);
+    for (int64_t x = warp0; x < n_pairs; x += nwarps) {
+        const int32_t k = order[x];
+        const PairGeom g = geom[k];
+        const int N = g.n, M = g.m;
+        double *Aa = W.A + W.a_off[k], *Ab = Aa + (M + 1);
+        int32_t *prev = W.prev + W.prev_off[k];
+        const int64_t sdoc = src.doc[k], tdoc = tgt.doc[k];
+        for (int c = lane; c <= M; c += 32) Aa[c] = c == 0 ? 0.0 : NEG;
+        __syncwarp();
+        for (int i = 1; i <= N; ++i) {
+            const SimRow row = sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P);
+            const uchar2 *crow = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)(i - 1) * M;
+            int32_t *prow = prev + (int64_t)(i - 1) * (M + 1);
+            // suffix maxima Q(c') = max_{c >= c'} A(i-1, c) (nearest: smallest c),
+            // right to left; lane handles c' = 32 q + lane + 1 and keeps its value
+            const int nq = (M + 32) / 32;  // chunks covering c' = 1 .. M (+ padding)
+            // forward prefix maxima first, stored per chunk in registers is not
+            // possible for any M: the suffix pass writes Q into Ab (scratch)
+            MaxArg carry{NEG, 0x7fffffff};
+            for (int q = nq - 1; q >= 0; --q) {
+                const int c = 32 * q + lane + 1;
+                MaxArg v{c <= M ? Aa[c] : NEG, c <= M ? c : 0x7fffffff};
+                v = warp_max_scan<false, false>(v, lane);
+                if (better(carry.v, carry.a, v, false)) v = carry;
+                if (c <= M) {
+                    Ab[c] = v.v;
+                    prow[c] = v.a;  // provisional: the back predecessor of c
+                }
+                const double cv = __shfl_sync(kFull, v.v, 0);
+                const int ca = __shfl_sync(kFull, v.a, 0);
+                carry = {cv, ca};
+            }
+            __syncwarp();
+            // left to right: prefix maxima F(c') = max_{c < c'} A(i-1, c) + p c
+            // (nearest: largest c), then the three candidates of every c'
+            MaxArg pc{NEG, -1};
+            const double a0 = Aa[0];
+            for (int q = 0; q < nq; ++q) {
+                const int c = 32 * q + lane;  // predecessor pointer of c' = c + 1
+                MaxArg v{c <= M ? Aa[c] + p * (double)c : NEG, c};
+                v = warp_max_scan<true, true>(v, lane);
+                if (better(pc.v, pc.a, v, true)) v = pc;
+                const int c2 = c + 1;
+                double a_un = 0.0;
+                if (c2 <= M) a_un = Aa[c2];
+                __syncwarp();
+                if (c2 <= M) {
+                    const int lt = (int)(tgt.sent[tdoc + c2] - tgt.sent[tdoc + c2 - 1]);
+                    const uchar2 cq = crow[c2 - 1];
+                    const double sim = (double)similarity(cq.x, cq.y, row, sim_col(lt, P), K);
+                    double best = a_un - p;
+                    int arg = -1;
+                    const double fw = sim + v.v - p * (double)(c2 - 1);
+                    if (fw > best) {
+                        best = fw;
+                        arg = v.a;
+                    }
+                    const double bk = sim - p + Ab[c2];
+                    if (bk > best) {
+                        best = bk;
+                        arg = prow[c2];
+                    }
+                    prow[c2] = arg;
+                    Ab[c2] = best;
+                }
+                pc = {__shfl_sync(kFull, v.v, 31), __shfl_sync(kFull, v.a, 31)};
+            }
+            if (lane == 0) {
+                Ab[0] = a0 - p;
+                prow[0] = -1;
+            }
+            __syncwarp();
+            double *t = Aa;
+            Aa = Ab;
+            Ab = t;
+        }
+        // final pointer: max of A(N, c) - p (M - c), smallest c at ties
+        MaxArg best{NEG, 0x7fffffff};
+        for (int c = lane; c <= M; c += 32) {
+            const double v = Aa[c] - p * (double)(M - c);
+            if (better(v, c, best, false)) best = {v, c};
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double v = __shfl_xor_sync(kFull, best.v, off);
+            const int a = __shfl_xor_sync(kFull, best.a, off);
+            if (better(v, a, best, false)) best = {v, a};
+        }
+        // traceback (one lane): the matched cells, written from the end of the
+        // pair's window of N slots, and their similarities
+        if (lane == 0) {
+            int c = best.a;
+            int n = 0;
+            int32_t *li = W.li + W.link_off[k], *lj = W.lj + W.link_off[k];
+            float *ls = W.ls + W.link_off[k];
+            for (int i = N; i >= 1; --i) {
+                const int a = prev[(int64_t)(i - 1) * (M + 1) + c];
+                if (a != -1) {
+                    const int slot = N - 1 - n;
+                    const int lt = (int)(tgt.sent[tdoc + c] - tgt.sent[tdoc + c - 1]);
+                    const uchar2 cq = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)(i - 1) * M + c - 1];
+                    li[slot] = i - 1;
+                    lj[slot] = c - 1;
+                    ls[slot] = similarity(cq.x, cq.y, sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P),
+                                          sim_col(lt, P), K);
+                    ++n;
+                    c = a;
+                }
+            }
+            W.n_match[k] = n;
+            pair_score[k] = (float)best.v;
+        }
+        __syncwarp();
+    }
+}
+
+// Links of every pair with s >= thr, in row order, compacted at out_off.
+__global__ void __launch_bounds__(32 * kUcWarps)
+uc_count_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, float thr, UcScratch W, int32_t *kept) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp0; k < n_pairs; k += nwarps) {
+        const int N = geom[k].n, n = W.n_match[k];
+        const float *ls = W.ls + W.link_off[k] + N - n;
+        int c = 0;
+        for (int x = lane; x < n; x += 32) c += ls[x] >= thr;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(kFull, c, off);
+        if (lane == 0) kept[k] = c;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kUcWarps)
+uc_copy_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, float thr, UcScratch W, const int64_t *out_off,
+               int32_t *out_i, int32_t *out_j, float *out_s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = warp0; k < n_pairs; k += nwarps) {
+        const int N = geom[k].n, n = W.n_match[k];
+        const int64_t base = W.link_off[k] + N - n;
+        int64_t to = out_off[k];
+        for (int x0 = 0; x0 < n; x0 += 32) {
+            const int x = x0 + lane;
+            const float s = x < n ? W.ls[base + x] : 0.0f;
+            const bool keep = x < n && s >= thr;
+            const uint32_t m = __ballot_sync(kFull, keep);
+            if (keep) {
+                const int64_t o = to + __popc(m & ((1u << lane) - 1u));
+                out_i[o] = W.li[base + x];
+                out_j[o] = W.lj[base + x];
+                out_s[o] = s;
+            }
+            to += __popc(m);
+        }
+    }
+}
+
+int uc_grid(int64_t n_pairs, int n_sms) {
+    int64_t b = (n_pairs + kUcWarps - 1) / kUcWarps;
+    const int64_t cap = (int64_t)n_sms * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
+                                 int64_t n_pairs, const DevParams &P, const uint8_t *counts, const UcScratch &W,
+                                 float *pair_score, const int64_t *out_off_scan_in, int32_t *kept, int n_sms,
+                                 cudaStream_t st) {
+    (void)out_off_scan_in;
+    if (n_pairs == 0) return cudaSuccess;
+    unconstrained_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(src, tgt, geom, order, n_pairs, P, counts,
+                                                                           W, pair_score);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uc_count_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(geom, n_pairs, P.thr, W, kept);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unconstrained_copy(const PairGeom *geom, int64_t n_pairs, float thr, const UcScratch &W,
+                                      const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_s, int n_sms,
+                                      cudaStream_t st) {
+    if (n_pairs == 0) return cudaSuccess;
+    uc_copy_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(geom, n_pairs, thr, W, out_off, out_i, out_j,
+                                                                     out_s);
+    return cudaGetLastError();
+}
+
+}  // namespace gbm

@@ -94,6 +94,10 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "softnw_bwd": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_SoftOpts), C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_unconstrained_workspace_size": (C.c_int64, [C.c_void_p]),
+    "mine_unconstrained_link_capacity": (C.c_int64, [C.c_void_p]),
+    "mine_align_unconstrained": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.c_void_p, C.POINTER(_Out),
+                                           C.c_void_p]),
     "mine_align_pair_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                          C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
@@ -326,6 +330,28 @@ class Plan:
                "mine_link_gold_counts")
         return res
 
+    def align_unconstrained(self, params: MineParams, counts, out=None, ws=None, stream=None):
+        """The unconstrained (Yalign A*) aligner from counts
+        (mine_align_unconstrained): per pair the matched cells with s >= thr
+        in source order and the FP64 score."""
+        import torch
+        L = lib()
+        cap = max(int(L.mine_unconstrained_link_capacity(self._h)), 1)
+        if out is None:
+            out = {"link_off": torch.empty(self.n_pairs + 1, dtype=torch.int64, device="cuda"),
+                   "link_i": torch.empty(cap, dtype=torch.int32, device="cuda"),
+                   "link_j": torch.empty(cap, dtype=torch.int32, device="cuda"),
+                   "link_s": torch.empty(cap, dtype=torch.float32, device="cuda"),
+                   "pair_score": torch.empty(max(self.n_pairs, 1), dtype=torch.float32, device="cuda")}
+        if ws is None:
+            ws = torch.empty(int(L.mine_unconstrained_workspace_size(self._h)), dtype=torch.uint8, device="cuda")
+        s = self._out_struct(out, out["link_i"].numel())
+        p = params.c()
+        _check(L.mine_align_unconstrained(self._h, C.byref(p), _ptr(counts), _ptr(ws), C.byref(s), _stream(stream)),
+               "mine_align_unconstrained")
+        out["_ws"] = ws
+        return out
+
     def mine(self, params: MineParams, out=None, stream=None):
         """The whole hot path (counts, similarity, alignment, threshold)."""
         out = out if out is not None else self.new_output()
@@ -428,6 +454,18 @@ class BiPlan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def noalloc_result(n_links: int, pair_score: float):
+    """The (n_links, pair_score) that mine_align_pair_noalloc wrote, checked:
+    n_links == -1 (with a NaN score) says that a bounded wait for the staged
+    counts gave up on the device, so the links are invalid -- raised as
+    MINE_ETIMEOUT; anything else is returned unchanged."""
+    if int(n_links) == -1:
+        raise MinerError(MINE_ETIMEOUT, "mine_align_pair_noalloc (device-side staging wait)")
+    if int(n_links) < 0:
+        raise MinerError(MINE_EINVAL, f"mine_align_pair_noalloc: n_links = {int(n_links)}")
+    return int(n_links), float(pair_score)
 
 
 def links_per_pair(out, n_pairs):

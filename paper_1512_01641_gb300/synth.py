@@ -168,6 +168,18 @@ def make_dictionary(rng: np.random.Generator, v_src: int, v_tgt: int,
     return Dictionary(v_src, v_tgt, off.astype(np.int32), tgt.astype(np.int32))
 
 
+def thin_dictionary(dic: Dictionary, p_drop: float, seed: int) -> Dictionary:
+    """A copy of the dictionary with each entry dropped with probability
+    p_drop (lists may become empty): the incomplete dictionary a miner works
+    with when the data were made with the full one."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    keep = rng.random(len(dic.tgt)) >= p_drop
+    owner = np.repeat(np.arange(dic.v_src), np.diff(dic.off.astype(np.int64)))
+    off = np.zeros(dic.v_src + 1, np.int64)
+    np.cumsum(np.bincount(owner[keep], minlength=dic.v_src), out=off[1:])
+    return Dictionary(dic.v_src, dic.v_tgt, off.astype(np.int32), dic.tgt[keep].astype(np.int32))
+
+
 def lognormal_sizes(rng: np.random.Generator, n: int, median: float = 60.0,
                     sigma: float = 0.8, lo: int = 5, hi: int = 800) -> np.ndarray:
     x = rng.lognormal(mean=np.log(median), sigma=sigma, size=n)

@@ -169,21 +169,28 @@ def adam_tune(train: TuneData, held_out: TuneData, steps: int = 200, lr: float =
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     ev = held_out.f1(miner.params_from_theta(theta))
-    return TuneResult("adam", theta.tolist(), None, ev, secs,
+    if use_mb:
+        al.select(None)
+    train_f1 = train.f1(miner.params_from_theta(theta))["f1"]  # after the timed region
+    return TuneResult("adam", theta.tolist(), train_f1, ev, secs,
                       {"steps": steps, "lr": lr, "gamma": gamma, "tau": tau,
                        "batch_pairs": batch_pairs if use_mb else n,
                        "loss_first": losses[0], "loss_last": losses[-1]})
 
 
-def compare(train_batch, eval_batch, steps=200, grid=GRID, gamma=0.1, random_trials=343) -> dict:
+def compare(train_batch, eval_batch, steps=200, grid=GRID, gamma=0.1, random_trials=343, theta0=THETA0) -> dict:
     """Grid search vs the paper's random search vs Adam on the same GPU, all
-    evaluated on held-out pairs."""
+    started from theta0 (the grid and the random search keep its weights
+    w) and evaluated on held-out pairs."""
+    theta0 = np.asarray(theta0, np.float64)
     train, held = TuneData(train_batch), TuneData(eval_batch)
-    base = held.f1(miner.params_from_theta(THETA0))
-    g = grid_search(train, held, grid=grid)
-    r = random_search(train, held, trials=random_trials)
-    a = adam_tune(train, held, steps=steps, gamma=gamma)
-    return {"baseline_eval": base, "grid": g.as_dict(), "random": r.as_dict(), "adam": a.as_dict(),
+    base = held.f1(miner.params_from_theta(theta0))
+    base_train = train.f1(miner.params_from_theta(theta0))["f1"]
+    g = grid_search(train, held, theta0=theta0, grid=grid)
+    r = random_search(train, held, trials=random_trials, theta0=theta0)
+    a = adam_tune(train, held, steps=steps, gamma=gamma, theta0=theta0)
+    return {"theta0": theta0.tolist(), "baseline_eval": base, "baseline_train_f1": base_train,
+            "grid": g.as_dict(), "random": r.as_dict(), "adam": a.as_dict(),
             "f1_gap_points": 100 * (a.eval["f1"] - g.eval["f1"]),
             "speedup_vs_grid": g.seconds / a.seconds if a.seconds > 0 else None,
             "train_pairs": train_batch.n_pairs, "eval_pairs": eval_batch.n_pairs}

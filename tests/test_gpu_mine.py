@@ -56,8 +56,18 @@ def _dense_translation_batch():
     return synth.make_batch(79, 8, dic=dic, size_median=70, size_hi=160)
 
 
+def _fanout_batch(kmin, kmax, seed):
+    # every source id with kmin..kmax translations: fan-out 4 fills the tile
+    # kernel's fixed-width records (row groups of 16 and 8 rows), fan-out 6 is
+    # counted by the strip kernel instead
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dic = synth.make_dictionary(rng, 2000, 2000, kmin=kmin, kmax=kmax)
+    return synth.make_batch(seed + 1, 10, dic=dic, size_median=50, size_hi=140)
+
+
 BATCHES = {"single_40x45": synth.single_pair, "edges": _edge_batch, "mixed": _mixed_batch,
-           "long_sentences": _long_sentence_batch, "dense_translations": _dense_translation_batch}
+           "long_sentences": _long_sentence_batch, "dense_translations": _dense_translation_batch,
+           "fanout_4": lambda: _fanout_batch(4, 4, 81), "fanout_1_to_6": lambda: _fanout_batch(1, 6, 83)}
 
 
 @pytest.fixture(scope="module", params=list(BATCHES))

@@ -32,3 +32,35 @@ def test_anchor_lists_are_sorted_distinct_and_in_range():
         for s in range(n):
             x = a.ids[a.sent_off[s]:a.sent_off[s + 1]]
             assert np.all(np.diff(x) > 0)
+
+
+def test_noalloc_timeout_sentinel_is_reported():
+    # the allocation-free entry point has no plan to record a device-side
+    # timeout: it writes n_links = -1 and a NaN score, which the binding
+    # turns into MINE_ETIMEOUT
+    import math
+
+    import pytest
+
+    from paper_1512_01641_gb300 import miner
+    assert miner.noalloc_result(3, 1.25) == (3, 1.25)
+    assert miner.noalloc_result(0, -0.6) == (0, -0.6)
+    with pytest.raises(miner.MinerError) as e:
+        miner.noalloc_result(-1, math.nan)
+    assert e.value.code == miner.MINE_ETIMEOUT
+    with pytest.raises(miner.MinerError) as e:
+        miner.noalloc_result(-2, 0.0)
+    assert e.value.code == miner.MINE_EINVAL
+
+
+def test_thin_dictionary_keeps_a_share_of_each_list():
+    rng = np.random.Generator(np.random.PCG64(3))
+    dic = synth.make_dictionary(rng, 3000, 3000)
+    thin = synth.thin_dictionary(dic, 0.3, seed=4)
+    assert thin.off[0] == 0 and thin.off[-1] == len(thin.tgt) and np.all(np.diff(thin.off) >= 0)
+    kept = len(thin.tgt) / len(dic.tgt)
+    assert 0.66 < kept < 0.74
+    for v in rng.choice(3000, 50, replace=False):  # a subset of the original list, still sorted
+        a, b = set(dic.translations(v).tolist()), thin.translations(v).tolist()
+        assert set(b) <= a and b == sorted(b)
+    assert np.array_equal(synth.thin_dictionary(dic, 0.3, seed=4).tgt, thin.tgt)
