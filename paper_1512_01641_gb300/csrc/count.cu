@@ -590,7 +590,7 @@ count_strip_kernel(DevCorpus src, DevCorpus tgt, DevDict dict, const PairGeom *_
 //     writes 16 bytes: straight into the blocked layout (one 2 KB tile per
 //     32 x 32 block, row r at byte 64 r) or, row-major, through a tile.
 // The counts are the same integers as the other count kernels compute.
-constexpr int kTileWarps = 4;
+constexpr int kTileWarps = 8;
 constexpr int kTileThreads = 32 * kTileWarps;
 constexpr int kTileSlots = 1 << kStripLogSlots;  // 2048
 constexpr int kTileZero = kTileSlots;            // CM index that stays 0
@@ -605,7 +605,7 @@ struct alignas(16) TileSmem {
     uint32_t cm[kTileSlots + 4];    // column masks of the current block; cm[kTileZero] stays 0
     uint2 prec[kPosCap];            // per source position: byte offsets into cm of its translations' slots
     uint32_t tg[kTokCap + 8];       // staged target tokens, replaced in place by their row masks
-    uint32_t part[kTileWarps][8][32];  // per warp: 4 ms planes, 4 mt planes; then the output tile
+    uint32_t part[kTileWarps][4][32];  // per warp: 4 planes of its quarter counters; then the output tile
     uint8_t mt_t[32][36];           // mt bytes [column][row]
     uint8_t colid[kTokCap];
     uint8_t rowid[kPosCap];
@@ -690,7 +690,7 @@ __global__ void dict4_kernel(DevDict d, int32_t v_src, int4 *__restrict__ out) {
 }
 
 template <bool BLOCKED>
-__global__ void __launch_bounds__(kTileThreads, 5)
+__global__ void __launch_bounds__(kTileThreads, 4)
 count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, const PairGeom *__restrict__ geom,
                   const CountStripItem *__restrict__ items, int64_t n_items, int32_t *queue, bool bulk_ok,
                   uint8_t *__restrict__ counts, uint32_t *status) {
@@ -745,8 +745,8 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
             }
             for (int x = tid; x < kTileSlots / 2; x += kTileThreads)
                 reinterpret_cast<int4 *>(sm.ent)[x] = make_int4(kEmpty, 0, kEmpty, 0);
-            // row of every position: warp w writes positions 8w .. 8w+7 of each row
-            for (int t = 8 * warp; t < min(8 * warp + 8, my_len); ++t) sm.rowid[prow + t] = (uint8_t)lane;
+            // row of every position: warp w writes positions 4w .. 4w+3 of each row
+            for (int t = 4 * warp; t < min(4 * warp + 4, my_len); ++t) sm.rowid[prow + t] = (uint8_t)lane;
             if (tid == 0) sm.n_ent = 0;
             __syncthreads();
 #pragma unroll
@@ -812,7 +812,7 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                 const int sh = stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.tg, &sm.bar, bulk_ok, lane, bulk_b);
                 if (lane == 0) sm.tsh = sh | (bulk_b ? 1 << 30 : 0);
             };
-            if (warp == 3) {
+            if (warp == kTileWarps - 1) {
                 offsets(0);
                 stage_block(0);
                 offsets(1);
@@ -820,7 +820,11 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
             fence_proxy_async();
             __syncthreads();  // table, position records and block 0's staging complete
 
-            const int lq0 = (warp * my_len) >> 2, lq1 = ((warp + 1) * my_len) >> 2;  // this warp's quarter of the row
+            // warps 0-3 count ms, warps 4-7 mt, each over a quarter of every row's
+            // positions / every column's tokens
+            const bool ms_warp = warp < 4;
+            const int quarter = warp & 3;
+            const int lq0 = (quarter * my_len) >> 2, lq1 = ((quarter + 1) * my_len) >> 2;
             for (int jb = 0; jb < nblk; ++jb) {
                 const int c0 = jb * 32;
                 const int nc = min(32, g.m - c0);
@@ -868,35 +872,31 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                 __syncthreads();
                 // quarter passes
                 {
-                    BitCounter<4> mtq, msq;
-                    mtq.clear();
-                    msq.clear();
-                    if (lane < nc) {
+                    BitCounter<4> q4;
+                    q4.clear();
+                    if (!ms_warp && lane < nc) {
                         const int t0 = sm.ctpre[lane];
                         const int t1 = lane < 31 ? sm.ctpre[lane + 1] : n_tok;
                         const int L = t1 - t0;
-                        acc_words(mtq, tg + t0 + ((warp * L) >> 2), (((warp + 1) * L) >> 2) - ((warp * L) >> 2));
+                        acc_words(q4, tg + t0 + ((quarter * L) >> 2), (((quarter + 1) * L) >> 2) - ((quarter * L) >> 2));
                     }
                     int p = prow + lq0;
-                    const int pe = prow + lq1;
+                    const int pe = ms_warp ? prow + lq1 : p;
                     const unsigned char *cmb = reinterpret_cast<const unsigned char *>(sm.cm);
                     auto cmw = [&](uint32_t off) { return *reinterpret_cast<const uint32_t *>(cmb + off); };
                     for (; p + 2 <= pe; p += 2) {
                         const uint2 a = sm.prec[p], b = sm.prec[p + 1];
                         const uint32_t ha = cmw(a.x & 0xFFFFu) | cmw(a.x >> 16) | cmw(a.y & 0xFFFFu) | cmw(a.y >> 16);
                         const uint32_t hb = cmw(b.x & 0xFFFFu) | cmw(b.x >> 16) | cmw(b.y & 0xFFFFu) | cmw(b.y >> 16);
-                        msq.add(ha);
-                        msq.add(hb);
+                        q4.add(ha);
+                        q4.add(hb);
                     }
                     if (p < pe) {
                         const uint2 a = sm.prec[p];
-                        msq.add(cmw(a.x & 0xFFFFu) | cmw(a.x >> 16) | cmw(a.y & 0xFFFFu) | cmw(a.y >> 16));
+                        q4.add(cmw(a.x & 0xFFFFu) | cmw(a.x >> 16) | cmw(a.y & 0xFFFFu) | cmw(a.y >> 16));
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        sm.part[warp][k][lane] = msq.p[k];
-                        sm.part[warp][4 + k][lane] = mtq.p[k];
-                    }
+                    for (int k = 0; k < 4; ++k) sm.part[warp][k][lane] = q4.p[k];
                 }
                 fence_proxy_async();  // this block's accesses to tg come before the next block's copy into it
                 __syncthreads();
@@ -907,35 +907,36 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     if (tid + kTileThreads * k < n_tok) sm.cm[hit[k]] = 0u;
                 }
                 // the next block's tokens go out now (tg, ctpre, colid are free)
-                if (warp == 3 && jb + 1 < nblk) {
+                if (warp == kTileWarps - 1 && jb + 1 < nblk) {
                     stage_block(jb + 1);
                     offsets(jb + 2);
                 }
-                // combine the quarters; expand this warp's quarter of the bytes
-                uint32_t msw0, msw1;
+                // combine the quarters; expand a quarter of the bytes: ms warps
+                // columns 8q .. 8q+7 of row `lane`, mt warps rows 8q .. 8q+7 of
+                // column `lane` (into the transpose tile)
+                uint32_t msw0 = 0u, msw1 = 0u;
                 {
+                    const int base = ms_warp ? 0 : 4;
                     uint32_t q[4][4];
 #pragma unroll
                     for (int w = 0; w < 4; ++w)
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) q[w][k] = sm.part[w][k][lane];
-                    uint32_t ms5[5];
-                    add4x4(q[0], q[1], q[2], q[3], ms5);
-                    msw0 = nibble_bytes(ms5, 2 * warp);
-                    msw1 = nibble_bytes(ms5, 2 * warp + 1);
-#pragma unroll
-                    for (int w = 0; w < 4; ++w)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) q[w][k] = sm.part[w][4 + k][lane];
-                    uint32_t mt5[5];
-                    add4x4(q[0], q[1], q[2], q[3], mt5);
-                    *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * warp]) = nibble_bytes(mt5, 2 * warp);
-                    *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * warp + 4]) = nibble_bytes(mt5, 2 * warp + 1);
+                        for (int k = 0; k < 4; ++k) q[w][k] = sm.part[base + w][k][lane];
+                    uint32_t c5[5];
+                    add4x4(q[0], q[1], q[2], q[3], c5);
+                    const uint32_t b0 = nibble_bytes(c5, 2 * quarter), b1 = nibble_bytes(c5, 2 * quarter + 1);
+                    if (ms_warp) {
+                        msw0 = b0;
+                        msw1 = b1;
+                    } else {
+                        *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * quarter]) = b0;
+                        *reinterpret_cast<uint32_t *>(&sm.mt_t[lane][8 * quarter + 4]) = b1;
+                    }
                 }
                 __syncthreads();
-                // interleave (ms, mt) for row `lane`, columns 8w .. 8w+7
-                {
-                    const int c = 8 * warp;
+                // interleave (ms, mt) for row `lane`, columns 8q .. 8q+7 (ms warps)
+                if (ms_warp) {
+                    const int c = 8 * quarter;
                     const uint32_t mA = (uint32_t)sm.mt_t[c][lane] | ((uint32_t)sm.mt_t[c + 1][lane] << 8) |
                                         ((uint32_t)sm.mt_t[c + 2][lane] << 16) | ((uint32_t)sm.mt_t[c + 3][lane] << 24);
                     const uint32_t mB = (uint32_t)sm.mt_t[c + 4][lane] | ((uint32_t)sm.mt_t[c + 5][lane] << 8) |
@@ -945,14 +946,14 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     if (BLOCKED) {
                         if (rv) {
                             uint8_t *tile = counts + g.tb_off * 64 + ((int64_t)item.strip * nblk + jb) * 2048;
-                            *reinterpret_cast<uint4 *>(tile + 64 * lane + 16 * warp) = o;
+                            *reinterpret_cast<uint4 *>(tile + 64 * lane + 16 * quarter) = o;
                         }
                     } else {
                         uint32_t *ot = &sm.part[0][0][0];  // [32][17] words: the block's rows, interleaved
-                        ot[17 * lane + 4 * warp] = o.x;
-                        ot[17 * lane + 4 * warp + 1] = o.y;
-                        ot[17 * lane + 4 * warp + 2] = o.z;
-                        ot[17 * lane + 4 * warp + 3] = o.w;
+                        ot[17 * lane + 4 * quarter] = o.x;
+                        ot[17 * lane + 4 * quarter + 1] = o.y;
+                        ot[17 * lane + 4 * quarter + 2] = o.z;
+                        ot[17 * lane + 4 * quarter + 3] = o.w;
                     }
                 }
                 if (!BLOCKED) {
@@ -960,8 +961,8 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     const uint32_t *ot = &sm.part[0][0][0];
                     uint8_t *out_strip = counts + 2 * (g.cell_off + (int64_t)r0 * g.m + c0);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int i = 8 * warp + q;
+                    for (int q = 0; q < 32 / kTileWarps; ++q) {
+                        const int i = (32 / kTileWarps) * warp + q;
                         if (i >= g_lo && i < g_hi && lane < nc) {
                             const uint32_t wd = ot[17 * i + (lane >> 1)];
                             reinterpret_cast<uint16_t *>(out_strip + 2 * (int64_t)i * g.m)[lane] =
