@@ -640,6 +640,29 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
     }
 }
 
+// Row and column of the cells a thread visits in a chunk (cells c0 + t,
+// c0 + t + 256, ... of a pair with M columns): one 32-bit division per thread
+// and chunk, then constant steps; the sentence lengths of the current row and
+// column are kept (the row changes rarely).
+struct CellWalk {
+    int i, j, si, sj;  // current cell, step per visit (256 = si M + sj)
+    __device__ __forceinline__ CellWalk(int64_t c0, int t, int M) {
+        const uint32_t i0 = (uint32_t)(c0 / M), j0 = (uint32_t)(c0 - (int64_t)i0 * M) + (uint32_t)t;
+        i = (int)(i0 + j0 / (uint32_t)M);
+        j = (int)(j0 % (uint32_t)M);
+        si = 256 / M;
+        sj = 256 % M;
+    }
+    __device__ __forceinline__ void next(int M) {
+        i += si;
+        j += sj;
+        if (j >= M) {
+            j -= M;
+            ++i;
+        }
+    }
+};
+
 // Per-cell work of the loss: gate, clamped P and BCE (summed per chunk), or
 // (WANT_U) the tangent direction u = dL/dE of the backward.  One block per
 // chunk of kSoftChunk cells; the first chunk of a pair also sums V(N,M).
@@ -660,11 +683,17 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
         const int64_t cells = (int64_t)g.n * g.m;
         const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
         float acc = 0.0f;  // at most kSoftChunk / 256 terms per thread
-        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            const int i = (int)(c / g.m), j = (int)(c - (int64_t)i * g.m);
+        CellWalk cw(ch.c0, threadIdx.x, g.m > 0 ? g.m : 1);
+        int row_i = -1;
+        SimRow srow{};
+        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x, cw.next(g.m)) {
+            if (cw.i != row_i) {
+                row_i = cw.i;
+                srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
+            }
             const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + c];
-            const float sv = similarity(q.x, q.y, sim_row((int)(src.sent[sb + i + 1] - src.sent[sb + i]), P),
-                                        sim_col((int)(tgt.sent[tb + j + 1] - tgt.sent[tb + j]), P), C.K);
+            const float sv = similarity(q.x, q.y, srow, sim_col((int)(tgt.sent[tb + cw.j + 1] - tgt.sent[tb + cw.j]), P),
+                                        C.K);
             float G, bce;
             const float lp = cell_dldp(W.E[g.cell_off + c], sv, gold[g.cell_off + c], C, G, WANT_U ? nullptr : &bce);
             if (WANT_U)
@@ -716,12 +745,17 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
         const int64_t cells = (int64_t)g.n * g.m;
         const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
         float gr[7] = {0, 0, 0, 0, 0, 0, 0};  // at most kSoftChunk / 256 terms per thread
-        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            const int i = (int)(c / g.m), j = (int)(c - (int64_t)i * g.m);
-            const int ls = (int)(src.sent[sb + i + 1] - src.sent[sb + i]);
-            const int lt = (int)(tgt.sent[tb + j + 1] - tgt.sent[tb + j]);
+        CellWalk cw(ch.c0, threadIdx.x, g.m > 0 ? g.m : 1);
+        int row_i = -1;
+        SimRow srow{};
+        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x, cw.next(g.m)) {
+            if (cw.i != row_i) {
+                row_i = cw.i;
+                srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
+            }
+            const SimCol scol = sim_col((int)(tgt.sent[tb + cw.j + 1] - tgt.sent[tb + cw.j]), P);
             const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + c];
-            const float sv = similarity(q.x, q.y, sim_row(ls, P), sim_col(lt, P), C.K);
+            const float sv = similarity(q.x, q.y, srow, scol, C.K);
             const float Es = W.E[g.cell_off + c];
             const float Hu = W.U[g.cell_off + c];
             if (hvp) hvp[g.cell_off + c] = Hu;
@@ -731,8 +765,13 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
             const float direct = __fmul_rn(__fmul_rn(lp, Es), gg);  // dL/ds through the gate
             const float dlds = __fadd_rn(Hu, direct);
             const float dz = __fmul_rn(dlds, __fmul_rn(sv, __fsub_rn(1.0f, sv)));
+            // the features through the rows' and columns' reciprocals (a rounding
+            // more than the IEEE quotients: far below the gradient's tolerance)
             float f[4];
-            features(q.x, q.y, ls, lt, f);
+            f[0] = __fmul_rn(small_int_float(q.x), srow.rlen);
+            f[1] = __fmul_rn(small_int_float(q.y), scol.rlen);
+            f[3] = fminf(__fmul_rn(srow.len, scol.rlen), __fmul_rn(scol.len, srow.rlen));
+            f[2] = __fsub_rn(1.0f, f[3]);
 #pragma unroll
             for (int q4 = 0; q4 < 4; ++q4) gr[q4] = __fmaf_rn(dz, f[q4], gr[q4]);
             gr[4] = __fadd_rn(gr[4], dz);
