@@ -45,6 +45,7 @@ struct PairGeom {
     int64_t flag_off;  // first tile flag (nstrips * nchunk ints), -1 if one warp does the pair
     int32_t n, m;      // sentence counts
     int64_t soft_off;  // first float of the pair's soft-alignment checkpoint rows (nstrips * M)
+    int64_t ckw_off;   // first float of the pair's soft window checkpoints (nstrips * soft_ckw_floats(M))
     int32_t cw;        // fill column chunk width (multiple of 32)
     int32_t nchunk;    // number of column chunks
 };
@@ -200,12 +201,14 @@ struct SoftScratch {
     float *U;             // per cell: u = dL/dE, replaced by H u in the backward
     float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
     float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
-    float *sbuf;          // per-warp strip buffers
-    int64_t sbuf_stride;  // floats per warp
+    float *ckw;           // per strip: the sweep state at the start of every window
     int64_t items_cap, chunks_cap, ctr_cap;
 };
 
 int64_t soft_warps(int n_sms);
+// Floats of one strip's window checkpoints in a pair of M target sentences
+// (the adjoint sweeps recompute 8-step windows from them).
+__host__ __device__ inline int64_t soft_ckw_floats(int M) { return 128 * (32 * ((M + 31) / 32 + 1) / 8); }
 
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                                 const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,

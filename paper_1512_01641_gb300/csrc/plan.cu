@@ -159,6 +159,7 @@ struct mine_plan {
     int32_t *pair_order = nullptr;
     int64_t soft_rows = 0;              // sum over pairs of nstrips * M
     int64_t soft_strips = 0;            // sum over pairs of nstrips
+    int64_t soft_ckw = 0;               // floats of the soft window checkpoints
     int32_t max_m = 0;
     PlanKnobs knobs;
     PairGeom *geom = nullptr;
@@ -325,6 +326,7 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
     p->cell_off_h.assign(n + 1, 0);
     p->soft_rows = 0;
     p->soft_strips = 0;
+    p->soft_ckw = 0;
     p->max_m = 0;
     int64_t cell = 0, link = 0, flags = 0;
     tbw = hrow = vcol = 0;
@@ -340,6 +342,8 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
         g.hrow_off = hrow;
         g.vcol_off = vcol;
         g.soft_off = p->soft_rows;
+        g.ckw_off = p->soft_ckw;
+        p->soft_ckw += ((g.n + 31) / 32) * soft_ckw_floats(g.m);
         p->soft_rows += ((g.n + 31) / 32) * (int64_t)g.m;
         p->soft_strips += (g.n + 31) / 32;
         p->max_m = std::max(p->max_m, g.m);
@@ -794,7 +798,7 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct SoftLayout {
-    int64_t partial, vpart, queue, items, chunks, prog1, prog2, E, U, ckv, ckt, qrow, qtrow, sbuf, total, sbuf_stride;
+    int64_t partial, vpart, queue, items, chunks, prog1, prog2, E, U, ckv, ckt, qrow, qtrow, ckw, total;
     int64_t items_cap, chunks_cap, ctr_cap;
 };
 
@@ -831,9 +835,8 @@ static SoftLayout soft_layout(const mine_plan *p) {
     o = align_up(o + rows, 256);
     L.qtrow = o;
     o = align_up(o + rows, 256);
-    L.sbuf_stride = 6 * (int64_t)(p->max_m + 31) * 32;
-    L.sbuf = o;
-    o = align_up(o + soft_warps(p->n_sms) * L.sbuf_stride * 4, 256);
+    L.ckw = o;
+    o = align_up(o + std::max<int64_t>(p->soft_ckw, 1) * 4, 256);
     L.total = o;
     return L;
 }
@@ -855,8 +858,7 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     W.ckt = reinterpret_cast<float *>(b + L.ckt);
     W.qrow = reinterpret_cast<float *>(b + L.qrow);
     W.qtrow = reinterpret_cast<float *>(b + L.qtrow);
-    W.sbuf = reinterpret_cast<float *>(b + L.sbuf);
-    W.sbuf_stride = L.sbuf_stride;
+    W.ckw = reinterpret_cast<float *>(b + L.ckw);
     W.items_cap = L.items_cap;
     W.chunks_cap = L.chunks_cap;
     W.ctr_cap = L.ctr_cap;

@@ -50,6 +50,7 @@ namespace gbm {
 namespace {
 
 constexpr int kSoftWarps = 4;
+constexpr int kWin = 8;  // steps of a window of the adjoint sweep's recompute
 constexpr float kLn2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float lg2_approx(float x) {
@@ -71,7 +72,8 @@ struct SoftCtx {
     float *U;              // pair's tangent direction u = dL/dE, then H u
     SimCol *colv;          // shared: column constants of the block being prepared
     float (*svb)[32][32];  // shared: similarities of the current and previous block [2][row][col]
-    float (*ub)[32][32];   // shared: u of the current and previous block
+    float (*ub)[32][32];   // shared: u of the current and previous block (TAN)
+    float (*wb)[kWin][32]; // shared: the recomputed window's per-cell weights [component][step][lane]
     int64_t wait_limit;    // bounded spins of a strip wait
     uint32_t *status;      // timeout bit
     bool failed;           // a wait of the current item gave up
@@ -160,29 +162,60 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv
     __syncwarp();
 }
 
-// Forward sweep of strip s (rows 32s..32s+31, lane = row, skewed by lane).
+// One cell of the forward recurrence (lane's row, column j): the soft max
+// of the three candidates, its weights and the next DOWN / RIGHT differences
+// (and, TAN, the tangents along u).  Tangent: with the weights summing to
+// one, every difference the sweeps need is a weighted sum of pairwise
+// candidate differences, so nothing cancels when one weight is close to 1 (a
+// saturated alignment); e.g. u - D' = wu (u - A') + wl (u - B').  cd, cu, cl:
+// the coefficients c_k - D' of the weight tangents.
+template <bool TAN>
+__device__ __forceinline__ void soft_cell(const SoftCtx &C, int lane, int j, float a_up, float at_up, float &b,
+                                          float &bt, float &a_down, float &at_down, float &wd, float &wu, float &wl,
+                                          float &cd, float &cu, float &cl) {
+    const int bb = (j >> 5) & 1, c = j & 31;
+    const float sv = C.svb[bb][lane][c];
+    const float D = soft3(sv, a_up, b, C, wd, wu, wl);
+    const float e = __fsub_rn(D, C.two_p);
+    const float nb2 = __fsub_rn(e, a_up);
+    a_down = __fsub_rn(e, b);
+    cd = cu = cl = 0.0f;
+    if (TAN) {
+        const float uu = C.ub[bb][lane][c];
+        const float dua = __fsub_rn(uu, at_up), dub = __fsub_rn(uu, bt), dab = __fsub_rn(at_up, bt);
+        cd = __fmaf_rn(wu, dua, __fmul_rn(wl, dub));
+        cu = __fmaf_rn(wl, dab, -__fmul_rn(wd, dua));
+        cl = -__fmaf_rn(wd, dub, __fmul_rn(wu, dab));
+        at_down = __fmaf_rn(wd, dub, __fmul_rn(wu, dab));  // D' - B'
+        bt = __fmaf_rn(wd, dua, -__fmul_rn(wl, dab));      // D' - A'
+    }
+    b = nb2;
+}
+
+// Forward (value) sweep of strip s (rows 32s..32s+31, lane = row, skewed by
+// lane).
 //   TAN:   also run the tangent along u (needs U of the pair)
-//   STORE: write the per-cell quantities the reverse sweep needs into sbuf,
-//          anti-diagonal major: sbuf[k][t][lane] for step t, component k
 // ck*_top: the strip above's checkpoint row (UP candidates of row 32s-1);
 // ck*_out: this strip's checkpoint row (written by the last lane), may be null.
+// ckw_out: the state of every lane at the start of every kWin-step window
+// (b, a_down and, TAN, bt, at_down; 128 floats per window), from which the
+// adjoint sweep recomputes the strip a window at a time.
 // vlast (may be null): receives the DOWN outputs of row N-1, V(N,j) - V(N,j-1) - p,
 // from which V(N,M) is summed in FP64 outside the sweep.
 // Split pairs (strips on different warps): wait_top (may be null) counts the
 // checkpoint columns the strip above has published, pub (may be null)
 // receives this strip's count (lane 31 writes column j at step j + 31, so
 // after block jb columns 0..32 jb are out).
-template <bool TAN, bool STORE>
+template <bool TAN>
 __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *__restrict__ ckv_top,
                                                const float *__restrict__ ckt_top, float *__restrict__ ckv_out,
-                                               float *__restrict__ ckt_out, float *__restrict__ sbuf,
+                                               float *__restrict__ ckt_out, float *__restrict__ ckw_out,
                                                float *__restrict__ vlast, const int32_t *wait_top = nullptr,
                                                int32_t *pub = nullptr) {
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
     C.row = sim_row(rv ? (int)(C.ssent[r + 1] - C.ssent[r]) : 1, C.P);
-    const int64_t plane = (int64_t)(C.M + 31) * 32;
     const int nb = (C.M + 31) >> 5;
     float b = -C.two_p, a_down = 0.0f;
     float bt = 0.0f, at_down = 0.0f;
@@ -197,6 +230,15 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
 #pragma unroll 4
         for (int u = 0; u < 32; ++u) {
             const int t = 32 * jb + u;
+            if (ckw_out && (u % kWin) == 0) {
+                float *q = ckw_out + (int64_t)(t / kWin) * 128 + lane;
+                q[0] = b;
+                q[32] = a_down;
+                if (TAN) {
+                    q[64] = bt;
+                    q[96] = at_down;
+                }
+            }
             float a_up = __shfl_up_sync(kFull, a_down, 1);
             float at_up = TAN ? __shfl_up_sync(kFull, at_down, 1) : 0.0f;
             const float h0 = __shfl_sync(kFull, hv, u);
@@ -207,39 +249,8 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
             }
             const int j = t - lane;
             if (rv && j >= 0 && j < C.M) {
-                const int bb = (j >> 5) & 1, c = j & 31;
-                const float sv = C.svb[bb][lane][c];
-                float wd, wu, wl;
-                const float D = soft3(sv, a_up, b, C, wd, wu, wl);
-                const float e = __fsub_rn(D, C.two_p);
-                const float nb2 = __fsub_rn(e, a_up);
-                a_down = __fsub_rn(e, b);
-                // tangent: with the weights summing to one, every difference the
-                // sweeps need is a weighted sum of pairwise candidate differences,
-                // so nothing cancels when one weight is close to 1 (a saturated
-                // alignment); e.g. u - D' = wu (u - A') + wl (u - B').
-                float cd = 0.0f, cu = 0.0f, cl = 0.0f;
-                if (TAN) {
-                    const float uu = C.ub[bb][lane][c];
-                    const float dua = __fsub_rn(uu, at_up), dub = __fsub_rn(uu, bt), dab = __fsub_rn(at_up, bt);
-                    cd = __fmaf_rn(wu, dua, __fmul_rn(wl, dub));
-                    cu = __fmaf_rn(wl, dab, -__fmul_rn(wd, dua));
-                    cl = -__fmaf_rn(wd, dub, __fmul_rn(wu, dab));
-                    at_down = __fmaf_rn(wd, dub, __fmul_rn(wu, dab));  // D' - B'
-                    bt = __fmaf_rn(wd, dua, -__fmul_rn(wl, dab));      // D' - A'
-                }
-                b = nb2;
-                if (STORE) {
-                    float *q = sbuf + (int64_t)t * 32 + lane;
-                    q[0] = wd;
-                    q[plane] = wu;
-                    q[2 * plane] = wl;
-                    if (TAN) {
-                        q[3 * plane] = cd;
-                        q[4 * plane] = cu;
-                        q[5 * plane] = cl;
-                    }
-                }
+                float wd, wu, wl, cd, cu, cl;
+                soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl);
                 if (lane == 31 && ckv_out) {
                     __stcg(ckv_out + j, a_down);
                     if (TAN) __stcg(ckt_out + j, at_down);
@@ -252,111 +263,163 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
     __syncwarp();
 }
 
-// Reverse sweep over strip s with the weights the STORE forward left in sbuf:
-// the adjoint Q (E = Q wd) and, with TAN, its tangent Q' (H u = Q' wd + Q wd').
-// Reverse skew: lane i handles column M-1-(t-(31-i)) at step t, so that the
-// cell below (lane i+1) was done one step earlier; its outflows come up by a
-// shuffle, the strip below's through qrow/qtrow.
-// Split pairs: wait_below (may be null) counts the steps the strip below has
-// published, pub (may be null) receives this strip's count (lane 0 writes
-// column j of qrow at step M + 30 - j).
+// The adjoint sweep of a strip, a window of kWin anti-diagonals at a time
+// from the right end: the window's forward steps are recomputed from the
+// state the value sweep saved at its start (same arithmetic, so the same
+// weights) into the warp's shared window buffer, then the reverse steps run
+// over them.  Reverse: the adjoint Q (E = Q wd) and, with TAN, its tangent Q'
+// (H u = Q' wd + Q wd').  Reverse step tr handles the cells of forward step
+// t = M + 30 - tr (lane i, column t - i), so that the cell below (lane i+1)
+// was done one step earlier; its outflows come up by a shuffle, the strip
+// below's through qrow/qtrow (lane 0 writes column j of qrow at step
+// M + 30 - j).  Split pairs: wait_below (may be null) counts the reverse steps
+// the strip below has published, pub (may be null) receives this strip's.
+// Floats of one strip's window checkpoints: 128 per window, the value sweep
+// runs 32 (nb + 1) steps.
+__device__ __forceinline__ int64_t soft_ckw_strip(int M) {
+    static_assert(kWin == 8, "soft_ckw_floats assumes 8-step windows");
+    return soft_ckw_floats(M);
+}
+
+struct RevState {
+    float q_send, dflow, qright, qt_send, dtflow, qtright;
+};
+
 template <bool TAN>
-__device__ __forceinline__ void soft_rev_strip(SoftCtx &C, int s, const float *__restrict__ sbuf, float *qrow,
-                                               float *qtrow, float rgamma, const int32_t *wait_below = nullptr,
-                                               int32_t *pub = nullptr) {
+__device__ __forceinline__ void soft_fwd_window(SoftCtx &C, int s, int t0, float hv, float htv,
+                                                const float *__restrict__ ckw_w) {
+    const int lane = C.lane;
+    const bool rv = 32 * s + lane < C.N;
+    float b = ckw_w[lane], a_down = ckw_w[32 + lane];
+    float bt = TAN ? ckw_w[64 + lane] : 0.0f, at_down = TAN ? ckw_w[96 + lane] : 0.0f;
+    const int u0 = t0 & 31;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+        const int t = t0 + k;
+        float a_up = __shfl_up_sync(kFull, a_down, 1);
+        float at_up = TAN ? __shfl_up_sync(kFull, at_down, 1) : 0.0f;
+        const float h0 = __shfl_sync(kFull, hv, u0 + k);
+        const float ht0 = TAN ? __shfl_sync(kFull, htv, u0 + k) : 0.0f;
+        if (lane == 0) {
+            a_up = h0;
+            if (TAN) at_up = ht0;
+        }
+        const int j = t - lane;
+        if (rv && j >= 0 && j < C.M) {
+            float wd, wu, wl, cd, cu, cl;
+            soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl);
+            C.wb[0][k][lane] = wd;
+            C.wb[1][k][lane] = wu;
+            C.wb[2][k][lane] = wl;
+            if (TAN) {
+                C.wb[3][k][lane] = cd;
+                C.wb[4][k][lane] = cu;
+                C.wb[5][k][lane] = cl;
+            }
+        }
+    }
+}
+
+template <bool TAN>
+__device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevState &R, float *qrow, float *qtrow,
+                                                float rgamma, const int32_t *wait_below, int32_t *pub, int &have) {
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
     const bool last = s == C.nstrips - 1;
-    const int64_t plane = (int64_t)(C.M + 31) * 32;
     const int T = C.M + 31;
-    float q_send = 0.0f, dflow = 0.0f, qright = 0.0f;
-    float qt_send = 0.0f, dtflow = 0.0f, qtright = 0.0f;
-    constexpr int NC = TAN ? 6 : 3;
-    constexpr int CH = 8;  // steps per prefetched chunk
-    int have = 0;
-    // chunk loader: the weights of steps t0..t0+7 (registers) and, in lanes
-    // 0..7, the inflow from the strip below for the columns lane 31 meets then
-    // (down to column M-8-t0, which the strip below writes at its step t0+38)
-    auto load = [&](int t0, float (&w)[CH][NC], float &qb, float &qtb) {
-        if (wait_below) soft_wait(C, wait_below, min(t0 + CH + 31, T), have);
+    const int tr0 = C.M + 30 - (t0 + kWin - 1);  // reverse step of the window's last forward step
+    // the inflow from the strip below for the columns lane 31 meets in this
+    // window (lane k: reverse step tr0 + k), which the strip below writes at
+    // its step tr0 + k + 31
+    if (wait_below) soft_wait(C, wait_below, min(tr0 + kWin + 31, T), have);
+    const int jl = C.M - 1 - (tr0 + lane);
+    const bool in = !last && lane < kWin && jl >= 0 && jl < C.M;
+    const float qb = in ? __ldcg(qrow + jl) : 0.0f;
+    const float qtb = (TAN && in) ? __ldcg(qtrow + jl) : 0.0f;
 #pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const int t = t0 + k;
-            const float *q = sbuf + (int64_t)(C.M + 30 - t) * 32 + lane;
-#pragma unroll
-            for (int cpt = 0; cpt < NC; ++cpt) w[k][cpt] = t < T ? __ldcg(q + cpt * plane) : 0.0f;
+    for (int k = 0; k < kWin; ++k) {
+        const int tr = tr0 + k;
+        if (tr < 0) continue;  // forward steps past the strip's last cell
+        float from_below = __shfl_down_sync(kFull, R.q_send, 1);
+        float from_below_t = TAN ? __shfl_down_sync(kFull, R.qt_send, 1) : 0.0f;
+        const float fb = __shfl_sync(kFull, qb, k);
+        const float fbt = TAN ? __shfl_sync(kFull, qtb, k) : 0.0f;
+        const int j = C.M - 1 - (tr - (31 - lane));
+        if (lane == 31) {
+            from_below = fb;
+            if (TAN) from_below_t = fbt;
         }
-        const int jl = C.M - 1 - (t0 + lane);  // lane 31's column at step t0 + lane
-        const bool in = !last && lane < CH && jl >= 0 && jl < C.M;
-        qb = in ? __ldcg(qrow + jl) : 0.0f;
-        qtb = (TAN && in) ? __ldcg(qtrow + jl) : 0.0f;
-    };
-    float wa[CH][NC], wb[CH][NC];
-    float qa = 0.0f, qta = 0.0f, qb = 0.0f, qtb = 0.0f;
-    load(0, wa, qa, qta);
-    auto run = [&](int t0, const float (&w)[CH][NC], float qbl, float qtbl) {
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            const int t = t0 + k;
-            if (t >= T) break;
-            float from_below = __shfl_down_sync(kFull, q_send, 1);
-            float from_below_t = TAN ? __shfl_down_sync(kFull, qt_send, 1) : 0.0f;
-            const float fb = __shfl_sync(kFull, qbl, k);
-            const float fbt = TAN ? __shfl_sync(kFull, qtbl, k) : 0.0f;
-            const int j = C.M - 1 - (t - (31 - lane));
-            if (lane == 31) {
-                from_below = fb;
-                if (TAN) from_below_t = fbt;
+        if (rv && j >= 0 && j < C.M) {
+            const int kk = kWin - 1 - k;  // the forward step's slot in the window
+            const float wd = C.wb[0][kk][lane], wu = C.wb[1][kk][lane], wl = C.wb[2][kk][lane];
+            float Q = __fadd_rn(from_below, R.qright);
+            float Qt = TAN ? __fadd_rn(from_below_t, R.qtright) : 0.0f;
+            if (r == C.N - 1 && j == C.M - 1) {
+                Q = 1.0f;
+                Qt = 0.0f;
             }
-            if (rv && j >= 0 && j < C.M) {
-                const float wd = w[k][0], wu = w[k][1], wl = w[k][2];
-                float Q = __fadd_rn(from_below, qright);
-                float Qt = TAN ? __fadd_rn(from_below_t, qtright) : 0.0f;
-                if (r == C.N - 1 && j == C.M - 1) {
-                    Q = 1.0f;
-                    Qt = 0.0f;
-                }
-                const float Ec = __fmul_rn(Q, wd);
-                qright = __fmul_rn(Q, wl);
-                q_send = __fadd_rn(__fmul_rn(Q, wu), dflow);
-                dflow = Ec;
-                const int64_t c = (int64_t)r * C.M + j;
-                if (TAN) {
-                    // weight tangents w_k' = w_k (c_k - D') / gamma
-                    const float wdt = __fmul_rn(__fmul_rn(wd, w[k][3]), rgamma);
-                    const float wut = __fmul_rn(__fmul_rn(wu, w[k][4]), rgamma);
-                    const float wlt = __fmul_rn(__fmul_rn(wl, w[k][5]), rgamma);
-                    const float Hu = __fmaf_rn(Q, wdt, __fmul_rn(Qt, wd));
-                    qtright = __fmaf_rn(Q, wlt, __fmul_rn(Qt, wl));
-                    qt_send = __fadd_rn(__fmaf_rn(Q, wut, __fmul_rn(Qt, wu)), dtflow);
-                    dtflow = Hu;
-                    C.U[c] = Hu;
-                    if (lane == 0) __stcg(qtrow + j, qt_send);
-                } else {
-                    C.E[c] = Ec;
-                }
-                if (lane == 0) __stcg(qrow + j, q_send);
+            const float Ec = __fmul_rn(Q, wd);
+            R.qright = __fmul_rn(Q, wl);
+            R.q_send = __fadd_rn(__fmul_rn(Q, wu), R.dflow);
+            R.dflow = Ec;
+            const int64_t c = (int64_t)r * C.M + j;
+            if (TAN) {
+                // weight tangents w_k' = w_k (c_k - D') / gamma
+                const float wdt = __fmul_rn(__fmul_rn(wd, C.wb[3][kk][lane]), rgamma);
+                const float wut = __fmul_rn(__fmul_rn(wu, C.wb[4][kk][lane]), rgamma);
+                const float wlt = __fmul_rn(__fmul_rn(wl, C.wb[5][kk][lane]), rgamma);
+                const float Hu = __fmaf_rn(Q, wdt, __fmul_rn(Qt, wd));
+                R.qtright = __fmaf_rn(Q, wlt, __fmul_rn(Qt, wl));
+                R.qt_send = __fadd_rn(__fmaf_rn(Q, wut, __fmul_rn(Qt, wu)), R.dtflow);
+                R.dtflow = Hu;
+                C.U[c] = Hu;
+                if (lane == 0) __stcg(qtrow + j, R.qt_send);
             } else {
-                q_send = dflow = qright = 0.0f;
-                qt_send = dtflow = qtright = 0.0f;
+                C.E[c] = Ec;
             }
+            if (lane == 0) __stcg(qrow + j, R.q_send);
+        } else {
+            R.q_send = R.dflow = R.qright = 0.0f;
+            R.qt_send = R.dtflow = R.qtright = 0.0f;
         }
-    };
-    auto publish = [&](int t0) {
-        if (pub && lane == 0) st_release(pub, min(t0 + CH, T));
-    };
-    // two chunks in flight: load chunk c+1 while chunk c runs
-    for (int t0 = 0; t0 < T; t0 += 2 * CH) {
-        if (t0 + CH < T) load(t0 + CH, wb, qb, qtb);
-        run(t0, wa, qa, qta);
-        publish(t0);
-        if (t0 + CH >= T) break;
-        if (t0 + 2 * CH < T) load(t0 + 2 * CH, wa, qa, qta);
-        run(t0 + CH, wb, qb, qtb);
-        publish(t0 + CH);
     }
-    __syncwarp();
+    if (pub && lane == 0) st_release(pub, min(max(tr0 + kWin, 0), T));
+}
+
+// The whole adjoint sweep of strip s (after its value sweep saved ckw).
+template <bool TAN>
+__device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const float *__restrict__ ckv_top,
+                                                   const float *__restrict__ ckt_top, const float *__restrict__ ckw,
+                                                   float *qrow, float *qtrow, float rgamma,
+                                                   const int32_t *wait_below = nullptr, int32_t *pub = nullptr) {
+    const int lane = C.lane;
+    const int r = 32 * s + lane;
+    const bool rv = r < C.N;
+    C.row = sim_row(rv ? (int)(C.ssent[r + 1] - C.ssent[r]) : 1, C.P);
+    const int nb = (C.M + 31) >> 5;
+    RevState R{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int have = 0;
+    int cur = -1;  // the block whose windows run (blocks cur and cur - 1 are prepared)
+    float hv = 0.0f, htv = 0.0f;
+    for (int w = (C.M + 30) / kWin; w >= 0; --w) {
+        const int t0 = w * kWin, jb = t0 >> 5;
+        if (jb != cur) {
+            // windows of block jb read blocks jb and jb - 1; going left, block jb
+            // is ready from block jb + 1's windows except at the start
+            if (cur < 0 && jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
+            if (jb >= 1) soft_prep_block<TAN>(C, r, rv, jb - 1);
+            cur = jb;
+            const int colx = 32 * jb + lane;
+            const bool top = s > 0 && colx < C.M;
+            hv = top ? __ldcg(ckv_top + colx) : -C.two_p;
+            htv = (TAN && top) ? __ldcg(ckt_top + colx) : 0.0f;
+        }
+        soft_fwd_window<TAN>(C, s, t0, hv, htv, ckw + (int64_t)w * 128);
+        __syncwarp();
+        soft_rev_window<TAN>(C, s, t0, R, qrow, qtrow, rgamma, wait_below, pub, have);
+        __syncwarp();
+    }
 }
 
 __device__ __forceinline__ bool next_item(int32_t *queue, int32_t n, int lane, int32_t &it) {
@@ -399,17 +462,35 @@ __device__ __forceinline__ SoftCtx make_ctx(const DevParams &P, const SoftArgs &
     return C;
 }
 
-struct SoftSmem {
+// Per-warp shared memory of the sweep kernels (the value sweep of the
+// forward needs no u).
+struct SoftSmemFwd {
+    float sv[2][32][32];
+    float wb[3][kWin][32];
+    SimCol colv[32];
+};
+struct SoftSmemBwd {
     float sv[2][32][32];
     float ub[2][32][32];
+    float wb[6][kWin][32];
     SimCol colv[32];
 };
 
+template <bool TAN>
 __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
-    SoftSmem &sm = reinterpret_cast<SoftSmem *>(raw)[threadIdx.x >> 5];
-    C.svb = sm.sv;
-    C.ub = sm.ub;
-    C.colv = sm.colv;
+    if (TAN) {
+        SoftSmemBwd &sm = reinterpret_cast<SoftSmemBwd *>(raw)[threadIdx.x >> 5];
+        C.svb = sm.sv;
+        C.ub = sm.ub;
+        C.wb = sm.wb;
+        C.colv = sm.colv;
+    } else {
+        SoftSmemFwd &sm = reinterpret_cast<SoftSmemFwd *>(raw)[threadIdx.x >> 5];
+        C.svb = sm.sv;
+        C.ub = nullptr;
+        C.wb = sm.wb;
+        C.colv = sm.colv;
+    }
 }
 
 // Sweep 1 (value) + sweep 2 (adjoint): V(N,M) and E for every cell.  A
@@ -423,10 +504,8 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
                     SoftScratch W) {
     extern __shared__ __align__(16) unsigned char soft_smem[];
     SoftCtx C = make_ctx(P, A);
-    bind_smem(C, soft_smem);
+    bind_smem<false>(C, soft_smem);
     const int lane = C.lane;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    float *sbuf = W.sbuf + gw * W.sbuf_stride;
     const int32_t n_items = W.queue[1];
     int32_t it;
     while (next_item(W.queue, n_items, lane, it)) {
@@ -441,26 +520,24 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
         float *vlast = ckv + (int64_t)(S - 1) * C.M;  // the last strip writes no checkpoint
         float *qrow = W.qrow + g.soft_off;
         auto top = [&](int s) { return s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr; };
+        auto ckw = [&](int s) { return W.ckw + g.ckw_off + (int64_t)s * soft_ckw_strip(C.M); };
         if (I.kind == 0) {
             for (int s = 0; s < S; ++s)
-                soft_fwd_strip<false, false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
-                                             nullptr, sbuf, s + 1 == S ? vlast : nullptr);
-            for (int s = S - 1; s >= 0; --s) {
-                soft_fwd_strip<false, true>(C, s, top(s), nullptr, nullptr, nullptr, sbuf, nullptr);
-                soft_rev_strip<false>(C, s, sbuf, qrow, nullptr, 0.0f);
-            }
+                soft_fwd_strip<false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr, nullptr,
+                                      ckw(s), s + 1 == S ? vlast : nullptr);
+            for (int s = S - 1; s >= 0; --s) soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), qrow, nullptr, 0.0f);
         } else {
             const int s = I.strip;
             int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
             if (I.kind == 1) {
-                soft_fwd_strip<false, false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
-                                             nullptr, sbuf, s + 1 == S ? vlast : nullptr,
-                                             s > 0 ? p1 + s - 1 : nullptr,
-                                             (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
+                soft_fwd_strip<false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr, nullptr,
+                                      ckw(s), s + 1 == S ? vlast : nullptr, s > 0 ? p1 + s - 1 : nullptr,
+                                      (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
             } else {
-                soft_fwd_strip<false, true>(C, s, top(s), nullptr, nullptr, nullptr, sbuf, nullptr,
-                                            s > 0 ? p1 + s - 1 : nullptr, nullptr);
-                soft_rev_strip<false>(C, s, sbuf, qrow, nullptr, 0.0f, s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
+                int have = 0;  // this strip's value sweep (and so the one above) complete
+                soft_wait(C, p1 + s, C.M, have);
+                soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), qrow, nullptr, 0.0f,
+                                          s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
             }
         }
     }
@@ -474,10 +551,8 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
                      SoftScratch W) {
     extern __shared__ __align__(16) unsigned char soft_smem[];
     SoftCtx C = make_ctx(P, A);
-    bind_smem(C, soft_smem);
+    bind_smem<true>(C, soft_smem);
     const int lane = C.lane;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    float *sbuf = W.sbuf + gw * W.sbuf_stride;
     const float rgamma = 1.0f / A.gamma;
     const int32_t n_items = W.queue[1];
     int32_t it;
@@ -495,26 +570,26 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
         float *qtrow = W.qtrow + g.soft_off;
         auto topv = [&](int s) { return s > 0 ? ckv + (int64_t)(s - 1) * C.M : nullptr; };
         auto topt = [&](int s) { return s > 0 ? ckt + (int64_t)(s - 1) * C.M : nullptr; };
+        auto ckw = [&](int s) { return W.ckw + g.ckw_off + (int64_t)s * soft_ckw_strip(C.M); };
         if (I.kind == 0) {
-            for (int s = 0; s + 1 < S; ++s)
-                soft_fwd_strip<true, false>(C, s, topv(s), topt(s), ckv + (int64_t)s * C.M, ckt + (int64_t)s * C.M,
-                                            sbuf, nullptr);
-            for (int s = S - 1; s >= 0; --s) {
-                soft_fwd_strip<true, true>(C, s, topv(s), topt(s), nullptr, nullptr, sbuf, nullptr);
-                soft_rev_strip<true>(C, s, sbuf, qrow, qtrow, rgamma);
-            }
+            for (int s = 0; s < S; ++s)
+                soft_fwd_strip<true>(C, s, topv(s), topt(s), s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
+                                     s + 1 < S ? ckt + (int64_t)s * C.M : nullptr, ckw(s), nullptr);
+            for (int s = S - 1; s >= 0; --s)
+                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), qrow, qtrow, rgamma);
         } else {
             const int s = I.strip;
             int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
             if (I.kind == 1) {
-                if (s + 1 < S)  // the last strip's checkpoint is not needed
-                    soft_fwd_strip<true, false>(C, s, topv(s), topt(s), ckv + (int64_t)s * C.M,
-                                                ckt + (int64_t)s * C.M, sbuf, nullptr, s > 0 ? p1 + s - 1 : nullptr,
-                                                (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
+                soft_fwd_strip<true>(C, s, topv(s), topt(s), s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
+                                     s + 1 < S ? ckt + (int64_t)s * C.M : nullptr, ckw(s), nullptr,
+                                     s > 0 ? p1 + s - 1 : nullptr,
+                                     (int64_t)I.ctr + s == A.skip_ctr ? nullptr : p1 + s);
             } else {
-                soft_fwd_strip<true, true>(C, s, topv(s), topt(s), nullptr, nullptr, sbuf, nullptr,
-                                           s > 0 ? p1 + s - 1 : nullptr, nullptr);
-                soft_rev_strip<true>(C, s, sbuf, qrow, qtrow, rgamma, s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
+                int have = 0;  // this strip's value sweep (and so the one above) complete
+                soft_wait(C, p1 + s, C.M, have);
+                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), qrow, qtrow, rgamma,
+                                         s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
             }
         }
     }
@@ -825,9 +900,8 @@ int soft_grid(int n_sms) { return n_sms * 3; }
 
 int64_t soft_warps(int n_sms) { return (int64_t)soft_grid(n_sms) * kSoftWarps; }
 
-static cudaError_t set_soft_smem(const void *kern) {
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(SoftSmem) * kSoftWarps));
+static cudaError_t set_soft_smem(const void *kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 static void launch_soft_items(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const SoftArgs &A,
@@ -841,9 +915,9 @@ cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, cons
                                 float *value, int n_sms, cudaStream_t st) {
     launch_soft_items(geom, order, n_pairs, A, W, n_sms, st);
     if (n_pairs > 0) {
-        cudaError_t e = set_soft_smem((const void *)soft_forward_kernel);
+        cudaError_t e = set_soft_smem((const void *)soft_forward_kernel, sizeof(SoftSmemFwd) * kSoftWarps);
         if (e != cudaSuccess) return e;
-        soft_forward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmem) * kSoftWarps, st>>>(
+        soft_forward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmemFwd) * kSoftWarps, st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
         soft_loss_kernel<false><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
     }
@@ -859,10 +933,10 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
                                  float *grad, float *hvp, int n_sms, cudaStream_t st) {
     launch_soft_items(geom, order, n_pairs, A, W, n_sms, st);
     if (n_pairs > 0) {
-        cudaError_t e = set_soft_smem((const void *)soft_backward_kernel);
+        cudaError_t e = set_soft_smem((const void *)soft_backward_kernel, sizeof(SoftSmemBwd) * kSoftWarps);
         if (e != cudaSuccess) return e;
         soft_loss_kernel<true><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
-        soft_backward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmem) * kSoftWarps, st>>>(
+        soft_backward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmemBwd) * kSoftWarps, st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
         soft_chain_kernel<<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W, hvp);
     }
