@@ -715,6 +715,42 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
     }
 }
 
+// Sum over a block of 256 threads in a fixed order (butterflies within the
+// warps, then the eight warp sums in warp order); the total reaches thread 0.
+__device__ __forceinline__ double block_sum256(double v, double *ws) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    __syncthreads();  // the previous use of ws is complete
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w) t += ws[w];
+    return t;
+}
+
+// NV sums over a block of 256 threads at once, in the same fixed order as
+// block_sum256; thread q < NV receives sum q.
+template <int NV>
+__device__ __forceinline__ double block_sums256(const double (&v)[NV], double (*ws)[8]) {
+    double x[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        x[q] = v[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_xor_sync(kFull, x[q], off);
+    }
+    __syncthreads();  // the previous use of ws is complete
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) ws[q][threadIdx.x >> 5] = x[q];
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < NV)
+        for (int w = 0; w < 8; ++w) t += ws[threadIdx.x][w];
+    return t;
+}
+
 // Row and column of the cells a thread visits in a chunk (cells c0 + t,
 // c0 + t + 256, ... of a pair with M columns): one 32-bit division per thread
 // and chunk, then constant steps; the sentence lengths of the current row and
@@ -746,8 +782,7 @@ __global__ void __launch_bounds__(256)
 soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
                  DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
                  SoftScratch W) {
-    __shared__ double red[256];
-    __shared__ double vred[256];
+    __shared__ double ws[8];
     SoftCtx C = make_ctx(P, A);
     const int32_t n_chunks = W.queue[2];
     for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
@@ -766,11 +801,12 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
                 row_i = cw.i;
                 srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
             }
-            const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + c];
-            const float sv = similarity(q.x, q.y, srow, sim_col((int)(tgt.sent[tb + cw.j + 1] - tgt.sent[tb + cw.j]), P),
-                                        C.K);
+            const uchar2 q = __ldg(reinterpret_cast<const uchar2 *>(counts) + g.cell_off + c);
+            const float sv = similarity(
+                q.x, q.y, srow, sim_col((int)(__ldg(tgt.sent + tb + cw.j + 1) - __ldg(tgt.sent + tb + cw.j)), P), C.K);
             float G, bce;
-            const float lp = cell_dldp(W.E[g.cell_off + c], sv, gold[g.cell_off + c], C, G, WANT_U ? nullptr : &bce);
+            const float lp = cell_dldp(__ldg(W.E + g.cell_off + c), sv, __ldg(gold + g.cell_off + c), C, G,
+                                       WANT_U ? nullptr : &bce);
             if (WANT_U)
                 W.U[g.cell_off + c] = __fmul_rn(lp, G);
             else
@@ -783,23 +819,14 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
             const float *vlast = W.ckv + g.soft_off + (int64_t)((g.n + 31) / 32 - 1) * g.m;
             for (int j = threadIdx.x; j < g.m; j += blockDim.x) vs += (double)vlast[j] + (double)P.gap;
         }
-        red[threadIdx.x] = (double)acc;
-        vred[threadIdx.x] = vs;
-        __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if ((int)threadIdx.x < off) {
-                red[threadIdx.x] += red[threadIdx.x + off];
-                vred[threadIdx.x] += vred[threadIdx.x + off];
-            }
-            __syncthreads();
-        }
+        const double lsum = block_sum256((double)acc, ws);
+        const double vsum = ch.c0 == 0 ? block_sum256(vs, ws) : 0.0;
         if (threadIdx.x == 0) {
-            W.partial[(int64_t)x * kSoftSlots] = red[0];
+            W.partial[(int64_t)x * kSoftSlots] = lsum;
             if (ch.c0 == 0)
-                W.vpart[ch.pos] = (g.n > 0 && g.m > 0) ? vred[0] - (double)P.gap * (double)g.n
+                W.vpart[ch.pos] = (g.n > 0 && g.m > 0) ? vsum - (double)P.gap * (double)g.n
                                                        : -(double)P.gap * (double)(g.n + g.m);
         }
-        __syncthreads();
     }
 }
 
@@ -809,7 +836,7 @@ __global__ void __launch_bounds__(256)
 soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
                   DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
                   SoftScratch W, float *__restrict__ hvp) {
-    __shared__ double red[7][256];
+    __shared__ double ws[7][8];
     SoftCtx C = make_ctx(P, A);
     const int32_t n_chunks = W.queue[2];
     for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
@@ -828,14 +855,14 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
                 row_i = cw.i;
                 srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
             }
-            const SimCol scol = sim_col((int)(tgt.sent[tb + cw.j + 1] - tgt.sent[tb + cw.j]), P);
-            const uchar2 q = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + c];
+            const SimCol scol = sim_col((int)(__ldg(tgt.sent + tb + cw.j + 1) - __ldg(tgt.sent + tb + cw.j)), P);
+            const uchar2 q = __ldg(reinterpret_cast<const uchar2 *>(counts) + g.cell_off + c);
             const float sv = similarity(q.x, q.y, srow, scol, C.K);
-            const float Es = W.E[g.cell_off + c];
-            const float Hu = W.U[g.cell_off + c];
+            const float Es = __ldg(W.E + g.cell_off + c);
+            const float Hu = __ldg(W.U + g.cell_off + c);
             if (hvp) hvp[g.cell_off + c] = Hu;
             float G;
-            const float lp = cell_dldp(Es, sv, gold[g.cell_off + c], C, G, nullptr);
+            const float lp = cell_dldp(Es, sv, __ldg(gold + g.cell_off + c), C, G, nullptr);
             const float gg = __fmul_rn(__fmul_rn(G, __fsub_rn(1.0f, G)), C.ktau * kLn2);
             const float direct = __fmul_rn(__fmul_rn(lp, Es), gg);  // dL/ds through the gate
             const float dlds = __fadd_rn(Hu, direct);
@@ -853,17 +880,11 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
             gr[5] = __fmaf_rn(2.0f, Hu, gr[5]);
             gr[6] = __fsub_rn(gr[6], direct);
         }
+        double gd[7];
 #pragma unroll
-        for (int q7 = 0; q7 < 7; ++q7) red[q7][threadIdx.x] = (double)gr[q7];
-        __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if ((int)threadIdx.x < off)
-#pragma unroll
-                for (int q7 = 0; q7 < 7; ++q7) red[q7][threadIdx.x] += red[q7][threadIdx.x + off];
-            __syncthreads();
-        }
-        if (threadIdx.x < 7) W.partial[(int64_t)x * kSoftSlots + 1 + threadIdx.x] = red[threadIdx.x][0];
-        __syncthreads();
+        for (int q7 = 0; q7 < 7; ++q7) gd[q7] = (double)gr[q7];
+        const double t = block_sums256<7>(gd, ws);
+        if (threadIdx.x < 7) W.partial[(int64_t)x * kSoftSlots + 1 + threadIdx.x] = t;
     }
 }
 
@@ -917,7 +938,11 @@ cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, cons
     if (n_pairs > 0) {
         cudaError_t e = set_soft_smem((const void *)soft_forward_kernel, sizeof(SoftSmemFwd) * kSoftWarps);
         if (e != cudaSuccess) return e;
-        soft_forward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmemFwd) * kSoftWarps, st>>>(
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_forward_kernel, 32 * kSoftWarps,
+                                                          sizeof(SoftSmemFwd) * kSoftWarps);
+        if (e != cudaSuccess) return e;
+        soft_forward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftWarps, sizeof(SoftSmemFwd) * kSoftWarps, st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
         soft_loss_kernel<false><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
     }
@@ -935,8 +960,12 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
     if (n_pairs > 0) {
         cudaError_t e = set_soft_smem((const void *)soft_backward_kernel, sizeof(SoftSmemBwd) * kSoftWarps);
         if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_backward_kernel, 32 * kSoftWarps,
+                                                          sizeof(SoftSmemBwd) * kSoftWarps);
+        if (e != cudaSuccess) return e;
         soft_loss_kernel<true><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
-        soft_backward_kernel<<<soft_grid(n_sms), 32 * kSoftWarps, sizeof(SoftSmemBwd) * kSoftWarps, st>>>(
+        soft_backward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftWarps, sizeof(SoftSmemBwd) * kSoftWarps, st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
         soft_chain_kernel<<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W, hvp);
     }
