@@ -94,7 +94,9 @@ def parse():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the single-pair, 10,000-pair, NW-only and soft-NW records")
     ap.add_argument("--soft-step", action="store_true",
-                    help="only time one soft-NW forward+backward on a 4,096-pair tuning minibatch (profiling)")
+                    help="only time one soft-NW forward+backward (profiling): on a 4,096-pair tuning minibatch, "
+                         "or with --soft-config soft on the 4,096 planted pairs of the soft configuration")
+    ap.add_argument("--soft-config", default="tune", choices=["tune", "soft"])
     return ap.parse_args()
 
 
@@ -408,9 +410,12 @@ def soft_step(args):
     JSON line with the CUDA-event times."""
     import torch
     from paper_1512_01641_gb300 import miner, tune
-    rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
-    dic = synth.make_dictionary(rng, 50_000, 50_000)
-    td = tune.TuneData(synth.tune_batch(4096, seed=synth.SEED_BASE + 4, dic=dic))
+    if args.soft_config == "soft":
+        td = tune.TuneData(synth.soft_batch())
+    else:
+        rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
+        dic = synth.make_dictionary(rng, 50_000, 50_000)
+        td = tune.TuneData(synth.tune_batch(4096, seed=synth.SEED_BASE + 4, dic=dic))
     al = miner.SoftAligner(td.plan, td.counts, td.gold, 0.1, 0.05)
     p = miner.params_from_theta(tune.THETA0)
     for _ in range(max(args.warmup, 2)):
@@ -424,7 +429,8 @@ def soft_step(args):
     al.backward(p)
     ev[2].record()
     torch.cuda.synchronize()
-    print(json.dumps({"soft_step": {"pairs": td.plan.n_pairs, "cells": td.plan.n_cells, "gamma": 0.1,
+    print(json.dumps({"soft_step": {"config": args.soft_config, "pairs": td.plan.n_pairs, "cells": td.plan.n_cells,
+                                    "gamma": 0.1,
                                     "forward_ms": ev[0].elapsed_time(ev[1]),
                                     "backward_ms": ev[1].elapsed_time(ev[2])}}))
 
@@ -556,30 +562,30 @@ def _pinned_inputs(batch):
     return [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host]
 
 
-def e2e_run(batch, params, steps, options=None):
-    """Public API from pinned host buffers, one batch at a time: upload,
-    plan (with the given plan options), mine, download, destroy.  Median
-    seconds per step."""
+def e2e_host_abi(batch, params, steps, options=None):
+    """The C ABI from host buffers: one mine_pairs_host call per step (upload
+    from pinned host memory, plan, mine, download of links and scores, all
+    inside the call).  Median seconds per step, bytes each way."""
     import torch
     from paper_1512_01641_gb300 import miner
     pinned = _pinned_inputs(batch)
     h2d = sum(t.numel() * t.element_size() for t in pinned)
-    times, d2h = [], 0
+    ns, mt = np.diff(batch.src.doc_sent_off), np.diff(batch.tgt.doc_sent_off)
+    cap = max(int(np.minimum(ns, mt).sum()), 1)
+    out = {"link_off": torch.empty(batch.n_pairs + 1, dtype=torch.int64).pin_memory(),
+           "link_i": torch.empty(cap, dtype=torch.int32).pin_memory(),
+           "link_j": torch.empty(cap, dtype=torch.int32).pin_memory(),
+           "link_s": torch.empty(cap, dtype=torch.float32).pin_memory(),
+           "pair_score": torch.empty(max(batch.n_pairs, 1), dtype=torch.float32).pin_memory()}
+    miner.mine_host(pinned, batch.dic.v_src, batch.dic.v_tgt, params, options, out)  # warm-up
+    times = []
     for _ in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dev = [t.to("cuda", non_blocking=True) for t in pinned]
-        db = miner.DeviceBatch(*dev, batch.dic.v_src, batch.dic.v_tgt)
-        plan = miner.Plan(db, options=options)
-        out = plan.mine(params)
-        n = int(out["link_off"][-1].item())
-        res = {"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"].cpu(),
-               "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(), "link_s": out["link_s"][:n].cpu()}
-        torch.cuda.synchronize()
+        miner.mine_host(pinned, batch.dic.v_src, batch.dic.v_tgt, params, options, out)
         times.append(time.perf_counter() - t0)
-        d2h = 8 + sum(t.numel() * t.element_size() for t in res.values())
-        plan.close()
-        del dev, db, out
+    n = int(out["link_off"][-1])
+    d2h = out["link_off"].numel() * 8 + batch.n_pairs * 4 + n * 12
     return float(np.median(times)), h2d, d2h
 
 
@@ -729,16 +735,19 @@ def main():
     if not args.no_e2e:
         plan_keep = plan
         opts = dict(tuned["best"]) if tuned else {}
-        e_seq, h2d, d2h = e2e_run(batch, params, args.e2e_steps, opts)
+        e_abi, h2d, d2h = e2e_host_abi(batch, params, args.e2e_steps, opts)
         e_t, d2h_p = e2e_pipelined(batch, params, args.e2e_stream_steps, opts)
-        e2e = {"value": cells_step / world / e_t * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h_p, "seconds_per_step": e_t,
-               "includes": "per step: H2D of the inputs from pinned host memory, plan creation (validation, "
-                           "geometry, scratch), mine_pairs, D2H of links and scores; batches streamed "
-                           f"through BatchPipeline ({args.e2e_stream_steps} steps incl. pipeline fill and drain)",
+        e2e = {"value": cells_step / world / e_abi * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e_abi,
+               "includes": "one mine_pairs_host C-ABI call per step: H2D of the inputs from pinned host memory, "
+                           "plan creation (validation, geometry, scratch), mining, D2H of links and scores "
+                           f"(median of {args.e2e_steps} steps)",
                "plan_options": opts,
-               "sequential": {"value": cells_step / world / e_seq * world, "seconds_per_step": e_seq,
-                              "includes": "one batch at a time, nothing overlapped"}}
+               "pipelined": {"value": cells_step / world / e_t * world, "seconds_per_step": e_t,
+                             "d2h_bytes_per_step": d2h_p,
+                             "includes": "the same work streamed batch after batch through BatchPipeline (the "
+                                         "next batch's upload and plan overlap the current mining; "
+                                         f"{args.e2e_stream_steps} steps incl. pipeline fill and drain)"}}
         plan = plan_keep
 
     cpu = ties = None

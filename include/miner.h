@@ -154,6 +154,22 @@ int mine_align(mine_plan *plan, const mine_params *params, const uint8_t *counts
 int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
                miner_stream_t stream);
 
+/* The whole hot path from HOST buffers, for callers that hold the corpora in
+ * host memory and have no device buffers of their own: the corpus and
+ * dictionary structs' arrays are HOST pointers (pinned memory copies at full
+ * speed, pageable memory works); the library uploads them into memory from its
+ * pool, plans (with the options, as mine_plan_create_with_options; the CUDA
+ * graph is off unless an option turns it on), runs mine_pairs, and writes the
+ * results to the host arrays: link_off (n_docs+1), the links (link_capacity
+ * entries, at least the sum over pairs of min(N_k, M_k)) and pair_score
+ * (n_docs).  SYNCHRONOUS: returns when the results are in host memory and
+ * everything the call allocated is back in the pool.  Error codes as
+ * mine_plan_create and mine_pairs, MINE_ETIMEOUT as mine_plan_check. */
+int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict, const mine_params *params,
+                    const int32_t *options, const int64_t *values, int n_options, int64_t *link_off,
+                    int32_t *link_i, int32_t *link_j, float *link_s, float *pair_score, int64_t link_capacity,
+                    miner_stream_t stream);
+
 /* Link quality against gold links (gold: one 0/1 byte per cell, per-cell
  * layout as the counts): counts3[0] = links that are gold, counts3[1] =
  * links, counts3[2] = gold cells (device, 3 x uint64).  Micro precision =

@@ -1257,3 +1257,85 @@ int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------- host-buffer mining
+extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                               const mine_params *params, const int32_t *options, const int64_t *values,
+                               int n_options, int64_t *link_off, int32_t *link_i, int32_t *link_j, float *link_s,
+                               float *pair_score, int64_t link_capacity, miner_stream_t stream) {
+    if (!src || !tgt || !dict || !params || !link_off || (src->n_docs > 0 && !pair_score)) return MINE_EINVAL;
+    if (src->n_docs != tgt->n_docs || src->n_docs < 0 || src->n_sents < 0 || tgt->n_sents < 0 || src->n_tok < 0 ||
+        tgt->n_tok < 0 || dict->v_src <= 0 || dict->n_entries < 0 || link_capacity < 0)
+        return MINE_EINVAL;
+    if (!src->doc_sent_off || !src->sent_tok_off || !tgt->doc_sent_off || !tgt->sent_tok_off || !dict->off ||
+        (src->n_tok > 0 && !src->tok) || (tgt->n_tok > 0 && !tgt->tok) || (dict->n_entries > 0 && !dict->tgt))
+        return MINE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int device;
+    MINE_CK(cudaGetDevice(&device));
+    // device copies of the inputs, from the library's pool (returned on every path)
+    PoolTemp<int64_t> sdoc(st), ssent(st), tdoc(st), tsent(st);
+    PoolTemp<int32_t> stok(st), ttok(st), doff(st), dtgt(st);
+    const int64_t n = src->n_docs;
+    MINE_CK(dalloc(&sdoc.p, (size_t)n + 1, device, st));
+    MINE_CK(dalloc(&tdoc.p, (size_t)n + 1, device, st));
+    MINE_CK(dalloc(&ssent.p, (size_t)src->n_sents + 1, device, st));
+    MINE_CK(dalloc(&tsent.p, (size_t)tgt->n_sents + 1, device, st));
+    MINE_CK(dalloc(&stok.p, (size_t)std::max<int64_t>(src->n_tok, 1), device, st));
+    MINE_CK(dalloc(&ttok.p, (size_t)std::max<int64_t>(tgt->n_tok, 1), device, st));
+    MINE_CK(dalloc(&doff.p, (size_t)dict->v_src + 1, device, st));
+    MINE_CK(dalloc(&dtgt.p, (size_t)std::max<int64_t>(dict->n_entries, 1), device, st));
+    auto up = [&](void *d, const void *h, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    MINE_CK(up(sdoc.p, src->doc_sent_off, (n + 1) * 8));
+    MINE_CK(up(tdoc.p, tgt->doc_sent_off, (n + 1) * 8));
+    MINE_CK(up(ssent.p, src->sent_tok_off, (src->n_sents + 1) * 8));
+    MINE_CK(up(tsent.p, tgt->sent_tok_off, (tgt->n_sents + 1) * 8));
+    MINE_CK(up(stok.p, src->tok, src->n_tok * 4));
+    MINE_CK(up(ttok.p, tgt->tok, tgt->n_tok * 4));
+    MINE_CK(up(doff.p, dict->off, ((size_t)dict->v_src + 1) * 4));
+    MINE_CK(up(dtgt.p, dict->tgt, dict->n_entries * 4));
+    const mine_corpus ds{src->n_docs, src->n_sents, src->n_tok, sdoc.p, ssent.p, stok.p};
+    const mine_corpus dt{tgt->n_docs, tgt->n_sents, tgt->n_tok, tdoc.p, tsent.p, ttok.p};
+    const mine_dict dd{dict->v_src, dict->v_tgt, dict->n_entries, doff.p, dtgt.p};
+    // a plan used once: no graph capture unless the caller's options ask for it
+    if (n_options < 0 || (n_options > 0 && (!options || !values))) return MINE_EINVAL;
+    std::vector<int32_t> opt(1, MINE_OPT_USE_GRAPH);
+    std::vector<int64_t> val(1, 0);
+    opt.insert(opt.end(), options, options + n_options);
+    val.insert(val.end(), values, values + n_options);
+    mine_plan *p = nullptr;
+    int r = mine_plan_create_with_options(&ds, &dt, &dd, opt.data(), val.data(), (int)opt.size(), &p, stream);
+    if (r != MINE_OK) return r;
+    struct PlanGuard {
+        mine_plan *p;
+        ~PlanGuard() { mine_plan_destroy(p); }
+    } guard{p};
+    if (link_capacity < p->link_cap || (p->link_cap > 0 && (!link_i || !link_j || !link_s))) return MINE_EINVAL;
+    PoolTemp<int64_t> o_off(st);
+    PoolTemp<int32_t> o_i(st), o_j(st);
+    PoolTemp<float> o_s(st), o_score(st);
+    MINE_CK(dalloc(&o_off.p, (size_t)n + 1, device, st));
+    MINE_CK(dalloc(&o_i.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
+    MINE_CK(dalloc(&o_j.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
+    MINE_CK(dalloc(&o_s.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
+    MINE_CK(dalloc(&o_score.p, (size_t)std::max<int64_t>(n, 1), device, st));
+    mine_out out{o_off.p, o_i.p, o_j.p, o_s.p, o_score.p, std::max<int64_t>(p->link_cap, 1)};
+    r = mine_pairs(p, params, &out, stream);
+    if (r != MINE_OK) return r;
+    MINE_CK(cudaMemcpyAsync(link_off, o_off.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+    if (n > 0) MINE_CK(cudaMemcpyAsync(pair_score, o_score.p, n * 4, cudaMemcpyDeviceToHost, st));
+    MINE_CK(cudaStreamSynchronize(st));
+    r = mine_plan_check(p, stream);
+    if (r != MINE_OK) return r;
+    const int64_t total = link_off[n];
+    if (total < 0 || total > link_capacity) return MINE_EINVAL;
+    if (total > 0) {
+        MINE_CK(cudaMemcpyAsync(link_i, o_i.p, total * 4, cudaMemcpyDeviceToHost, st));
+        MINE_CK(cudaMemcpyAsync(link_j, o_j.p, total * 4, cudaMemcpyDeviceToHost, st));
+        MINE_CK(cudaMemcpyAsync(link_s, o_s.p, total * 4, cudaMemcpyDeviceToHost, st));
+    }
+    MINE_CK(cudaStreamSynchronize(st));
+    return MINE_OK;
+}

@@ -94,6 +94,9 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "softnw_bwd": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.POINTER(_SoftOpts), C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mine_pairs_host": (C.c_int, [C.POINTER(_Corpus), C.POINTER(_Corpus), C.POINTER(_Dict), C.POINTER(_Params),
+                                  C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int64, C.c_void_p]),
     "mine_unconstrained_workspace_size": (C.c_int64, [C.c_void_p]),
     "mine_unconstrained_link_capacity": (C.c_int64, [C.c_void_p]),
     "mine_align_unconstrained": (C.c_int, [C.c_void_p, C.POINTER(_Params), C.c_void_p, C.c_void_p, C.POINTER(_Out),
@@ -454,6 +457,43 @@ class BiPlan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def mine_host(host, v_src: int, v_tgt: int, params: "MineParams", options: dict | None = None, out=None,
+              stream=None):
+    """mine_pairs_host: the whole hot path from host arrays.  host: the eight
+    CSR arrays (src doc/sent/tok, tgt doc/sent/tok, dict off/tgt) as numpy
+    arrays or CPU tensors (pinned ones copy at full speed); out (optional):
+    host tensors link_off, link_i, link_j, link_s, pair_score to fill.
+    Returns out with the links of every pair."""
+    import torch
+    t = [x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x)) for x in host]
+    n = t[0].numel() - 1
+    ns, mt = torch.diff(t[0]), torch.diff(t[3])
+    cap = max(int(torch.minimum(ns, mt).sum()), 1)
+    if out is None:
+        out = {"link_off": torch.empty(n + 1, dtype=torch.int64), "link_i": torch.empty(cap, dtype=torch.int32),
+               "link_j": torch.empty(cap, dtype=torch.int32), "link_s": torch.empty(cap, dtype=torch.float32),
+               "pair_score": torch.empty(max(n, 1), dtype=torch.float32)}
+
+    def corpus(doc, sent, tok):
+        c = _Corpus()
+        c.n_docs, c.n_sents, c.n_tok = doc.numel() - 1, sent.numel() - 1, tok.numel()
+        c.doc_sent_off, c.sent_tok_off, c.tok = doc.data_ptr(), sent.data_ptr(), tok.data_ptr() if tok.numel() else 0
+        return c
+    cs, ct = corpus(*t[0:3]), corpus(*t[3:6])
+    d = _Dict()
+    d.v_src, d.v_tgt, d.n_entries = int(v_src), int(v_tgt), t[7].numel()
+    d.off, d.tgt = t[6].data_ptr(), t[7].data_ptr() if t[7].numel() else 0
+    opts = dict(options or {})
+    ids = (C.c_int32 * max(len(opts), 1))(*[OPTIONS[k] for k in opts])
+    vals = (C.c_int64 * max(len(opts), 1))(*[int(v) for v in opts.values()])
+    p = params.c()
+    _check(lib().mine_pairs_host(C.byref(cs), C.byref(ct), C.byref(d), C.byref(p), ids, vals, len(opts),
+                                 out["link_off"].data_ptr(), out["link_i"].data_ptr(), out["link_j"].data_ptr(),
+                                 out["link_s"].data_ptr(), out["pair_score"].data_ptr(), out["link_i"].numel(),
+                                 _stream(stream)), "mine_pairs_host")
+    return out
 
 
 def noalloc_result(n_links: int, pair_score: float):

@@ -42,3 +42,37 @@ def test_pipeline_results_equal_plan_mine(options):
     for a, b in zip(ref, got):
         for k in a:
             assert torch.equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_host_buffer_entry_point_equals_plan_mine(pinned):
+    """mine_pairs_host (inputs and outputs in host memory, one C-ABI call)
+    gives exactly the links and scores of Plan.mine on device buffers; a
+    short output is rejected."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    b = synth.make_batch(97, 60, v_src=3000, v_tgt=3000)
+    params = miner.MineParams()
+    with miner.Plan(miner.DeviceBatch.from_batch(b)) as plan:
+        out = plan.mine(params)
+        n = int(out["link_off"][-1])
+        ref = {"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"][:plan.n_pairs].cpu(),
+               "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(), "link_s": out["link_s"][:n].cpu()}
+        cap = plan.link_capacity
+    host = [b.src.doc_sent_off, b.src.sent_tok_off, b.src.tok, b.tgt.doc_sent_off, b.tgt.sent_tok_off, b.tgt.tok,
+            b.dic.off, b.dic.tgt]
+    host = [torch.from_numpy(np.ascontiguousarray(a)) for a in host]
+    if pinned:
+        host = [t.pin_memory() for t in host]
+    got = miner.mine_host(host, b.dic.v_src, b.dic.v_tgt, params)
+    m = int(got["link_off"][-1])
+    assert m == n
+    assert torch.equal(got["link_off"], ref["link_off"])
+    assert torch.equal(got["pair_score"][:b.n_pairs], ref["pair_score"])
+    for k in ("link_i", "link_j", "link_s"):
+        assert torch.equal(got[k][:m], ref[k]), k
+    short = {k: v.clone() for k, v in got.items()}
+    for k in ("link_i", "link_j", "link_s"):
+        short[k] = short[k][:cap - 1].clone()
+    with pytest.raises(miner.MinerError):
+        miner.mine_host(host, b.dic.v_src, b.dic.v_tgt, params, out=short)
