@@ -50,6 +50,7 @@ namespace gbm {
 namespace {
 
 constexpr int kSoftWarps = 4;
+constexpr int kSoftBwdWarps = 2;  // the backward's 22.5 KB of shared memory per warp: five 2-warp CTAs per SM
 constexpr int kWin = 8;  // steps of a window of the adjoint sweep's recompute
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -545,7 +546,7 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
 
 // Sweep 3 (value + tangent, checkpoints) + sweep 4 (adjoint and its tangent):
 // H u for every cell, written over u.  Same work list as the forward.
-__global__ void __launch_bounds__(32 * kSoftWarps)
+__global__ void __launch_bounds__(32 * kSoftBwdWarps)
 soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
                      DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
                      SoftScratch W) {
@@ -958,14 +959,15 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
                                  float *grad, float *hvp, int n_sms, cudaStream_t st) {
     launch_soft_items(geom, order, n_pairs, A, W, n_sms, st);
     if (n_pairs > 0) {
-        cudaError_t e = set_soft_smem((const void *)soft_backward_kernel, sizeof(SoftSmemBwd) * kSoftWarps);
+        cudaError_t e = set_soft_smem((const void *)soft_backward_kernel, sizeof(SoftSmemBwd) * kSoftBwdWarps);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_backward_kernel, 32 * kSoftWarps,
-                                                          sizeof(SoftSmemBwd) * kSoftWarps);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_backward_kernel, 32 * kSoftBwdWarps,
+                                                          sizeof(SoftSmemBwd) * kSoftBwdWarps);
         if (e != cudaSuccess) return e;
         soft_loss_kernel<true><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
-        soft_backward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftWarps, sizeof(SoftSmemBwd) * kSoftWarps, st>>>(
+        soft_backward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftBwdWarps, sizeof(SoftSmemBwd) * kSoftBwdWarps,
+                               st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
         soft_chain_kernel<<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W, hvp);
     }
