@@ -97,6 +97,7 @@ def parse():
                     help="only time one soft-NW forward+backward (profiling): on a 4,096-pair tuning minibatch, "
                          "or with --soft-config soft on the 4,096 planted pairs of the soft configuration")
     ap.add_argument("--soft-config", default="tune", choices=["tune", "soft"])
+    ap.add_argument("--soft-pairs", type=int, default=4096, help="pairs of the --soft-step minibatch")
     return ap.parse_args()
 
 
@@ -411,11 +412,11 @@ def soft_step(args):
     import torch
     from paper_1512_01641_gb300 import miner, tune
     if args.soft_config == "soft":
-        td = tune.TuneData(synth.soft_batch())
+        td = tune.TuneData(synth.soft_batch(args.soft_pairs))
     else:
         rng = np.random.Generator(np.random.PCG64(synth.SEED_BASE + 40))
         dic = synth.make_dictionary(rng, 50_000, 50_000)
-        td = tune.TuneData(synth.tune_batch(4096, seed=synth.SEED_BASE + 4, dic=dic))
+        td = tune.TuneData(synth.tune_batch(args.soft_pairs, seed=synth.SEED_BASE + 4, dic=dic))
     al = miner.SoftAligner(td.plan, td.counts, td.gold, 0.1, 0.05)
     p = miner.params_from_theta(tune.THETA0)
     for _ in range(max(args.warmup, 2)):

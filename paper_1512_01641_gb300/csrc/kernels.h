@@ -233,10 +233,10 @@ struct UcScratch {
 };
 // Scores, matches and per-pair kept-link counts (kept), then the compaction
 // of the kept links (s >= thr) at out_off.
+// max_m: the largest M of the pairs (rows in shared memory when they fit).
 cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
                                  int64_t n_pairs, const DevParams &P, const uint8_t *counts, const UcScratch &W,
-                                 float *pair_score, const int64_t *out_off_scan_in, int32_t *kept, int n_sms,
-                                 cudaStream_t st);
+                                 float *pair_score, int max_m, int32_t *kept, int n_sms, cudaStream_t st);
 cudaError_t launch_unconstrained_copy(const PairGeom *geom, int64_t n_pairs, float thr, const UcScratch &W,
                                       const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_s, int n_sms,
                                       cudaStream_t st);

@@ -1248,7 +1248,7 @@ int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint
     W.ls = reinterpret_cast<float *>(b + L.ls);
     int32_t *kept = reinterpret_cast<int32_t *>(b + L.kept);
     const DevParams P = to_dev(*params);
-    MINE_CK(launch_unconstrained(p->src, p->tgt, p->geom, p->pair_order, n, P, counts, W, out->pair_score, nullptr,
+    MINE_CK(launch_unconstrained(p->src, p->tgt, p->geom, p->pair_order, n, P, counts, W, out->pair_score, p->max_m,
                                  kept, p->n_sms, st));
     MINE_CK(launch_scan(kept, n, out->link_off, st));
     MINE_CK(launch_unconstrained_copy(p->geom, n, P.thr, W, out->link_off, out->link_i, out->link_j, out->link_s,

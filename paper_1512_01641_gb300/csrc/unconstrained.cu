@@ -16,6 +16,7 @@
 // warp scans.  Exact ties prefer unmatched, then a forward match, then a move
 // back; among predecessors the nearest pointer; at the end the smallest final
 // pointer.  Scores are FP64 (a comparison baseline, off the mining path).
+#include <algorithm>
 #include <cmath>
 
 #include "kernels.h"
@@ -176,6 +177,142 @@ unconstrained_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
     }
 }
 
+// The same DP with the rows in shared memory (per warp: A of the previous and
+// the current row, and the suffix maxima with their indices) and each row
+// scanned in 32 contiguous segments, one per lane: a lane's serial pass over
+// its segment, then one warp scan of the 32 segment maxima, instead of a warp
+// scan per 32 columns.  Same candidates, same arithmetic, same tie rules.
+__device__ __forceinline__ MaxArg excl_scan_left(MaxArg x, int lane) {  // max over lanes < lane, larger index at ties
+    MaxArg y = warp_max_scan<true, true>(x, lane);
+    MaxArg e{__shfl_up_sync(kFull, y.v, 1), __shfl_up_sync(kFull, y.a, 1)};
+    if (lane == 0) e = {-INFINITY, -1};
+    return e;
+}
+__device__ __forceinline__ MaxArg excl_scan_right(MaxArg x, int lane) {  // max over lanes > lane, smaller index at ties
+    MaxArg y = warp_max_scan<false, false>(x, lane);
+    MaxArg e{__shfl_down_sync(kFull, y.v, 1), __shfl_down_sync(kFull, y.a, 1)};
+    if (lane == 31) e = {-INFINITY, 0x7fffffff};
+    return e;
+}
+
+__global__ void unconstrained_smem_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
+                                          const int32_t *__restrict__ order, int64_t n_pairs, DevParams P,
+                                          const uint8_t *__restrict__ counts, UcScratch W, float *pair_score,
+                                          int mcap) {
+    extern __shared__ __align__(16) unsigned char uc_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *Aa = reinterpret_cast<double *>(uc_smem) + (int64_t)warp * 3 * mcap;
+    double *Ab = Aa + mcap, *Qv = Ab + mcap;
+    int32_t *Qa = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(uc_smem) + (int64_t)(blockDim.x >> 5) * 3 * mcap) +
+                  (int64_t)warp * mcap;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double p = (double)P.gap;
+    const double NEG = -INFINITY;
+    const SimConst K = sim_const(P);
+    for (int64_t x = warp0; x < n_pairs; x += nwarps) {
+        const int32_t k = order[x];
+        const PairGeom g = geom[k];
+        const int N = g.n, M = g.m;
+        int32_t *prev = W.prev + W.prev_off[k];
+        const int64_t sdoc = src.doc[k], tdoc = tgt.doc[k];
+        const int L = (M + 1 + 31) / 32;  // columns 0..M in 32 segments
+        const int lo = lane * L, hi = min(lo + L, M + 1);
+        for (int c = lane; c <= M; c += 32) Aa[c] = c == 0 ? 0.0 : NEG;
+        __syncwarp();
+        for (int i = 1; i <= N; ++i) {
+            const SimRow row = sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P);
+            const uchar2 *crow = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)(i - 1) * M;
+            int32_t *prow = prev + (int64_t)(i - 1) * (M + 1);
+            // suffix maxima of A(i-1, .) inside the segment, right to left
+            MaxArg run{NEG, 0x7fffffff};
+            for (int c = hi - 1; c >= lo; --c) {
+                const double v = Aa[c];
+                if (v >= run.v) run = {v, c};
+                Qv[c] = run.v;
+                Qa[c] = run.a;
+            }
+            const MaxArg right = excl_scan_right(run, lane);
+            // prefix maxima of A(i-1, c) + p c over the lower lanes' segments
+            MaxArg agg{NEG, -1};
+            for (int c = lo; c < hi; ++c) {
+                const double v = Aa[c] + p * (double)c;
+                if (v >= agg.v) agg = {v, c};
+            }
+            MaxArg pre = excl_scan_left(agg, lane);
+            __syncwarp();
+            // candidates of c' in the segment, left to right (pre: the best
+            // forward predecessor c < c')
+            for (int c2 = lo; c2 < hi; ++c2) {
+                const double a_here = Aa[c2];
+                if (c2 >= 1) {
+                    const int lt = (int)(tgt.sent[tdoc + c2] - tgt.sent[tdoc + c2 - 1]);
+                    const uchar2 cq = crow[c2 - 1];
+                    const double sim = (double)similarity(cq.x, cq.y, row, sim_col(lt, P), K);
+                    double best = a_here - p;
+                    int arg = -1;
+                    const double fw = sim + pre.v - p * (double)(c2 - 1);
+                    if (fw > best) {
+                        best = fw;
+                        arg = pre.a;
+                    }
+                    const MaxArg q = right.v > Qv[c2] ? right : MaxArg{Qv[c2], Qa[c2]};
+                    const double bk = sim - p + q.v;
+                    if (bk > best) {
+                        best = bk;
+                        arg = q.a;
+                    }
+                    Ab[c2] = best;
+                    prow[c2] = arg;
+                } else {
+                    Ab[0] = a_here - p;
+                    prow[0] = -1;
+                }
+                const double v = a_here + p * (double)c2;
+                if (v >= pre.v) pre = {v, c2};
+            }
+            __syncwarp();
+            double *t = Aa;
+            Aa = Ab;
+            Ab = t;
+        }
+        MaxArg best{NEG, 0x7fffffff};
+        for (int c = lane; c <= M; c += 32) {
+            const double v = Aa[c] - p * (double)(M - c);
+            if (better(v, c, best, false)) best = {v, c};
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double v = __shfl_xor_sync(kFull, best.v, off);
+            const int a = __shfl_xor_sync(kFull, best.a, off);
+            if (better(v, a, best, false)) best = {v, a};
+        }
+        if (lane == 0) {
+            int c = best.a;
+            int n = 0;
+            int32_t *li = W.li + W.link_off[k], *lj = W.lj + W.link_off[k];
+            float *ls = W.ls + W.link_off[k];
+            for (int i = N; i >= 1; --i) {
+                const int a = prev[(int64_t)(i - 1) * (M + 1) + c];
+                if (a != -1) {
+                    const int slot = N - 1 - n;
+                    const int lt = (int)(tgt.sent[tdoc + c] - tgt.sent[tdoc + c - 1]);
+                    const uchar2 cq = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)(i - 1) * M + c - 1];
+                    li[slot] = i - 1;
+                    lj[slot] = c - 1;
+                    ls[slot] = similarity(cq.x, cq.y, sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P),
+                                          sim_col(lt, P), K);
+                    ++n;
+                    c = a;
+                }
+            }
+            W.n_match[k] = n;
+            pair_score[k] = (float)best.v;
+        }
+        __syncwarp();
+    }
+}
+
 // Links of every pair with s >= thr, in row order, compacted at out_off.
 __global__ void __launch_bounds__(32 * kUcWarps)
 uc_count_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, float thr, UcScratch W, int32_t *kept) {
@@ -230,13 +367,30 @@ int uc_grid(int64_t n_pairs, int n_sms) {
 
 cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
                                  int64_t n_pairs, const DevParams &P, const uint8_t *counts, const UcScratch &W,
-                                 float *pair_score, const int64_t *out_off_scan_in, int32_t *kept, int n_sms,
-                                 cudaStream_t st) {
-    (void)out_off_scan_in;
+                                 float *pair_score, int max_m, int32_t *kept, int n_sms, cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    unconstrained_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(src, tgt, geom, order, n_pairs, P, counts,
-                                                                           W, pair_score);
-    cudaError_t e = cudaGetLastError();
+    // rows in shared memory when one warp's (28 bytes per column) fit
+    const int mcap = max_m + 1;
+    const int64_t per_warp = 28 * (int64_t)mcap;
+    const int warps = (int)std::min<int64_t>(kUcWarps, (200 << 10) / per_warp);
+    cudaError_t e;
+    if (warps >= 1) {
+        const size_t smem = (size_t)(per_warp * warps);
+        e = cudaFuncSetAttribute(unconstrained_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unconstrained_smem_kernel, 32 * warps, smem);
+        if (e != cudaSuccess) return e;
+        int64_t blocks = (n_pairs + warps - 1) / warps;
+        const int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
+        if (blocks > cap) blocks = cap;
+        unconstrained_smem_kernel<<<(unsigned)blocks, 32 * warps, smem, st>>>(src, tgt, geom, order, n_pairs, P, counts,
+                                                                            W, pair_score, mcap);
+    } else {
+        unconstrained_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(src, tgt, geom, order, n_pairs, P,
+                                                                               counts, W, pair_score);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uc_count_kernel<<<uc_grid(n_pairs, n_sms), 32 * kUcWarps, 0, st>>>(geom, n_pairs, P.thr, W, kept);
     return cudaGetLastError();
