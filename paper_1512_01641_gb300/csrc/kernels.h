@@ -225,18 +225,23 @@ struct UcScratch {
     const int64_t *a_off;     // per pair: first double of its two DP rows (2 (M+1))
     const int64_t *prev_off;  // per pair: first int of its predecessor pointers (N (M+1))
     const int64_t *link_off;  // per pair: first slot of its window of N matched cells
-    double *A;
+    int64_t *A;               // two score rows per pair (fixed point, units of 2^-k)
     int32_t *prev;
     int32_t *li, *lj;
     float *ls;
     int32_t *n_match;         // per pair: matched cells (at the end of the window)
 };
+// Pairs whose target has fewer than kUcShortCols sentences run with small
+// shared rows and many warps per SM; the others with rows sized by max_m.
+constexpr int kUcShortCols = 256;
 // Scores, matches and per-pair kept-link counts (kept), then the compaction
-// of the kept links (s >= thr) at out_off.
-// max_m: the largest M of the pairs (rows in shared memory when they fit).
+// of the kept links (s >= thr) at out_off.  order: the pairs with
+// M + 1 <= kUcShortCols first (n_short of them), then the rest; max_m: the
+// largest M of the pairs.
 cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
-                                 int64_t n_pairs, const DevParams &P, const uint8_t *counts, const UcScratch &W,
-                                 float *pair_score, int max_m, int32_t *kept, int n_sms, cudaStream_t st);
+                                 int64_t n_short, int64_t n_pairs, const DevParams &P, const uint8_t *counts,
+                                 const UcScratch &W, float *pair_score, int max_m, int32_t *kept, int n_sms,
+                                 cudaStream_t st);
 cudaError_t launch_unconstrained_copy(const PairGeom *geom, int64_t n_pairs, float thr, const UcScratch &W,
                                       const int64_t *out_off, int32_t *out_i, int32_t *out_j, float *out_s, int n_sms,
                                       cudaStream_t st);

@@ -198,6 +198,8 @@ struct mine_plan {
     mine_params graph_params{};
     int64_t graph_captures = 0;
     std::vector<int64_t> uc_off_h;  // per-pair workspace offsets of the unconstrained aligner
+    std::vector<int32_t> uc_order_h;  // its pair order: short targets first (uc_n_short of them)
+    int64_t uc_n_short = 0;
 };
 
 // Launch f() on stream st; with timing enabled, bracket it by two events.
@@ -1169,7 +1171,7 @@ int mine_links_combine(mine_plan *f, const mine_out *of, mine_plan *r, const min
 namespace {
 
 struct UcLayout {
-    int64_t offs, n_match, kept, A, prev, li, lj, ls, total;
+    int64_t offs, order, n_match, kept, A, prev, li, lj, ls, total;
     int64_t a_total, prev_total, link_total;
 };
 
@@ -1185,6 +1187,8 @@ UcLayout uc_layout(const mine_plan *p) {
     int64_t o = 0;
     L.offs = o;
     o = up(o + 3 * std::max<int64_t>(n, 1) * 8);
+    L.order = o;
+    o = up(o + std::max<int64_t>(n, 1) * 4);
     L.n_match = o;
     o = up(o + std::max<int64_t>(n, 1) * 4);
     L.kept = o;
@@ -1233,23 +1237,34 @@ int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint
             pv += (int64_t)g.n * ((int64_t)g.m + 1);
             lk += g.n;
         }
+        // largest pairs first within each class
+        p->uc_order_h.clear();
+        p->uc_order_h.reserve((size_t)n);
+        for (int32_t k : p->pair_order_h)
+            if (p->geom_h[k].m + 1 <= kUcShortCols) p->uc_order_h.push_back(k);
+        p->uc_n_short = (int64_t)p->uc_order_h.size();
+        for (int32_t k : p->pair_order_h)
+            if (p->geom_h[k].m + 1 > kUcShortCols) p->uc_order_h.push_back(k);
     }
     char *b = static_cast<char *>(ws);
-    if (n > 0) MINE_CK(cudaMemcpyAsync(b + L.offs, p->uc_off_h.data(), 3 * n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (n > 0) {
+        MINE_CK(cudaMemcpyAsync(b + L.offs, p->uc_off_h.data(), 3 * n * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        MINE_CK(cudaMemcpyAsync(b + L.order, p->uc_order_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
     UcScratch W;
     W.a_off = reinterpret_cast<const int64_t *>(b + L.offs);
     W.prev_off = W.a_off + n;
     W.link_off = W.a_off + 2 * n;
     W.n_match = reinterpret_cast<int32_t *>(b + L.n_match);
-    W.A = reinterpret_cast<double *>(b + L.A);
+    W.A = reinterpret_cast<int64_t *>(b + L.A);
     W.prev = reinterpret_cast<int32_t *>(b + L.prev);
     W.li = reinterpret_cast<int32_t *>(b + L.li);
     W.lj = reinterpret_cast<int32_t *>(b + L.lj);
     W.ls = reinterpret_cast<float *>(b + L.ls);
     int32_t *kept = reinterpret_cast<int32_t *>(b + L.kept);
     const DevParams P = to_dev(*params);
-    MINE_CK(launch_unconstrained(p->src, p->tgt, p->geom, p->pair_order, n, P, counts, W, out->pair_score, p->max_m,
-                                 kept, p->n_sms, st));
+    MINE_CK(launch_unconstrained(p->src, p->tgt, p->geom, reinterpret_cast<const int32_t *>(b + L.order), p->uc_n_short,
+                                 n, P, counts, W, out->pair_score, p->max_m, kept, p->n_sms, st));
     MINE_CK(launch_scan(kept, n, out->link_off, st));
     MINE_CK(launch_unconstrained_copy(p->geom, n, P.thr, W, out->link_off, out->link_i, out->link_j, out->link_s,
                                       p->n_sms, st));

@@ -118,11 +118,6 @@ __device__ __forceinline__ float soft3(float s, float a, float b, const SoftCtx 
     return __fmaf_rn(C.kln, lg2_approx(z), m);
 }
 
-__device__ __forceinline__ float cell_similarity(const SoftCtx &C, const SimRow &row, int r, int j) {
-    const uchar2 q = C.cnt[(int64_t)r * C.M + j];
-    return similarity(q.x, q.y, row, sim_col((int)(C.tsent[j + 1] - C.tsent[j]), C.P), C.K);
-}
-
 // Gate, clamped P and dBCE/dP of one cell (dBCE/dP is 0 where P was clamped);
 // the loss term of the cell goes to *bce when asked.
 __device__ __forceinline__ float cell_dldp(float E, float sv, int g, const SoftCtx &C, float &G, float *bce) {
@@ -716,13 +711,14 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
     }
 }
 
-// Sum over a block of 256 threads in a fixed order (butterflies within the
-// warps, then the eight warp sums in warp order); the total reaches thread 0.
-__device__ __forceinline__ double block_sum256(double v, double *ws) {
+// Sum over a block of 256 threads in a fixed order: FP32 butterflies within
+// the warps (each thread's value is itself an FP32 sum of a few terms), then
+// the eight warp sums in warp order in FP64; the total reaches thread 0.
+__device__ __forceinline__ double block_sum256(float v, double *ws) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, off));
     __syncthreads();  // the previous use of ws is complete
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)v;
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
@@ -733,18 +729,18 @@ __device__ __forceinline__ double block_sum256(double v, double *ws) {
 // NV sums over a block of 256 threads at once, in the same fixed order as
 // block_sum256; thread q < NV receives sum q.
 template <int NV>
-__device__ __forceinline__ double block_sums256(const double (&v)[NV], double (*ws)[8]) {
-    double x[NV];
+__device__ __forceinline__ double block_sums256(const float (&v)[NV], double (*ws)[8]) {
+    float x[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         x[q] = v[q];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_xor_sync(kFull, x[q], off);
+        for (int off = 16; off > 0; off >>= 1) x[q] = __fadd_rn(x[q], __shfl_xor_sync(kFull, x[q], off));
     }
     __syncthreads();  // the previous use of ws is complete
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) ws[q][threadIdx.x >> 5] = x[q];
+        for (int q = 0; q < NV; ++q) ws[q][threadIdx.x >> 5] = (double)x[q];
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x < NV)
@@ -815,12 +811,12 @@ soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom
         }
         if (WANT_U) continue;
         // V(N,M) = -N p + sum_j (DOWN output of row N-1 at column j + p)
-        double vs = 0.0;
+        float vs = 0.0f;  // at most M / 256 terms per thread
         if (ch.c0 == 0 && g.n > 0 && g.m > 0) {
             const float *vlast = W.ckv + g.soft_off + (int64_t)((g.n + 31) / 32 - 1) * g.m;
-            for (int j = threadIdx.x; j < g.m; j += blockDim.x) vs += (double)vlast[j] + (double)P.gap;
+            for (int j = threadIdx.x; j < g.m; j += blockDim.x) vs = __fadd_rn(vs, __fadd_rn(vlast[j], P.gap));
         }
-        const double lsum = block_sum256((double)acc, ws);
+        const double lsum = block_sum256(acc, ws);
         const double vsum = ch.c0 == 0 ? block_sum256(vs, ws) : 0.0;
         if (threadIdx.x == 0) {
             W.partial[(int64_t)x * kSoftSlots] = lsum;
@@ -881,10 +877,7 @@ soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geo
             gr[5] = __fmaf_rn(2.0f, Hu, gr[5]);
             gr[6] = __fsub_rn(gr[6], direct);
         }
-        double gd[7];
-#pragma unroll
-        for (int q7 = 0; q7 < 7; ++q7) gd[q7] = (double)gr[q7];
-        const double t = block_sums256<7>(gd, ws);
+        const double t = block_sums256<7>(gr, ws);
         if (threadIdx.x < 7) W.partial[(int64_t)x * kSoftSlots + 1 + threadIdx.x] = t;
     }
 }
