@@ -175,34 +175,30 @@ struct SoftArgs {
     uint32_t *status;    // plan status word (timeout bit)
     int split;           // 0: one warp per pair, 1: split long pairs, 2: split every pair of >= 2 strips
     int64_t skip_ctr;    // fault injection: this forward progress counter is never published (-1: off)
+    float *hvp;          // backward: per cell H u (null: not wanted)
 };
-constexpr int kSoftChunk = 4096;  // cells per chunk of the per-cell kernels
-constexpr int kSoftSlots = 8;     // per chunk: loss sum, seven gradient sums
+constexpr int kSoftSlots = 16;  // per strip: loss sum, the gradient's H u parts, its gate parts
+constexpr int kSoftRedBlocks = 64;  // first-level blocks of the partial sums' reduction
 // Work item of the sweep kernels: a whole pair (kind 0), or one strip of a
 // split pair in the forward wavefront (kind 1) or in the adjoint wavefront
-// (kind 2); ctr = the pair's first progress counter.
+// (kind 2); ctr = the pair's first progress counter, slot = the pair's first
+// strip slot of the partial sums.
 struct SoftItem {
-    int32_t pos, strip, kind, ctr;
-};
-// Chunk of the per-cell kernels: cells [c0, c0 + kSoftChunk) of listed pair pos.
-struct SoftChunk {
-    int32_t pos, pad;
-    int64_t c0;
+    int32_t pos, strip, kind, ctr, slot;
 };
 struct SoftScratch {
-    double *partial;      // per chunk: kSoftSlots sums
+    double *partial;      // per strip slot: kSoftSlots sums
     double *vpart;        // per listed pair: V(N,M)
-    int32_t *queue;       // [0] work counter, [1] items, [2] chunks
+    double *red;          // kSoftRedBlocks x 8: first-level sums of the partial sums
+    int32_t *queue;       // [0] work counter, [1] items, [2] strip slots
     SoftItem *items;      // sweep work list
-    SoftChunk *chunks;    // per-cell work list
     int32_t *prog1;       // per strip of a split pair: forward columns published
     int32_t *prog2;       // per strip of a split pair: adjoint steps published
     float *E;             // expected alignment per cell
-    float *U;             // per cell: u = dL/dE, replaced by H u in the backward
     float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
     float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
     float *ckw;           // per strip: the sweep state at the start of every window
-    int64_t items_cap, chunks_cap, ctr_cap;
+    int64_t items_cap, slots_cap, ctr_cap;
 };
 
 int64_t soft_warps(int n_sms);

@@ -800,33 +800,31 @@ int mine_pairs(mine_plan *p, const mine_params *params, mine_out *out, miner_str
 static int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct SoftLayout {
-    int64_t partial, vpart, queue, items, chunks, prog1, prog2, E, U, ckv, ckt, qrow, qtrow, ckw, total;
-    int64_t items_cap, chunks_cap, ctr_cap;
+    int64_t partial, vpart, red, queue, items, prog1, prog2, E, ckv, ckt, qrow, qtrow, ckw, total;
+    int64_t items_cap, slots_cap, ctr_cap;
 };
 
 static SoftLayout soft_layout(const mine_plan *p) {
     SoftLayout L;
     L.items_cap = p->n_pairs + 2 * p->soft_strips;
-    L.chunks_cap = p->n_pairs + p->n_cells / kSoftChunk + 1;
+    L.slots_cap = p->soft_strips;
     L.ctr_cap = p->soft_strips;
     int64_t o = 0;
     L.partial = o;
-    o = align_up(o + L.chunks_cap * kSoftSlots * (int64_t)sizeof(double), 256);
+    o = align_up(o + std::max<int64_t>(L.slots_cap, 1) * kSoftSlots * (int64_t)sizeof(double), 256);
     L.vpart = o;
     o = align_up(o + std::max<int64_t>(p->n_pairs, 1) * (int64_t)sizeof(double), 256);
+    L.red = o;
+    o = align_up(o + kSoftRedBlocks * 8 * (int64_t)sizeof(double), 256);
     L.queue = o;
     o = align_up(o + 16, 256);
     L.items = o;
     o = align_up(o + std::max<int64_t>(L.items_cap, 1) * (int64_t)sizeof(SoftItem), 256);
-    L.chunks = o;
-    o = align_up(o + L.chunks_cap * (int64_t)sizeof(SoftChunk), 256);
     L.prog1 = o;
     o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
     L.prog2 = o;
     o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
     L.E = o;
-    o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
-    L.U = o;
     o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
     const int64_t rows = std::max<int64_t>(p->soft_rows, 1) * 4;
     L.ckv = o;
@@ -849,20 +847,19 @@ static SoftScratch soft_scratch(const mine_plan *p, void *ws) {
     SoftScratch W;
     W.partial = reinterpret_cast<double *>(b + L.partial);
     W.vpart = reinterpret_cast<double *>(b + L.vpart);
+    W.red = reinterpret_cast<double *>(b + L.red);
     W.queue = reinterpret_cast<int32_t *>(b + L.queue);
     W.items = reinterpret_cast<SoftItem *>(b + L.items);
-    W.chunks = reinterpret_cast<SoftChunk *>(b + L.chunks);
     W.prog1 = reinterpret_cast<int32_t *>(b + L.prog1);
     W.prog2 = reinterpret_cast<int32_t *>(b + L.prog2);
     W.E = reinterpret_cast<float *>(b + L.E);
-    W.U = reinterpret_cast<float *>(b + L.U);
     W.ckv = reinterpret_cast<float *>(b + L.ckv);
     W.ckt = reinterpret_cast<float *>(b + L.ckt);
     W.qrow = reinterpret_cast<float *>(b + L.qrow);
     W.qtrow = reinterpret_cast<float *>(b + L.qtrow);
     W.ckw = reinterpret_cast<float *>(b + L.ckw);
     W.items_cap = L.items_cap;
-    W.chunks_cap = L.chunks_cap;
+    W.slots_cap = L.slots_cap;
     W.ctr_cap = L.ctr_cap;
     return W;
 }
@@ -876,6 +873,7 @@ static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, con
     A.status = p->S.status;
     A.split = p->knobs.soft_split;
     A.skip_ctr = p->knobs.skip_soft;
+    A.hvp = nullptr;
     int64_t cells = p->n_cells;
     order = p->pair_order;
     n = p->n_pairs;

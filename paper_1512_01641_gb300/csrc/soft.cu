@@ -30,27 +30,29 @@
 // Because every path takes N + M - 2 #diag gap steps, V(s,p) = V0(s + 2p) -
 // p (N + M), so dE/dp = 2 H 1 and dL/dp (through E) = 2 sum(H u).
 //
-// Memory: per cell only E and u are kept (u is computed at the start of the
-// backward and replaced by H u in place).  The
-// forward sweeps checkpoint the boundary row of every 32-row strip; a backward
-// sweep recomputes the strip's forward from its checkpoint into a per-warp
-// strip buffer (anti-diagonal major, so that both the skewed forward and the
-// reverse-skewed backward move 128 contiguous bytes per step) and then runs
-// the reverse sweep over it.  One warp owns a pair.
+// Memory: per cell only E is kept.  The value sweeps checkpoint the boundary
+// row of every 32-row strip and the sweep state at the start of every
+// 8-step window; an adjoint sweep recomputes a window's forward steps from
+// that state into shared memory and then runs the reverse steps over them.
+// One warp owns a pair, or one strip of a pair split over warps.
 //
-// The sweeps carry only the recurrences: the similarities (and u) of a
-// 32 x 32 block are computed before its 32 steps into shared memory (rotated,
-// so that writes and the skewed reads hit distinct banks), and the reverse
-// sweeps fetch their per-cell weights eight steps ahead.  The loss, u and the
-// chain rule to the seven parameters are per-cell work, done by separate
-// fully parallel kernels.
+// The sweeps carry the recurrences and the per-cell work: the similarities
+// (and, in the backward, u = dL/dE from E and the gold links) of a 32 x 32
+// block are computed before its 32 steps into shared memory (rotated, so
+// that writes and the skewed reads hit distinct banks); the forward's reverse
+// steps add each cell's loss term where E is formed, the backward's reverse
+// steps each cell's chain rule to the seven parameters where H u is formed.
+// Per strip the sums go, in a fixed order, to the strip's slot of the
+// partial sums, so that splitting a pair over warps changes no bit.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace gbm {
 namespace {
 
 constexpr int kSoftWarps = 4;
-constexpr int kSoftBwdWarps = 2;  // the backward's 22.5 KB of shared memory per warp: five 2-warp CTAs per SM
+constexpr int kSoftBwdWarps = 2;  // 23 KB of shared memory per warp: four 2-warp CTAs per SM
 constexpr int kWin = 8;  // steps of a window of the adjoint sweep's recompute
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -70,8 +72,8 @@ struct SoftCtx {
     const uchar2 *cnt;     // pair's counts
     const uint8_t *gold;   // pair's gold links (0/1 per cell)
     float *E;              // pair's expected alignment
-    float *U;              // pair's tangent direction u = dL/dE, then H u
-    SimCol *colv;          // shared: column constants of the block being prepared
+    float *hvp;            // pair's H u output (backward, may be null)
+    SimCol (*colb)[32];    // shared: column constants of the current and previous block [2][col]
     float (*svb)[32][32];  // shared: similarities of the current and previous block [2][row][col]
     float (*ub)[32][32];   // shared: u of the current and previous block (TAN)
     float (*wb)[kWin][32]; // shared: the recomputed window's per-cell weights [component][step][lane]
@@ -130,14 +132,16 @@ __device__ __forceinline__ float cell_dldp(float E, float sv, int g, const SoftC
     return __fmul_rn(g ? -rcp_approx(Pr) : rcp_approx(__fsub_rn(1.0f, Pr)), C.inv_cells);
 }
 
-// Similarities (and u) of block jb of the current strip into shared buffer
-// jb & 1; lane = row, columns written in rotated order.
+// Similarities (and, TAN, u = dL/dE from E and the gold links) of block jb
+// of the current strip into shared buffer jb & 1 with the block's column
+// constants; lane = row, columns written in rotated order.
 template <bool TAN>
 __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv, int jb) {
     const int lane = C.lane;
     const int col0 = 32 * jb;
+    SimCol *cv = C.colb[jb & 1];
     __syncwarp();
-    C.colv[lane] = sim_col(col0 + lane < C.M ? (int)(C.tsent[col0 + lane + 1] - C.tsent[col0 + lane]) : 1, C.P);
+    cv[lane] = sim_col(col0 + lane < C.M ? (int)(C.tsent[col0 + lane + 1] - C.tsent[col0 + lane]) : 1, C.P);
     __syncwarp();
     float(*sv)[32] = C.svb[jb & 1];
     float(*ub)[32] = C.ub[jb & 1];
@@ -149,8 +153,12 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv
         float v = 0.0f, u = 0.0f;
         if (rv && col < C.M) {
             const uchar2 q = rowc[col];
-            v = similarity(q.x, q.y, C.row, C.colv[c], C.K);
-            if (TAN) u = C.U[(int64_t)r * C.M + col];
+            v = similarity(q.x, q.y, C.row, cv[c], C.K);
+            if (TAN) {
+                const int64_t cell = (int64_t)r * C.M + col;
+                float G;
+                u = __fmul_rn(cell_dldp(C.E[cell], v, C.gold[cell], C, G, nullptr), G);
+            }
         }
         sv[lane][c] = v;
         if (TAN) ub[lane][c] = u;
@@ -281,6 +289,29 @@ struct RevState {
     float q_send, dflow, qright, qt_send, dtflow, qtright;
 };
 
+// Per-lane sums of the per-cell terms of a strip: the loss (forward) or the
+// seven gradient components (backward), in FP32 over one 32-column block,
+// then folded into FP64.
+struct SoftAcc {
+    float f[7];
+    double d[7];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            f[q] = 0.0f;
+            d[q] = 0.0;
+        }
+    }
+    template <int NV>
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            d[q] += (double)f[q];
+            f[q] = 0.0f;
+        }
+    }
+};
+
 template <bool TAN>
 __device__ __forceinline__ void soft_fwd_window(SoftCtx &C, int s, int t0, float hv, float htv,
                                                 const float *__restrict__ ckw_w) {
@@ -316,9 +347,46 @@ __device__ __forceinline__ void soft_fwd_window(SoftCtx &C, int s, int t0, float
     }
 }
 
+// The similarity's features of a cell (count pair in the low bytes of qg):
+// ms / ls, mt / lt, 1 - q, q with q = min(ls / lt, lt / ls), through the rows'
+// and columns' reciprocals (a rounding more than the IEEE quotients: far
+// below the gradient's tolerance).
+__device__ __forceinline__ void cell_features(const SoftCtx &C, uint32_t qg, const SimCol &sc, float (&f)[4]) {
+    f[0] = __fmul_rn(small_int_float((int)(qg & 0xFFu)), C.row.rlen);
+    f[1] = __fmul_rn(small_int_float((int)((qg >> 8) & 0xFFu)), sc.rlen);
+    f[3] = fminf(__fmul_rn(C.row.len, sc.rlen), __fmul_rn(sc.len, C.row.rlen));
+    f[2] = __fsub_rn(1.0f, f[3]);
+}
+
+// The per-cell inputs of a window's cells (forward step t0 + kk, lane's
+// column t0 + kk - lane): the count pair and, in the forward, the gold link,
+// loaded before the window's forward recompute so that their latency
+// overlaps it.
+struct CellIn {
+    uint32_t qg[kWin];  // count pair (bytes 0, 1) | gold (byte 2)
+};
 template <bool TAN>
-__device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevState &R, float *qrow, float *qtrow,
-                                                float rgamma, const int32_t *wait_below, int32_t *pub, int &have) {
+__device__ __forceinline__ void soft_cell_inputs(const SoftCtx &C, int s, int t0, CellIn &X) {
+    const int lane = C.lane;
+    const int r = 32 * s + lane;
+    const bool rv = r < C.N;
+#pragma unroll
+    for (int kk = 0; kk < kWin; ++kk) {
+        const int j = t0 + kk - lane;
+        X.qg[kk] = 0u;
+        if (rv && j >= 0 && j < C.M) {
+            const int64_t c = (int64_t)r * C.M + j;
+            const uchar2 q = C.cnt[c];
+            X.qg[kk] = (uint32_t)q.x | ((uint32_t)q.y << 8);
+            if (!TAN) X.qg[kk] |= (uint32_t)C.gold[c] << 16;
+        }
+    }
+}
+
+template <bool TAN>
+__device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevState &R, SoftAcc &Z, const CellIn &X,
+                                                float *qrow, float *qtrow, float rgamma, const int32_t *wait_below,
+                                                int32_t *pub, int &have) {
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
@@ -360,6 +428,7 @@ __device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevSt
             R.q_send = __fadd_rn(__fmul_rn(Q, wu), R.dflow);
             R.dflow = Ec;
             const int64_t c = (int64_t)r * C.M + j;
+            const float sv = C.svb[(j >> 5) & 1][lane][j & 31];
             if (TAN) {
                 // weight tangents w_k' = w_k (c_k - D') / gamma
                 const float wdt = __fmul_rn(__fmul_rn(wd, C.wb[3][kk][lane]), rgamma);
@@ -369,10 +438,35 @@ __device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevSt
                 R.qtright = __fmaf_rn(Q, wlt, __fmul_rn(Qt, wl));
                 R.qt_send = __fadd_rn(__fmaf_rn(Q, wut, __fmul_rn(Qt, wu)), R.dtflow);
                 R.dtflow = Hu;
-                C.U[c] = Hu;
+                if (C.hvp) C.hvp[c] = Hu;
                 if (lane == 0) __stcg(qtrow + j, R.qt_send);
+                // the cell's chain rule, H u part: dL/ds gets H u, then to w
+                // (through s(1-s) and the features), b and gap (2 H u); the
+                // part through the gate (dL/dP E dG/ds) is summed by the forward
+                const float dz = __fmul_rn(Hu, __fmul_rn(sv, __fsub_rn(1.0f, sv)));
+                float f[4];
+                cell_features(C, X.qg[kk], C.colb[(j >> 5) & 1][j & 31], f);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) Z.f[q4] = __fmaf_rn(dz, f[q4], Z.f[q4]);
+                Z.f[4] = __fadd_rn(Z.f[4], dz);
+                Z.f[5] = __fmaf_rn(2.0f, Hu, Z.f[5]);
             } else {
                 C.E[c] = Ec;
+                // the cell's loss term and the part of dL/ds through the gate,
+                // dL/dP E dG/ds, to w (through s(1-s) and the features), b
+                // and thr
+                float G, bce;
+                const float lp = cell_dldp(Ec, sv, (int)(X.qg[kk] >> 16), C, G, &bce);
+                Z.f[0] = __fadd_rn(Z.f[0], bce);
+                const float gg = __fmul_rn(__fmul_rn(G, __fsub_rn(1.0f, G)), C.ktau * kLn2);
+                const float direct = __fmul_rn(__fmul_rn(lp, Ec), gg);
+                const float dz = __fmul_rn(direct, __fmul_rn(sv, __fsub_rn(1.0f, sv)));
+                float f[4];
+                cell_features(C, X.qg[kk], C.colb[(j >> 5) & 1][j & 31], f);
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4) Z.f[1 + q4] = __fmaf_rn(dz, f[q4], Z.f[1 + q4]);
+                Z.f[5] = __fadd_rn(Z.f[5], dz);
+                Z.f[6] = __fsub_rn(Z.f[6], direct);
             }
             if (lane == 0) __stcg(qrow + j, R.q_send);
         } else {
@@ -387,8 +481,9 @@ __device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevSt
 template <bool TAN>
 __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const float *__restrict__ ckv_top,
                                                    const float *__restrict__ ckt_top, const float *__restrict__ ckw,
-                                                   float *qrow, float *qtrow, float rgamma,
+                                                   SoftAcc &Z, float *qrow, float *qtrow, float rgamma,
                                                    const int32_t *wait_below = nullptr, int32_t *pub = nullptr) {
+    constexpr int NV = TAN ? 6 : 7;
     const int lane = C.lane;
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
@@ -401,6 +496,7 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
     for (int w = (C.M + 30) / kWin; w >= 0; --w) {
         const int t0 = w * kWin, jb = t0 >> 5;
         if (jb != cur) {
+            Z.fold<NV>();
             // windows of block jb read blocks jb and jb - 1; going left, block jb
             // is ready from block jb + 1's windows except at the start
             if (cur < 0 && jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
@@ -411,11 +507,31 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
             hv = top ? __ldcg(ckv_top + colx) : -C.two_p;
             htv = (TAN && top) ? __ldcg(ckt_top + colx) : 0.0f;
         }
+        CellIn X;
+        soft_cell_inputs<TAN>(C, s, t0, X);
         soft_fwd_window<TAN>(C, s, t0, hv, htv, ckw + (int64_t)w * 128);
         __syncwarp();
-        soft_rev_window<TAN>(C, s, t0, R, qrow, qtrow, rgamma, wait_below, pub, have);
+        soft_rev_window<TAN>(C, s, t0, R, Z, X, qrow, qtrow, rgamma, wait_below, pub, have);
         __syncwarp();
     }
+    Z.fold<NV>();
+}
+
+// The strip's sums over the warp (FP64 butterflies, a fixed order) into its
+// slot of the partial sums.  Forward: the loss at slot[0], the gate parts of
+// the gradient (w0..w3, b, thr) at slot[8 + q]; backward: the H u parts
+// (w0..w3, b, gap) at slot[1 + q].
+template <bool TAN>
+__device__ __forceinline__ void soft_store_strip(const SoftAcc &Z, double *slot, int lane) {
+    constexpr int kSlot[2][7] = {{0, 8, 9, 10, 11, 12, 14}, {1, 2, 3, 4, 5, 6, 7}};
+#pragma unroll
+    for (int q = 0; q < (TAN ? 6 : 7); ++q) {
+        double v = Z.d[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) slot[kSlot[TAN][q]] = v;
+    }
+    if (lane == 0) slot[TAN ? 7 : 13] = 0.0;  // no H u part of thr, no gate part of gap
 }
 
 __device__ __forceinline__ bool next_item(int32_t *queue, int32_t n, int lane, int32_t &it) {
@@ -436,7 +552,7 @@ __device__ __forceinline__ void ctx_for_pair(SoftCtx &C, const PairGeom &g, int6
     C.cnt = reinterpret_cast<const uchar2 *>(counts) + g.cell_off;
     C.gold = gold + g.cell_off;
     C.E = W.E + g.cell_off;
-    C.U = W.U + g.cell_off;
+    C.hvp = nullptr;
 }
 
 __device__ __forceinline__ SoftCtx make_ctx(const DevParams &P, const SoftArgs &A) {
@@ -463,13 +579,13 @@ __device__ __forceinline__ SoftCtx make_ctx(const DevParams &P, const SoftArgs &
 struct SoftSmemFwd {
     float sv[2][32][32];
     float wb[3][kWin][32];
-    SimCol colv[32];
+    SimCol colv[2][32];
 };
 struct SoftSmemBwd {
     float sv[2][32][32];
     float ub[2][32][32];
     float wb[6][kWin][32];
-    SimCol colv[32];
+    SimCol colv[2][32];
 };
 
 template <bool TAN>
@@ -479,13 +595,13 @@ __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
         C.svb = sm.sv;
         C.ub = sm.ub;
         C.wb = sm.wb;
-        C.colv = sm.colv;
+        C.colb = sm.colv;
     } else {
         SoftSmemFwd &sm = reinterpret_cast<SoftSmemFwd *>(raw)[threadIdx.x >> 5];
         C.svb = sm.sv;
         C.ub = nullptr;
         C.wb = sm.wb;
-        C.colv = sm.colv;
+        C.colb = sm.colv;
     }
 }
 
@@ -494,7 +610,7 @@ __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
 // strips run on different warps, the value sweep top-down (kind 1) and the
 // recompute + adjoint sweep bottom-up (kind 2), each strip a little behind
 // its neighbour.  Every wait is on an item listed (so dequeued) earlier.
-__global__ void __launch_bounds__(32 * kSoftWarps)
+__global__ void __launch_bounds__(32 * kSoftWarps, 4)
 soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
                     DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
                     SoftScratch W) {
@@ -521,7 +637,12 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
             for (int s = 0; s < S; ++s)
                 soft_fwd_strip<false>(C, s, top(s), nullptr, s + 1 < S ? ckv + (int64_t)s * C.M : nullptr, nullptr,
                                       ckw(s), s + 1 == S ? vlast : nullptr);
-            for (int s = S - 1; s >= 0; --s) soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), qrow, nullptr, 0.0f);
+            for (int s = S - 1; s >= 0; --s) {
+                SoftAcc Z;
+                Z.clear();
+                soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), Z, qrow, nullptr, 0.0f);
+                soft_store_strip<false>(Z, W.partial + (int64_t)(I.slot + s) * kSoftSlots, lane);
+            }
         } else {
             const int s = I.strip;
             int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
@@ -532,8 +653,11 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
             } else {
                 int have = 0;  // this strip's value sweep (and so the one above) complete
                 soft_wait(C, p1 + s, C.M, have);
-                soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), qrow, nullptr, 0.0f,
+                SoftAcc Z;
+                Z.clear();
+                soft_adjoint_strip<false>(C, s, top(s), nullptr, ckw(s), Z, qrow, nullptr, 0.0f,
                                           s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
+                soft_store_strip<false>(Z, W.partial + (int64_t)(I.slot + s) * kSoftSlots, lane);
             }
         }
     }
@@ -557,6 +681,7 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
         const int32_t k = order[I.pos];
         const PairGeom g = geom[k];
         ctx_for_pair(C, g, k, src, tgt, counts, gold, W);
+        C.hvp = A.hvp ? A.hvp + g.cell_off : nullptr;
         C.failed = false;
         if (C.N <= 0 || C.M <= 0) continue;
         const int S = C.nstrips;
@@ -571,8 +696,12 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
             for (int s = 0; s < S; ++s)
                 soft_fwd_strip<true>(C, s, topv(s), topt(s), s + 1 < S ? ckv + (int64_t)s * C.M : nullptr,
                                      s + 1 < S ? ckt + (int64_t)s * C.M : nullptr, ckw(s), nullptr);
-            for (int s = S - 1; s >= 0; --s)
-                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), qrow, qtrow, rgamma);
+            for (int s = S - 1; s >= 0; --s) {
+                SoftAcc Z;
+                Z.clear();
+                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), Z, qrow, qtrow, rgamma);
+                soft_store_strip<true>(Z, W.partial + (int64_t)(I.slot + s) * kSoftSlots, lane);
+            }
         } else {
             const int s = I.strip;
             int32_t *p1 = W.prog1 + I.ctr, *p2 = W.prog2 + I.ctr;
@@ -584,8 +713,11 @@ soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ 
             } else {
                 int have = 0;  // this strip's value sweep (and so the one above) complete
                 soft_wait(C, p1 + s, C.M, have);
-                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), qrow, qtrow, rgamma,
+                SoftAcc Z;
+                Z.clear();
+                soft_adjoint_strip<true>(C, s, topv(s), topt(s), ckw(s), Z, qrow, qtrow, rgamma,
                                          s + 1 < S ? p2 + s + 1 : nullptr, p2 + s);
+                soft_store_strip<true>(Z, W.partial + (int64_t)(I.slot + s) * kSoftSlots, lane);
             }
         }
     }
@@ -625,8 +757,8 @@ __device__ int64_t block_scan(int64_t v, int64_t &total) {
 // (split = 1; every such pair with split = 2, none with split = 0).  Split
 // pairs come first, each as S value-sweep items (top-down) followed by S
 // adjoint items (bottom-up), then the whole pairs in list order.  Every
-// listed pair also gets ceil(cells / kSoftChunk) (at least one) chunks of
-// per-cell work.  Zeroes the progress counters and the work counter.
+// listed pair with cells gets S slots of per-strip partial sums, in list
+// order.  Zeroes the progress counters and the work counter.
 __global__ void __launch_bounds__(1024)
 soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs,
                   int64_t n_warps, int split, uint32_t *status, SoftScratch W) {
@@ -644,29 +776,28 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
     }
     (void)block_scan(chain, tot);
     const int64_t thr = split == 2 ? 0 : (split == 1 ? tot / (n_warps > 0 ? n_warps : 1) : INT64_MAX);
-    auto counts = [&](int64_t pos, int64_t &si, int64_t &sc, int64_t &wi, int64_t &ch) {
+    auto counts = [&](int64_t pos, int64_t &si, int64_t &sc, int64_t &wi, int64_t &sl) {
         int32_t n, m;
         const int64_t S = strips(pos, n, m);
         const bool sp = S >= 2 && m > 0 && S * (m + 32) > thr;
         si = sp ? 2 * S : 0;
         sc = sp ? S : 0;
         wi = sp ? 0 : 1;
-        const int64_t cells = (int64_t)n * m;
-        ch = cells > 0 ? (cells + kSoftChunk - 1) / kSoftChunk : 1;
+        sl = m > 0 ? S : 0;
     };
     // totals, checked against the workspace
     int64_t a[4] = {0, 0, 0, 0};
     for (int64_t pos = threadIdx.x; pos < n_pairs; pos += blockDim.x) {
-        int64_t si, sc, wi, ch;
-        counts(pos, si, sc, wi, ch);
+        int64_t si, sc, wi, sl;
+        counts(pos, si, sc, wi, sl);
         a[0] += si;
         a[1] += sc;
         a[2] += wi;
-        a[3] += ch;
+        a[3] += sl;
     }
     int64_t T[4];
     for (int q = 0; q < 4; ++q) (void)block_scan(a[q], T[q]);
-    const bool fits = T[0] + T[2] <= W.items_cap && T[1] <= W.ctr_cap && T[3] <= W.chunks_cap;
+    const bool fits = T[0] + T[2] <= W.items_cap && T[1] <= W.ctr_cap && T[3] <= W.slots_cap;
     if (!fits) {
         if (threadIdx.x == 0) {
             atomicOr(status, kStBadList);
@@ -676,33 +807,32 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
         }
         return;
     }
-    int64_t c_si = 0, c_sc = 0, c_wi = 0, c_ch = 0;
+    int64_t c_si = 0, c_sc = 0, c_wi = 0, c_sl = 0;
     for (int64_t base = 0; base < n_pairs; base += blockDim.x) {
         const int64_t pos = base + threadIdx.x;
-        int64_t si = 0, sc = 0, wi = 0, ch = 0;
-        if (pos < n_pairs) counts(pos, si, sc, wi, ch);
+        int64_t si = 0, sc = 0, wi = 0, sl = 0;
+        if (pos < n_pairs) counts(pos, si, sc, wi, sl);
         int64_t t0, t1, t2, t3;
         const int64_t o_si = c_si + block_scan(si, t0);
         const int64_t o_sc = c_sc + block_scan(sc, t1);
         const int64_t o_wi = c_wi + block_scan(wi, t2);
-        const int64_t o_ch = c_ch + block_scan(ch, t3);
+        const int64_t o_sl = c_sl + block_scan(sl, t3);
         c_si += t0;
         c_sc += t1;
         c_wi += t2;
-        c_ch += t3;
+        c_sl += t3;
         if (pos >= n_pairs) continue;
         if (si) {
             const int32_t S = (int32_t)sc;
             for (int32_t s = 0; s < S; ++s) {
-                W.items[o_si + s] = SoftItem{(int32_t)pos, s, 1, (int32_t)o_sc};
-                W.items[o_si + 2 * S - 1 - s] = SoftItem{(int32_t)pos, s, 2, (int32_t)o_sc};
+                W.items[o_si + s] = SoftItem{(int32_t)pos, s, 1, (int32_t)o_sc, (int32_t)o_sl};
+                W.items[o_si + 2 * S - 1 - s] = SoftItem{(int32_t)pos, s, 2, (int32_t)o_sc, (int32_t)o_sl};
                 W.prog1[o_sc + s] = 0;
                 W.prog2[o_sc + s] = 0;
             }
         } else {
-            W.items[T[0] + o_wi] = SoftItem{(int32_t)pos, 0, 0, 0};
+            W.items[T[0] + o_wi] = SoftItem{(int32_t)pos, 0, 0, 0, (int32_t)o_sl};
         }
-        for (int64_t c = 0; c < ch; ++c) W.chunks[o_ch + c] = SoftChunk{(int32_t)pos, 0, c * kSoftChunk};
     }
     if (threadIdx.x == 0) {
         W.queue[0] = 0;
@@ -711,194 +841,70 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
     }
 }
 
-// Sum over a block of 256 threads in a fixed order: FP32 butterflies within
-// the warps (each thread's value is itself an FP32 sum of a few terms), then
-// the eight warp sums in warp order in FP64; the total reaches thread 0.
-__device__ __forceinline__ double block_sum256(float v, double *ws) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, off));
-    __syncthreads();  // the previous use of ws is complete
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < 8; ++w) t += ws[w];
-    return t;
-}
-
-// NV sums over a block of 256 threads at once, in the same fixed order as
-// block_sum256; thread q < NV receives sum q.
-template <int NV>
-__device__ __forceinline__ double block_sums256(const float (&v)[NV], double (*ws)[8]) {
-    float x[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        x[q] = v[q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x[q] = __fadd_rn(x[q], __shfl_xor_sync(kFull, x[q], off));
-    }
-    __syncthreads();  // the previous use of ws is complete
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) ws[q][threadIdx.x >> 5] = (double)x[q];
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < NV)
-        for (int w = 0; w < 8; ++w) t += ws[threadIdx.x][w];
-    return t;
-}
-
-// Row and column of the cells a thread visits in a chunk (cells c0 + t,
-// c0 + t + 256, ... of a pair with M columns): one 32-bit division per thread
-// and chunk, then constant steps; the sentence lengths of the current row and
-// column are kept (the row changes rarely).
-struct CellWalk {
-    int i, j, si, sj;  // current cell, step per visit (256 = si M + sj)
-    __device__ __forceinline__ CellWalk(int64_t c0, int t, int M) {
-        const uint32_t i0 = (uint32_t)(c0 / M), j0 = (uint32_t)(c0 - (int64_t)i0 * M) + (uint32_t)t;
-        i = (int)(i0 + j0 / (uint32_t)M);
-        j = (int)(j0 % (uint32_t)M);
-        si = 256 / M;
-        sj = 256 % M;
-    }
-    __device__ __forceinline__ void next(int M) {
-        i += si;
-        j += sj;
-        if (j >= M) {
-            j -= M;
-            ++i;
-        }
-    }
-};
-
-// Per-cell work of the loss: gate, clamped P and BCE (summed per chunk), or
-// (WANT_U) the tangent direction u = dL/dE of the backward.  One block per
-// chunk of kSoftChunk cells; the first chunk of a pair also sums V(N,M).
-template <bool WANT_U>
+// V(N,M) of every listed pair (one warp per pair) from the DOWN outputs of
+// its last row, V(N,j) - V(N,j-1) - p (written by the value sweep):
+// V(N,M) = -N p + sum_j (output_j + p), lane-strided FP32 partial sums and
+// an FP64 butterfly in a fixed order.
 __global__ void __launch_bounds__(256)
-soft_loss_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                 DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
-                 SoftScratch W) {
-    __shared__ double ws[8];
-    SoftCtx C = make_ctx(P, A);
-    const int32_t n_chunks = W.queue[2];
-    for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
-        const SoftChunk ch = W.chunks[x];
-        const int32_t k = order[ch.pos];
-        const PairGeom g = geom[k];
-        const int64_t sb = src.doc[k], tb = tgt.doc[k];
-        const int64_t cells = (int64_t)g.n * g.m;
-        const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
-        float acc = 0.0f;  // at most kSoftChunk / 256 terms per thread
-        CellWalk cw(ch.c0, threadIdx.x, g.m > 0 ? g.m : 1);
-        int row_i = -1;
-        SimRow srow{};
-        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x, cw.next(g.m)) {
-            if (cw.i != row_i) {
-                row_i = cw.i;
-                srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
-            }
-            const uchar2 q = __ldg(reinterpret_cast<const uchar2 *>(counts) + g.cell_off + c);
-            const float sv = similarity(
-                q.x, q.y, srow, sim_col((int)(__ldg(tgt.sent + tb + cw.j + 1) - __ldg(tgt.sent + tb + cw.j)), P), C.K);
-            float G, bce;
-            const float lp = cell_dldp(__ldg(W.E + g.cell_off + c), sv, __ldg(gold + g.cell_off + c), C, G,
-                                       WANT_U ? nullptr : &bce);
-            if (WANT_U)
-                W.U[g.cell_off + c] = __fmul_rn(lp, G);
-            else
-                acc = __fadd_rn(acc, bce);
+soft_value_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs, DevParams P,
+                  SoftScratch W) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = warp0; x < n_pairs; x += nwarps) {
+        const PairGeom g = geom[order[x]];
+        if (g.n <= 0 || g.m <= 0) {
+            if (lane == 0) W.vpart[x] = -(double)P.gap * (double)(g.n + g.m);
+            continue;
         }
-        if (WANT_U) continue;
-        // V(N,M) = -N p + sum_j (DOWN output of row N-1 at column j + p)
-        float vs = 0.0f;  // at most M / 256 terms per thread
-        if (ch.c0 == 0 && g.n > 0 && g.m > 0) {
-            const float *vlast = W.ckv + g.soft_off + (int64_t)((g.n + 31) / 32 - 1) * g.m;
-            for (int j = threadIdx.x; j < g.m; j += blockDim.x) vs = __fadd_rn(vs, __fadd_rn(vlast[j], P.gap));
-        }
-        const double lsum = block_sum256(acc, ws);
-        const double vsum = ch.c0 == 0 ? block_sum256(vs, ws) : 0.0;
-        if (threadIdx.x == 0) {
-            W.partial[(int64_t)x * kSoftSlots] = lsum;
-            if (ch.c0 == 0)
-                W.vpart[ch.pos] = (g.n > 0 && g.m > 0) ? vsum - (double)P.gap * (double)g.n
-                                                       : -(double)P.gap * (double)(g.n + g.m);
-        }
-    }
-}
-
-// Per-cell chain rule: dL/ds = H u + dL/dP E dG/ds, then to w, b (through
-// s(1-s) f), gap (2 H u) and thr (-dL/dP E dG/ds).  One block per chunk.
-__global__ void __launch_bounds__(256)
-soft_chain_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
-                  DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
-                  SoftScratch W, float *__restrict__ hvp) {
-    __shared__ double ws[7][8];
-    SoftCtx C = make_ctx(P, A);
-    const int32_t n_chunks = W.queue[2];
-    for (int32_t x = blockIdx.x; x < n_chunks; x += gridDim.x) {
-        const SoftChunk ch = W.chunks[x];
-        const int32_t k = order[ch.pos];
-        const PairGeom g = geom[k];
-        const int64_t sb = src.doc[k], tb = tgt.doc[k];
-        const int64_t cells = (int64_t)g.n * g.m;
-        const int64_t c1 = ch.c0 + kSoftChunk < cells ? ch.c0 + kSoftChunk : cells;
-        float gr[7] = {0, 0, 0, 0, 0, 0, 0};  // at most kSoftChunk / 256 terms per thread
-        CellWalk cw(ch.c0, threadIdx.x, g.m > 0 ? g.m : 1);
-        int row_i = -1;
-        SimRow srow{};
-        for (int64_t c = ch.c0 + threadIdx.x; c < c1; c += blockDim.x, cw.next(g.m)) {
-            if (cw.i != row_i) {
-                row_i = cw.i;
-                srow = sim_row((int)(src.sent[sb + row_i + 1] - src.sent[sb + row_i]), P);
-            }
-            const SimCol scol = sim_col((int)(__ldg(tgt.sent + tb + cw.j + 1) - __ldg(tgt.sent + tb + cw.j)), P);
-            const uchar2 q = __ldg(reinterpret_cast<const uchar2 *>(counts) + g.cell_off + c);
-            const float sv = similarity(q.x, q.y, srow, scol, C.K);
-            const float Es = __ldg(W.E + g.cell_off + c);
-            const float Hu = __ldg(W.U + g.cell_off + c);
-            if (hvp) hvp[g.cell_off + c] = Hu;
-            float G;
-            const float lp = cell_dldp(Es, sv, __ldg(gold + g.cell_off + c), C, G, nullptr);
-            const float gg = __fmul_rn(__fmul_rn(G, __fsub_rn(1.0f, G)), C.ktau * kLn2);
-            const float direct = __fmul_rn(__fmul_rn(lp, Es), gg);  // dL/ds through the gate
-            const float dlds = __fadd_rn(Hu, direct);
-            const float dz = __fmul_rn(dlds, __fmul_rn(sv, __fsub_rn(1.0f, sv)));
-            // the features through the rows' and columns' reciprocals (a rounding
-            // more than the IEEE quotients: far below the gradient's tolerance)
-            float f[4];
-            f[0] = __fmul_rn(small_int_float(q.x), srow.rlen);
-            f[1] = __fmul_rn(small_int_float(q.y), scol.rlen);
-            f[3] = fminf(__fmul_rn(srow.len, scol.rlen), __fmul_rn(scol.len, srow.rlen));
-            f[2] = __fsub_rn(1.0f, f[3]);
+        const float *vlast = W.ckv + g.soft_off + (int64_t)((g.n + 31) / 32 - 1) * g.m;
+        float acc = 0.0f;
+        for (int j = lane; j < g.m; j += 32) acc = __fadd_rn(acc, __fadd_rn(vlast[j], P.gap));
+        double v = (double)acc;
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) gr[q4] = __fmaf_rn(dz, f[q4], gr[q4]);
-            gr[4] = __fadd_rn(gr[4], dz);
-            gr[5] = __fmaf_rn(2.0f, Hu, gr[5]);
-            gr[6] = __fsub_rn(gr[6], direct);
-        }
-        const double t = block_sums256<7>(gr, ws);
-        if (threadIdx.x < 7) W.partial[(int64_t)x * kSoftSlots + 1 + threadIdx.x] = t;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+        if (lane == 0) W.vpart[x] = v - (double)P.gap * (double)g.n;
     }
 }
 
-// Fixed-order reduction of the per-chunk partials (one block).
+// Fixed-order reduction of the per-strip partial sums in two launches:
+// block b of kSoftRedBlocks sums the slots [b per, (b + 1) per) (thread t
+// the slots t, t + 256, ... of that range, then a tree over the block) into
+// red[b]; one block then sums red[0..] in order.  out[q] = scale * the sum of
+// partial[first + q] (+ partial[first2 + q] when TWO), q < COUNT.
+template <int COUNT, bool TWO>
 __global__ void __launch_bounds__(256)
-soft_reduce_kernel(const double *__restrict__ partial, const int32_t *__restrict__ queue, int first, int count,
-                   float scale, float *__restrict__ out) {
-    __shared__ double red[256];
+soft_reduce_kernel(const double *__restrict__ partial, const int32_t *__restrict__ queue, int first, int first2,
+                   double *__restrict__ red) {
+    __shared__ double sh[COUNT][256];
     const int64_t n = queue[2];
-    for (int q = 0; q < count; ++q) {
-        double v = 0.0;
-        for (int64_t k = threadIdx.x; k < n; k += 256) v += partial[k * kSoftSlots + first + q];
-        red[threadIdx.x] = v;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t k0 = (int64_t)blockIdx.x * per, k1 = k0 + per < n ? k0 + per : n;
+    double v[COUNT];
+#pragma unroll
+    for (int q = 0; q < COUNT; ++q) v[q] = 0.0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+        const double *sl = partial + k * kSoftSlots;
+#pragma unroll
+        for (int q = 0; q < COUNT; ++q) v[q] += TWO ? sl[first + q] + sl[first2 + q] : sl[first + q];
+    }
+#pragma unroll
+    for (int q = 0; q < COUNT; ++q) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off)
+#pragma unroll
+            for (int q = 0; q < COUNT; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + off];
         __syncthreads();
-        for (int off = 128; off > 0; off >>= 1) {
-            if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[q] = (float)(red[0] * (double)scale);
-        __syncthreads();
+    }
+    if ((int)threadIdx.x < COUNT) red[(int64_t)blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void soft_reduce_final_kernel(const double *__restrict__ red, int count, float scale, float *__restrict__ out) {
+    if ((int)threadIdx.x < count) {
+        double t = 0.0;
+        for (int b = 0; b < kSoftRedBlocks; ++b) t += red[b * 8 + threadIdx.x];
+        out[threadIdx.x] = (float)(t * (double)scale);
     }
 }
 
@@ -938,9 +944,11 @@ cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, cons
         if (e != cudaSuccess) return e;
         soft_forward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftWarps, sizeof(SoftSmemFwd) * kSoftWarps, st>>>(
             src, tgt, geom, order, P, A, counts, gold, W);
-        soft_loss_kernel<false><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
+        soft_value_kernel<<<(unsigned)std::min<int64_t>((n_pairs + 7) / 8, (int64_t)n_sms * 8), 256, 0, st>>>(
+            geom, order, n_pairs, P, W);
     }
-    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, W.queue, 0, 1, A.inv_cells, loss);
+    soft_reduce_kernel<1, false><<<kSoftRedBlocks, 256, 0, st>>>(W.partial, W.queue, 0, 0, W.red);
+    soft_reduce_final_kernel<<<1, 32, 0, st>>>(W.red, 1, A.inv_cells, loss);
     if (value && n_pairs > 0)
         copy_values_kernel<<<(unsigned)((n_pairs + 255) / 256), 256, 0, st>>>(W.vpart, order, n_pairs, value);
     return cudaGetLastError();
@@ -958,13 +966,13 @@ cudaError_t launch_soft_backward(const DevCorpus &src, const DevCorpus &tgt, con
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, soft_backward_kernel, 32 * kSoftBwdWarps,
                                                           sizeof(SoftSmemBwd) * kSoftBwdWarps);
         if (e != cudaSuccess) return e;
-        soft_loss_kernel<true><<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W);
+        SoftArgs Ah = A;
+        Ah.hvp = hvp;
         soft_backward_kernel<<<n_sms * (per_sm > 0 ? per_sm : 1), 32 * kSoftBwdWarps, sizeof(SoftSmemBwd) * kSoftBwdWarps,
-                               st>>>(
-            src, tgt, geom, order, P, A, counts, gold, W);
-        soft_chain_kernel<<<n_sms * 8, 256, 0, st>>>(src, tgt, geom, order, P, A, counts, gold, W, hvp);
+                               st>>>(src, tgt, geom, order, P, Ah, counts, gold, W);
     }
-    soft_reduce_kernel<<<1, 256, 0, st>>>(W.partial, W.queue, 1, 7, dloss, grad);
+    soft_reduce_kernel<7, true><<<kSoftRedBlocks, 256, 0, st>>>(W.partial, W.queue, 1, 8, W.red);
+    soft_reduce_final_kernel<<<1, 32, 0, st>>>(W.red, 7, dloss, grad);
     return cudaGetLastError();
 }
 
