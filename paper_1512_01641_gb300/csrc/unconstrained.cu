@@ -366,6 +366,165 @@ unconstrained_smem_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restri
     }
 }
 
+// The same DP for long targets with one block of kUcCtaThreads threads per
+// pair: columns 0..M in one contiguous segment per thread, the segment
+// aggregates combined by block scans (a warp scan, then the warps' totals in
+// shared memory), two block barriers per row.  Same candidates, same
+// arithmetic, same tie rules.  Shared memory: mcap columns of A, Q (int64),
+// colc (float2), Qa (int32), Sm (float), then the scans' warp totals.
+constexpr int kUcCtaThreads = 128;
+constexpr int kUcCtaWarps = kUcCtaThreads / 32;
+
+__global__ void __launch_bounds__(kUcCtaThreads, 4)
+unconstrained_cta_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
+                         const int32_t *__restrict__ order, int64_t n_pairs, DevParams P,
+                         const uint8_t *__restrict__ counts, UcScratch W, float *pair_score, int mcap) {
+    extern __shared__ __align__(16) unsigned char uc_smem[];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    Fx *A = reinterpret_cast<Fx *>(uc_smem);
+    Fx *Qv = A + mcap;
+    float2 *colc = reinterpret_cast<float2 *>(Qv + mcap);
+    int32_t *Qa = reinterpret_cast<int32_t *>(colc + mcap);
+    float *Sm = reinterpret_cast<float *>(Qa + mcap);
+    MaxArg *tot_r = reinterpret_cast<MaxArg *>(Sm + mcap);  // at 32 mcap bytes: 8-byte aligned
+    MaxArg *tot_l = tot_r + kUcCtaWarps;
+    const Fx NEG = kNegFx;
+    const SimConst K = sim_const(P);
+    const float kb = __fmul_rn(-kLog2e, P.w[1]);
+    for (int64_t x = blockIdx.x; x < n_pairs; x += gridDim.x) {
+        const int32_t k = order[x];
+        const PairGeom g = geom[k];
+        const int N = g.n, M = g.m;
+        const FxGrid G = fx_grid(N, M, P.gap);
+        const Fx p = to_fx(P.gap, G);
+        int32_t *prev = W.prev + W.prev_off[k];
+        const int64_t sdoc = src.doc[k], tdoc = tgt.doc[k];
+        const int L = (M + 1 + kUcCtaThreads - 1) / kUcCtaThreads;
+        const int lo = min(t * L, M + 1), hi = min(lo + L, M + 1);
+        __syncthreads();  // the previous pair is done with the rows
+        for (int c = t; c <= M; c += kUcCtaThreads) {
+            A[c] = c == 0 ? 0 : NEG;
+            if (c >= 1) {
+                const int lt = (int)(tgt.sent[tdoc + c] - tgt.sent[tdoc + c - 1]);
+                colc[c] = make_float2(__frcp_rn((float)lt), (float)lt);
+            }
+        }
+        __syncthreads();
+        for (int i = 1; i <= N; ++i) {
+            const SimRow row = sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P);
+            const uchar2 *crow = reinterpret_cast<const uchar2 *>(counts) + g.cell_off + (int64_t)(i - 1) * M;
+            int32_t *prow = prev + (int64_t)(i - 1) * (M + 1);
+            for (int cb = 1 + t; cb <= M; cb += 4 * kUcCtaThreads) {
+                uchar2 q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    q[u] = cb + kUcCtaThreads * u <= M ? crow[cb + kUcCtaThreads * u - 1] : make_uchar2(0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c2 = cb + kUcCtaThreads * u;
+                    if (c2 <= M) {
+                        const float2 cc = colc[c2];
+                        const SimCol col{__fmul_rn(kb, cc.x), cc.y, cc.x, 0.0f};
+                        Sm[c2] = similarity(q[u].x, q[u].y, row, col, K);
+                    }
+                }
+            }
+            MaxArg run{NEG, 0x7fffffff};
+            for (int c = hi - 1; c >= lo; --c) {
+                const Fx v = A[c];
+                if (v >= run.v) run = {v, c};
+                Qv[c] = run.v;
+                Qa[c] = run.a;
+            }
+            MaxArg agg{NEG, -1};
+            for (int c = lo; c < hi; ++c) {
+                const Fx v = A[c] + p * (Fx)c;
+                if (v >= agg.v) agg = {v, c};
+            }
+            // block scans: over the threads after t (smaller index at ties)
+            // and before t (larger index at ties)
+            const MaxArg ir = warp_max_scan<false, false>(run, lane);
+            const MaxArg il = warp_max_scan<true, true>(agg, lane);
+            if (lane == 0) tot_r[warp] = ir;
+            if (lane == 31) tot_l[warp] = il;
+            MaxArg right{__shfl_down_sync(kFull, ir.v, 1), __shfl_down_sync(kFull, ir.a, 1)};
+            if (lane == 31) right = {NEG, 0x7fffffff};
+            MaxArg pre{__shfl_up_sync(kFull, il.v, 1), __shfl_up_sync(kFull, il.a, 1)};
+            if (lane == 0) pre = {NEG, -1};
+            __syncthreads();  // warp totals, and the row's similarities, are visible
+            for (int w = warp + 1; w < kUcCtaWarps; ++w)
+                if (better(tot_r[w].v, tot_r[w].a, right, false)) right = tot_r[w];
+            for (int w = 0; w < warp; ++w)
+                if (better(tot_l[w].v, tot_l[w].a, pre, true)) pre = tot_l[w];
+            for (int c2 = lo; c2 < hi; ++c2) {
+                const Fx a_here = A[c2];
+                if (c2 >= 1) {
+                    const Fx sim = to_fx(Sm[c2], G);
+                    Fx best = a_here - p;
+                    int arg = -1;
+                    const Fx fw = sim + pre.v - p * (Fx)(c2 - 1);
+                    if (fw > best) {
+                        best = fw;
+                        arg = pre.a;
+                    }
+                    const MaxArg q = right.v > Qv[c2] ? right : MaxArg{Qv[c2], Qa[c2]};
+                    const Fx bk = sim - p + q.v;
+                    if (bk > best) {
+                        best = bk;
+                        arg = q.a;
+                    }
+                    A[c2] = best;
+                    prow[c2] = arg;
+                } else {
+                    A[0] = a_here - p;
+                    prow[0] = -1;
+                }
+                const Fx v = a_here + p * (Fx)c2;
+                if (v >= pre.v) pre = {v, c2};
+            }
+            __syncthreads();  // the row is complete before the next one reads it
+        }
+        // final pointer: max of A(N, c) - p (M - c), smallest c at ties
+        MaxArg best{NEG, 0x7fffffff};
+        for (int c = t; c <= M; c += kUcCtaThreads) {
+            const Fx v = A[c] - p * (Fx)(M - c);
+            if (better(v, c, best, false)) best = {v, c};
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const Fx v = __shfl_xor_sync(kFull, best.v, off);
+            const int a = __shfl_xor_sync(kFull, best.a, off);
+            if (better(v, a, best, false)) best = {v, a};
+        }
+        if (lane == 0) tot_r[warp] = best;
+        __syncthreads();
+        if (t == 0) {
+            for (int w = 1; w < kUcCtaWarps; ++w)
+                if (better(tot_r[w].v, tot_r[w].a, best, false)) best = tot_r[w];
+            int c = best.a;
+            int n = 0;
+            int32_t *li = W.li + W.link_off[k], *lj = W.lj + W.link_off[k];
+            float *ls = W.ls + W.link_off[k];
+            for (int i = N; i >= 1; --i) {
+                const int a = prev[(int64_t)(i - 1) * (M + 1) + c];
+                if (a != -1) {
+                    const int slot = N - 1 - n;
+                    const int lt = (int)(tgt.sent[tdoc + c] - tgt.sent[tdoc + c - 1]);
+                    const uchar2 cq = reinterpret_cast<const uchar2 *>(counts)[g.cell_off + (int64_t)(i - 1) * M + c - 1];
+                    li[slot] = i - 1;
+                    lj[slot] = c - 1;
+                    ls[slot] = similarity(cq.x, cq.y, sim_row((int)(src.sent[sdoc + i] - src.sent[sdoc + i - 1]), P),
+                                          sim_col(lt, P), K);
+                    ++n;
+                    c = a;
+                }
+            }
+            W.n_match[k] = n;
+            pair_score[k] = from_fx(best.v, G);
+        }
+    }
+}
+
 // Links of every pair with s >= thr, in row order, compacted at out_off.
 __global__ void __launch_bounds__(32 * kUcWarps)
 uc_count_kernel(const PairGeom *__restrict__ geom, int64_t n_pairs, float thr, UcScratch W, int32_t *kept) {
@@ -450,15 +609,40 @@ cudaError_t launch_uc_rows(const DevCorpus &src, const DevCorpus &tgt, const Pai
 
 }  // namespace
 
+// The pairs order[0, n) with one block of kUcCtaThreads per pair, rows of
+// mcap columns in shared memory, or on the global-row kernel when they do not
+// fit.
+static cudaError_t launch_uc_cta(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
+                          int64_t n, const DevParams &P, const uint8_t *counts, const UcScratch &W, float *pair_score,
+                          int mcap, int n_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t bytes = 32 * (int64_t)mcap + 2 * kUcCtaWarps * (int64_t)sizeof(MaxArg);
+    if (bytes > (200 << 10))
+        return launch_uc_rows(src, tgt, geom, order, n, P, counts, W, pair_score, mcap, kUcWarps, n_sms, st);
+    cudaError_t e = cudaFuncSetAttribute(unconstrained_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unconstrained_cta_kernel, kUcCtaThreads, (size_t)bytes);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = n;
+    const int64_t cap = (int64_t)n_sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > cap) blocks = cap;
+    unconstrained_cta_kernel<<<(unsigned)blocks, kUcCtaThreads, (size_t)bytes, st>>>(src, tgt, geom, order, n, P,
+                                                                                    counts, W, pair_score, mcap);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unconstrained(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom, const int32_t *order,
                                  int64_t n_short, int64_t n_pairs, const DevParams &P, const uint8_t *counts,
                                  const UcScratch &W, float *pair_score, int max_m, int32_t *kept, int n_sms,
                                  cudaStream_t st) {
     if (n_pairs == 0) return cudaSuccess;
-    // long targets first (few pairs, rows sized by the longest), then the
-    // short ones, eight warps per block on 8 KB of rows each
-    cudaError_t e = launch_uc_rows(src, tgt, geom, order + n_short, n_pairs - n_short, P, counts, W, pair_score,
-                                   max_m + 1, kUcWarps, n_sms, st);
+    // long targets first (few pairs: a block of threads each, rows sized by
+    // the longest), then the short ones, eight warps per block on 8 KB of
+    // rows each
+    cudaError_t e = launch_uc_cta(src, tgt, geom, order + n_short, n_pairs - n_short, P, counts, W, pair_score,
+                                  max_m + 1, n_sms, st);
     if (e != cudaSuccess) return e;
     e = launch_uc_rows(src, tgt, geom, order, n_short, P, counts, W, pair_score, kUcShortCols, kUcShortWarps, n_sms, st);
     if (e != cudaSuccess) return e;

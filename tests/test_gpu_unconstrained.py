@@ -86,3 +86,27 @@ def test_unconstrained_rejects_short_outputs():
              "pair_score": torch.empty(3, dtype=torch.float32, device="cuda")}
     with pytest.raises(miner.MinerError):
         plan.align_unconstrained(miner.MineParams(), counts, out=short)
+
+
+def test_unconstrained_long_targets_vs_oracle():
+    """Targets of 256 sentences and more take the block-per-pair kernel
+    (segments of a few columns per thread, block scans): same scores and
+    links as the oracle, ties validated as above."""
+    from paper_1512_01641_gb300 import miner
+    ns = [20, 33, 5, 2]
+    ms = [300, 257, 400, 256]
+    dic = synth.make_dictionary(np.random.Generator(np.random.PCG64(704)), 800, 800)
+    batch = synth.make_batch(705, len(ns), dic=dic, planted_frac=0.0, src_sizes=ns, tgt_sizes=ms)
+    p = miner.MineParams(thr=-1.0)
+    g = _gpu(batch, p)
+    ref = oracle.mine(batch, p.w, p.b, p.gap, p.thr, want_sim=True)
+    for k in range(batch.n_pairs):
+        s = ref["sim"][k]
+        score, links = unconstrained.align(s, p.gap)
+        assert abs(g["score"][k] - score) <= H_REL * max(1.0, abs(score)), (k, g["score"][k], score)
+        path = [(i, j) for i, j, _ in g["links"][k]]
+        if path != links:
+            choice = [None] * s.shape[0]
+            for i, j in path:
+                choice[i] = j
+            assert unconstrained.path_score(s, p.gap, choice) >= score - TIE_TOL, (k, path, links)
