@@ -487,9 +487,16 @@ int mine_plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_
     return mine_plan_create_with_options(src, tgt, dict, nullptr, nullptr, 0, out, stream);
 }
 
-int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
-                                  const int32_t *options, const int64_t *values, int n_options,
-                                  mine_plan **out, miner_stream_t stream) {
+}  // extern "C"
+
+// Plan creation.  host_sd / host_td (may be null): host copies of the
+// document offsets, which spare the read-back of the device ones (and its
+// wait for everything queued before it on the stream); inputs_ready (may be
+// null): an event after which the token and dictionary arrays are in place,
+// waited for before the first kernel reads them.
+static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict, const int32_t *options,
+                       const int64_t *values, int n_options, mine_plan **out, miner_stream_t stream,
+                       const int64_t *host_sd, const int64_t *host_td, cudaEvent_t inputs_ready) {
     if (!src || !tgt || !dict || !out) return MINE_EINVAL;
     *out = nullptr;
     if (n_options < 0 || (n_options > 0 && (!options || !values))) return MINE_EINVAL;
@@ -537,17 +544,23 @@ int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt
     const int64_t n = src->n_docs;
     p->n_pairs = n;
 
-    // document sizes (synchronous read-back)
+    // document sizes (the caller's host copies, or a synchronous read-back)
     std::vector<int64_t> sd(n + 1), td(n + 1);
-    PLAN_CK(cudaMemcpyAsync(sd.data(), src->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PLAN_CK(cudaMemcpyAsync(td.data(), tgt->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PLAN_CK(cudaStreamSynchronize(st));
+    if (host_sd && host_td) {
+        std::copy(host_sd, host_sd + n + 1, sd.begin());
+        std::copy(host_td, host_td + n + 1, td.begin());
+    } else {
+        PLAN_CK(cudaMemcpyAsync(sd.data(), src->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PLAN_CK(cudaMemcpyAsync(td.data(), tgt->doc_sent_off, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PLAN_CK(cudaStreamSynchronize(st));
+    }
     if (sd[0] != 0 || td[0] != 0 || sd[n] != src->n_sents || td[n] != tgt->n_sents) return fail(MINE_EINVAL);
     for (int64_t k = 0; k < n; ++k)
         if (sd[k + 1] < sd[k] || td[k + 1] < td[k] || sd[k + 1] - sd[k] > (1 << 21) || td[k + 1] - td[k] > (1 << 21))
             return fail(MINE_EINVAL);
 
     // validation kernels
+    if (inputs_ready) PLAN_CK(cudaStreamWaitEvent(st, inputs_ready, 0));
     PLAN_CK(dalloc(&p->S.status, 4, p->device, st));
     PLAN_CK(dalloc(&p->stats, 4, p->device, st));
     PLAN_CK(cudaMemsetAsync(p->S.status, 0, 4 * sizeof(uint32_t), st));
@@ -636,6 +649,14 @@ int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt
     *out = p;
 #undef PLAN_CK
     return MINE_OK;
+}
+
+extern "C" {
+
+int mine_plan_create_with_options(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
+                                  const int32_t *options, const int64_t *values, int n_options,
+                                  mine_plan **out, miner_stream_t stream) {
+    return plan_create(src, tgt, dict, options, values, n_options, out, stream, nullptr, nullptr, nullptr);
 }
 
 void mine_plan_destroy(mine_plan *plan) { plan_free(plan); }
@@ -1298,8 +1319,32 @@ extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, c
     MINE_CK(dalloc(&ttok.p, (size_t)std::max<int64_t>(tgt->n_tok, 1), device, st));
     MINE_CK(dalloc(&doff.p, (size_t)dict->v_src + 1, device, st));
     MINE_CK(dalloc(&dtgt.p, (size_t)std::max<int64_t>(dict->n_entries, 1), device, st));
+    // the uploads run on a copy stream while the plan is built on the host
+    // from the caller's document offsets; the plan's first kernel waits for
+    // them, and the stream's later frees of these buffers follow that wait
+    // (several copy streams move the tokens no faster: the host link is the
+    // limit)
+    struct CopyStream {
+        cudaStream_t main, cs = nullptr;
+        cudaEvent_t ready = nullptr, ordered = nullptr;
+        bool recorded = false;  // ready marks the end of the copies
+        ~CopyStream() {         // runs before the buffers' stream-ordered frees on main
+            if (recorded)
+                (void)cudaStreamWaitEvent(main, ready, 0);
+            else if (cs)
+                (void)cudaStreamSynchronize(cs);  // an early exit: let enqueued copies finish
+            if (ready) cudaEventDestroy(ready);
+            if (ordered) cudaEventDestroy(ordered);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } C{st};
+    MINE_CK(cudaStreamCreateWithFlags(&C.cs, cudaStreamNonBlocking));
+    MINE_CK(cudaEventCreateWithFlags(&C.ready, cudaEventDisableTiming));
+    MINE_CK(cudaEventCreateWithFlags(&C.ordered, cudaEventDisableTiming));
+    MINE_CK(cudaEventRecord(C.ordered, st));  // the allocations above
+    MINE_CK(cudaStreamWaitEvent(C.cs, C.ordered, 0));
     auto up = [&](void *d, const void *h, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+        return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, C.cs) : cudaSuccess;
     };
     MINE_CK(up(sdoc.p, src->doc_sent_off, (n + 1) * 8));
     MINE_CK(up(tdoc.p, tgt->doc_sent_off, (n + 1) * 8));
@@ -1309,6 +1354,8 @@ extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, c
     MINE_CK(up(ttok.p, tgt->tok, tgt->n_tok * 4));
     MINE_CK(up(doff.p, dict->off, ((size_t)dict->v_src + 1) * 4));
     MINE_CK(up(dtgt.p, dict->tgt, dict->n_entries * 4));
+    MINE_CK(cudaEventRecord(C.ready, C.cs));
+    C.recorded = true;  // from here on every exit orders main after the copies
     const mine_corpus ds{src->n_docs, src->n_sents, src->n_tok, sdoc.p, ssent.p, stok.p};
     const mine_corpus dt{tgt->n_docs, tgt->n_sents, tgt->n_tok, tdoc.p, tsent.p, ttok.p};
     const mine_dict dd{dict->v_src, dict->v_tgt, dict->n_entries, doff.p, dtgt.p};
@@ -1319,7 +1366,8 @@ extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, c
     opt.insert(opt.end(), options, options + n_options);
     val.insert(val.end(), values, values + n_options);
     mine_plan *p = nullptr;
-    int r = mine_plan_create_with_options(&ds, &dt, &dd, opt.data(), val.data(), (int)opt.size(), &p, stream);
+    int r = plan_create(&ds, &dt, &dd, opt.data(), val.data(), (int)opt.size(), &p, stream, src->doc_sent_off,
+                        tgt->doc_sent_off, C.ready);
     if (r != MINE_OK) return r;
     struct PlanGuard {
         mine_plan *p;
