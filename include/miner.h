@@ -162,9 +162,13 @@ int mine_pairs(mine_plan *plan, const mine_params *params, mine_out *out,
  * graph is off unless an option turns it on), runs mine_pairs, and writes the
  * results to the host arrays: link_off (n_docs+1), the links (link_capacity
  * entries, at least the sum over pairs of min(N_k, M_k)) and pair_score
- * (n_docs).  SYNCHRONOUS: returns when the results are in host memory and
- * everything the call allocated is back in the pool.  Error codes as
- * mine_plan_create and mine_pairs, MINE_ETIMEOUT as mine_plan_check. */
+ * (n_docs).  The upload overlaps the planning (from the host document
+ * offsets); with MINE_OPT_HOST_CHUNKS the batch is mined in chunks of pairs,
+ * the upload and plan of the next chunk overlapping the mining of the current
+ * one; the results do not depend on the chunking.
+ * SYNCHRONOUS: returns when the results are in host memory and everything the
+ * call allocated is back in the pool.  Error codes as mine_plan_create and
+ * mine_pairs, MINE_ETIMEOUT as mine_plan_check. */
 int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict, const mine_params *params,
                     const int32_t *options, const int64_t *values, int n_options, int64_t *link_off,
                     int32_t *link_i, int32_t *link_j, float *link_s, float *pair_score, int64_t link_capacity,
@@ -291,6 +295,13 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
                                        list's order) is never published, so the strips that wait
                                        on it give up after MINE_OPT_WAIT_LIMIT polls and
                                        mine_plan_check reports MINE_ETIMEOUT (-1: off) */
+#define MINE_OPT_HOST_CHUNKS 12   /* mine_pairs_host only (not a plan option): the batch is
+                                     mined as this many contiguous chunks of pairs of about
+                                     equal cells, the upload and the plan of the next chunk
+                                     overlapping the mining of the current one (0, the
+                                     default: one chunk, whose upload overlaps its planning;
+                                     on a batch whose longest pairs end up in one chunk, more
+                                     chunks lose the overlap of long and short pairs) */
 int mine_plan_set_option(mine_plan *plan, int option, int64_t value);
 /* Current value of an option, or MINE_EINVAL for an unknown option. */
 int64_t mine_plan_get_option(const mine_plan *plan, int option);

@@ -3,6 +3,7 @@
 #include <mutex>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -1293,6 +1294,34 @@ int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint
 }  // extern "C"
 
 // ------------------------------------------------------- host-buffer mining
+namespace gbm {
+// In place: x[i] -= base (a chunk's sentence offsets, rebased to its first token).
+__global__ void rebase_offsets_kernel(int64_t *x, int64_t count, int64_t base) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) x[i] -= base;
+}
+}  // namespace gbm
+
+namespace {
+
+// One chunk of pairs [k0, k1) of mine_pairs_host: its device inputs (sentence
+// offsets rebased to the chunk's first token, tokens in buffers of their own,
+// so that every token array starts 16-byte aligned), its plan and outputs.
+struct HostChunk {
+    int64_t k0 = 0, k1 = 0, s0 = 0, s1 = 0, u0 = 0, u1 = 0;  // pairs, source sentences, target sentences
+    std::vector<int64_t> sdoc_h, tdoc_h;                       // rebased document offsets (host)
+    PoolTemp<int64_t> sdoc, ssent, tdoc, tsent, o_off;
+    PoolTemp<int32_t> stok, ttok, o_i, o_j;
+    PoolTemp<float> o_s, o_score;
+    mine_plan *plan = nullptr;
+    explicit HostChunk(cudaStream_t st)
+        : sdoc(st), ssent(st), tdoc(st), tsent(st), o_off(st), stok(st), ttok(st), o_i(st), o_j(st), o_s(st),
+          o_score(st) {}
+    ~HostChunk() { mine_plan_destroy(plan); }
+};
+
+}  // namespace
+
 extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, const mine_dict *dict,
                                const mine_params *params, const int32_t *options, const int64_t *values,
                                int n_options, int64_t *link_off, int32_t *link_i, int32_t *link_j, float *link_s,
@@ -1304,99 +1333,204 @@ extern "C" int mine_pairs_host(const mine_corpus *src, const mine_corpus *tgt, c
     if (!src->doc_sent_off || !src->sent_tok_off || !tgt->doc_sent_off || !tgt->sent_tok_off || !dict->off ||
         (src->n_tok > 0 && !src->tok) || (tgt->n_tok > 0 && !tgt->tok) || (dict->n_entries > 0 && !dict->tgt))
         return MINE_EINVAL;
+    if (n_options < 0 || (n_options > 0 && (!options || !values))) return MINE_EINVAL;
+    // a plan used once: no graph capture unless the caller's options ask for
+    // it; MINE_OPT_HOST_CHUNKS is this call's own
+    std::vector<int32_t> opt(1, MINE_OPT_USE_GRAPH);
+    std::vector<int64_t> val(1, 0);
+    int64_t want_chunks = 0;
+    for (int x = 0; x < n_options; ++x) {
+        if (options[x] == MINE_OPT_HOST_CHUNKS) {
+            if (values[x] < 0) return MINE_EINVAL;
+            want_chunks = values[x];
+        } else {
+            opt.push_back(options[x]);
+            val.push_back(values[x]);
+        }
+    }
+    const int64_t n = src->n_docs;
+    const int64_t *sd = src->doc_sent_off, *td = tgt->doc_sent_off;  // host
+    const int64_t *ss = src->sent_tok_off, *ts = tgt->sent_tok_off;  // host
+    // the offsets that delimit the chunks (the plans check the rest)
+    if (sd[0] != 0 || td[0] != 0 || sd[n] != src->n_sents || td[n] != tgt->n_sents) return MINE_EINVAL;
+    int64_t cells = 0, need = 0;  // cells, and link capacity: the sum over pairs of min(N, M)
+    for (int64_t k = 0; k < n; ++k) {
+        if (sd[k + 1] < sd[k] || td[k + 1] < td[k]) return MINE_EINVAL;
+        cells += (sd[k + 1] - sd[k]) * (td[k + 1] - td[k]);
+        need += std::min(sd[k + 1] - sd[k], td[k + 1] - td[k]);
+    }
+    if (link_capacity < need || (need > 0 && (!link_i || !link_j || !link_s))) return MINE_EINVAL;
+    if (ss[0] != 0 || ts[0] != 0 || ss[src->n_sents] != src->n_tok || ts[tgt->n_sents] != tgt->n_tok)
+        return MINE_EINVAL;
+    int64_t K = want_chunks > 0 ? want_chunks : 1;
+    K = std::max<int64_t>(1, std::min<int64_t>(K, std::max<int64_t>(n, 1)));
     cudaStream_t st = (cudaStream_t)stream;
     int device;
     MINE_CK(cudaGetDevice(&device));
-    // device copies of the inputs, from the library's pool (returned on every path)
-    PoolTemp<int64_t> sdoc(st), ssent(st), tdoc(st), tsent(st);
-    PoolTemp<int32_t> stok(st), ttok(st), doff(st), dtgt(st);
-    const int64_t n = src->n_docs;
-    MINE_CK(dalloc(&sdoc.p, (size_t)n + 1, device, st));
-    MINE_CK(dalloc(&tdoc.p, (size_t)n + 1, device, st));
-    MINE_CK(dalloc(&ssent.p, (size_t)src->n_sents + 1, device, st));
-    MINE_CK(dalloc(&tsent.p, (size_t)tgt->n_sents + 1, device, st));
-    MINE_CK(dalloc(&stok.p, (size_t)std::max<int64_t>(src->n_tok, 1), device, st));
-    MINE_CK(dalloc(&ttok.p, (size_t)std::max<int64_t>(tgt->n_tok, 1), device, st));
+
+    // streams: copies (cs), plan creation of the next chunk (ps), mining (st);
+    // every exit orders st after the copies and the plan work (the chunks'
+    // buffers are freed on st)
+    struct Streams {
+        cudaStream_t main, cs = nullptr, ps = nullptr;
+        cudaEvent_t ordered = nullptr, done_cs = nullptr, done_ps = nullptr;
+        ~Streams() {
+            for (cudaStream_t q : {cs, ps}) {
+                if (!q) continue;
+                cudaEvent_t ev = q == cs ? done_cs : done_ps;
+                if (ev && cudaEventRecord(ev, q) == cudaSuccess)
+                    (void)cudaStreamWaitEvent(main, ev, 0);
+                else
+                    (void)cudaStreamSynchronize(q);
+            }
+            for (cudaEvent_t ev : {ordered, done_cs, done_ps})
+                if (ev) cudaEventDestroy(ev);
+            if (cs) cudaStreamDestroy(cs);
+            if (ps) cudaStreamDestroy(ps);
+        }
+    };
+    // chunk bounds: about equal cells
+    std::vector<int64_t> bounds(1, 0);
+    {
+        int64_t acc = 0, next = 1;
+        for (int64_t k = 0; k < n && next < K; ++k) {
+            acc += (sd[k + 1] - sd[k]) * (td[k + 1] - td[k]);
+            if (acc * K >= next * cells && k + 1 < n) {
+                bounds.push_back(k + 1);
+                while (next < K && acc * K >= next * cells) ++next;
+            }
+        }
+        bounds.push_back(n);
+    }
+    const int nc = (int)bounds.size() - 1;
+    PoolTemp<int32_t> doff(st), dtgt(st);
+    std::vector<std::unique_ptr<HostChunk>> ch;
+    for (int c = 0; c < nc; ++c) {
+        ch.emplace_back(new HostChunk(st));
+        HostChunk &H = *ch.back();
+        H.k0 = bounds[c];
+        H.k1 = bounds[c + 1];
+        H.s0 = sd[H.k0];
+        H.s1 = sd[H.k1];
+        H.u0 = td[H.k0];
+        H.u1 = td[H.k1];
+        const int64_t nk = H.k1 - H.k0;
+        H.sdoc_h.resize(nk + 1);
+        H.tdoc_h.resize(nk + 1);
+        for (int64_t x = 0; x <= nk; ++x) {
+            H.sdoc_h[x] = sd[H.k0 + x] - H.s0;
+            H.tdoc_h[x] = td[H.k0 + x] - H.u0;
+        }
+        MINE_CK(dalloc(&H.sdoc.p, (size_t)nk + 1, device, st));
+        MINE_CK(dalloc(&H.tdoc.p, (size_t)nk + 1, device, st));
+        MINE_CK(dalloc(&H.ssent.p, (size_t)(H.s1 - H.s0) + 1, device, st));
+        MINE_CK(dalloc(&H.tsent.p, (size_t)(H.u1 - H.u0) + 1, device, st));
+        MINE_CK(dalloc(&H.stok.p, (size_t)std::max<int64_t>(ss[H.s1] - ss[H.s0], 1), device, st));
+        MINE_CK(dalloc(&H.ttok.p, (size_t)std::max<int64_t>(ts[H.u1] - ts[H.u0], 1), device, st));
+    }
     MINE_CK(dalloc(&doff.p, (size_t)dict->v_src + 1, device, st));
     MINE_CK(dalloc(&dtgt.p, (size_t)std::max<int64_t>(dict->n_entries, 1), device, st));
-    // the uploads run on a copy stream while the plan is built on the host
-    // from the caller's document offsets; the plan's first kernel waits for
-    // them, and the stream's later frees of these buffers follow that wait
-    // (several copy streams move the tokens no faster: the host link is the
-    // limit)
-    struct CopyStream {
-        cudaStream_t main, cs = nullptr;
-        cudaEvent_t ready = nullptr, ordered = nullptr;
-        bool recorded = false;  // ready marks the end of the copies
-        ~CopyStream() {         // runs before the buffers' stream-ordered frees on main
-            if (recorded)
-                (void)cudaStreamWaitEvent(main, ready, 0);
-            else if (cs)
-                (void)cudaStreamSynchronize(cs);  // an early exit: let enqueued copies finish
-            if (ready) cudaEventDestroy(ready);
-            if (ordered) cudaEventDestroy(ordered);
-            if (cs) cudaStreamDestroy(cs);
+    Streams S{st};
+    MINE_CK(cudaStreamCreateWithFlags(&S.cs, cudaStreamNonBlocking));
+    MINE_CK(cudaStreamCreateWithFlags(&S.ps, cudaStreamNonBlocking));
+    for (cudaEvent_t *ev : {&S.ordered, &S.done_cs, &S.done_ps})
+        MINE_CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    MINE_CK(cudaEventRecord(S.ordered, st));  // the allocations above
+    MINE_CK(cudaStreamWaitEvent(S.cs, S.ordered, 0));
+    std::vector<cudaEvent_t> ready(nc, nullptr);
+    struct Events {
+        std::vector<cudaEvent_t> &v;
+        ~Events() {
+            for (cudaEvent_t e : v)
+                if (e) cudaEventDestroy(e);
         }
-    } C{st};
-    MINE_CK(cudaStreamCreateWithFlags(&C.cs, cudaStreamNonBlocking));
-    MINE_CK(cudaEventCreateWithFlags(&C.ready, cudaEventDisableTiming));
-    MINE_CK(cudaEventCreateWithFlags(&C.ordered, cudaEventDisableTiming));
-    MINE_CK(cudaEventRecord(C.ordered, st));  // the allocations above
-    MINE_CK(cudaStreamWaitEvent(C.cs, C.ordered, 0));
+    } ev_guard{ready};
+    // every upload is enqueued at once, chunk by chunk (the dictionary first)
     auto up = [&](void *d, const void *h, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, C.cs) : cudaSuccess;
+        return bytes ? cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, S.cs) : cudaSuccess;
     };
-    MINE_CK(up(sdoc.p, src->doc_sent_off, (n + 1) * 8));
-    MINE_CK(up(tdoc.p, tgt->doc_sent_off, (n + 1) * 8));
-    MINE_CK(up(ssent.p, src->sent_tok_off, (src->n_sents + 1) * 8));
-    MINE_CK(up(tsent.p, tgt->sent_tok_off, (tgt->n_sents + 1) * 8));
-    MINE_CK(up(stok.p, src->tok, src->n_tok * 4));
-    MINE_CK(up(ttok.p, tgt->tok, tgt->n_tok * 4));
     MINE_CK(up(doff.p, dict->off, ((size_t)dict->v_src + 1) * 4));
     MINE_CK(up(dtgt.p, dict->tgt, dict->n_entries * 4));
-    MINE_CK(cudaEventRecord(C.ready, C.cs));
-    C.recorded = true;  // from here on every exit orders main after the copies
-    const mine_corpus ds{src->n_docs, src->n_sents, src->n_tok, sdoc.p, ssent.p, stok.p};
-    const mine_corpus dt{tgt->n_docs, tgt->n_sents, tgt->n_tok, tdoc.p, tsent.p, ttok.p};
-    const mine_dict dd{dict->v_src, dict->v_tgt, dict->n_entries, doff.p, dtgt.p};
-    // a plan used once: no graph capture unless the caller's options ask for it
-    if (n_options < 0 || (n_options > 0 && (!options || !values))) return MINE_EINVAL;
-    std::vector<int32_t> opt(1, MINE_OPT_USE_GRAPH);
-    std::vector<int64_t> val(1, 0);
-    opt.insert(opt.end(), options, options + n_options);
-    val.insert(val.end(), values, values + n_options);
-    mine_plan *p = nullptr;
-    int r = plan_create(&ds, &dt, &dd, opt.data(), val.data(), (int)opt.size(), &p, stream, src->doc_sent_off,
-                        tgt->doc_sent_off, C.ready);
-    if (r != MINE_OK) return r;
-    struct PlanGuard {
-        mine_plan *p;
-        ~PlanGuard() { mine_plan_destroy(p); }
-    } guard{p};
-    if (link_capacity < p->link_cap || (p->link_cap > 0 && (!link_i || !link_j || !link_s))) return MINE_EINVAL;
-    PoolTemp<int64_t> o_off(st);
-    PoolTemp<int32_t> o_i(st), o_j(st);
-    PoolTemp<float> o_s(st), o_score(st);
-    MINE_CK(dalloc(&o_off.p, (size_t)n + 1, device, st));
-    MINE_CK(dalloc(&o_i.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
-    MINE_CK(dalloc(&o_j.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
-    MINE_CK(dalloc(&o_s.p, (size_t)std::max<int64_t>(p->link_cap, 1), device, st));
-    MINE_CK(dalloc(&o_score.p, (size_t)std::max<int64_t>(n, 1), device, st));
-    mine_out out{o_off.p, o_i.p, o_j.p, o_s.p, o_score.p, std::max<int64_t>(p->link_cap, 1)};
-    r = mine_pairs(p, params, &out, stream);
-    if (r != MINE_OK) return r;
-    MINE_CK(cudaMemcpyAsync(link_off, o_off.p, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
-    if (n > 0) MINE_CK(cudaMemcpyAsync(pair_score, o_score.p, n * 4, cudaMemcpyDeviceToHost, st));
-    MINE_CK(cudaStreamSynchronize(st));
-    r = mine_plan_check(p, stream);
-    if (r != MINE_OK) return r;
-    const int64_t total = link_off[n];
-    if (total < 0 || total > link_capacity) return MINE_EINVAL;
-    if (total > 0) {
-        MINE_CK(cudaMemcpyAsync(link_i, o_i.p, total * 4, cudaMemcpyDeviceToHost, st));
-        MINE_CK(cudaMemcpyAsync(link_j, o_j.p, total * 4, cudaMemcpyDeviceToHost, st));
-        MINE_CK(cudaMemcpyAsync(link_s, o_s.p, total * 4, cudaMemcpyDeviceToHost, st));
+    for (int c = 0; c < nc; ++c) {
+        HostChunk &H = *ch[c];
+        const int64_t nk = H.k1 - H.k0;
+        MINE_CK(up(H.sdoc.p, H.sdoc_h.data(), (nk + 1) * 8));
+        MINE_CK(up(H.tdoc.p, H.tdoc_h.data(), (nk + 1) * 8));
+        MINE_CK(up(H.ssent.p, ss + H.s0, (H.s1 - H.s0 + 1) * 8));
+        MINE_CK(up(H.tsent.p, ts + H.u0, (H.u1 - H.u0 + 1) * 8));
+        MINE_CK(up(H.stok.p, src->tok + ss[H.s0], (ss[H.s1] - ss[H.s0]) * 4));
+        MINE_CK(up(H.ttok.p, tgt->tok + ts[H.u0], (ts[H.u1] - ts[H.u0]) * 4));
+        if (ss[H.s0] != 0)
+            gbm::rebase_offsets_kernel<<<64, 256, 0, S.cs>>>(H.ssent.p, H.s1 - H.s0 + 1, ss[H.s0]);
+        if (ts[H.u0] != 0)
+            gbm::rebase_offsets_kernel<<<64, 256, 0, S.cs>>>(H.tsent.p, H.u1 - H.u0 + 1, ts[H.u0]);
+        MINE_CK(cudaGetLastError());
+        MINE_CK(cudaEventCreateWithFlags(&ready[c], cudaEventDisableTiming));
+        MINE_CK(cudaEventRecord(ready[c], S.cs));
     }
-    MINE_CK(cudaStreamSynchronize(st));
+    const mine_dict dd{dict->v_src, dict->v_tgt, dict->n_entries, doff.p, dtgt.p};
+    auto make_plan = [&](int c) -> int {
+        HostChunk &H = *ch[c];
+        const int64_t nk = H.k1 - H.k0;
+        const mine_corpus ds{nk, H.s1 - H.s0, ss[H.s1] - ss[H.s0], H.sdoc.p, H.ssent.p, H.stok.p};
+        const mine_corpus dt{nk, H.u1 - H.u0, ts[H.u1] - ts[H.u0], H.tdoc.p, H.tsent.p, H.ttok.p};
+        int r = plan_create(&ds, &dt, &dd, opt.data(), val.data(), (int)opt.size(), &H.plan, (miner_stream_t)S.ps,
+                            H.sdoc_h.data(), H.tdoc_h.data(), ready[c]);
+        if (r != MINE_OK) return r;
+        const int64_t cap = std::max<int64_t>(H.plan->link_cap, 1);
+        MINE_CK(dalloc(&H.o_off.p, (size_t)nk + 1, device, S.ps));
+        MINE_CK(dalloc(&H.o_i.p, (size_t)cap, device, S.ps));
+        MINE_CK(dalloc(&H.o_j.p, (size_t)cap, device, S.ps));
+        MINE_CK(dalloc(&H.o_s.p, (size_t)cap, device, S.ps));
+        MINE_CK(dalloc(&H.o_score.p, (size_t)std::max<int64_t>(nk, 1), device, S.ps));
+        MINE_CK(cudaStreamSynchronize(S.ps));  // the plan and its outputs exist before st uses them
+        return MINE_OK;
+    };
+    std::vector<cudaEvent_t> mined(nc, nullptr);
+    Events mined_guard{mined};
+    auto mine = [&](int c) -> int {
+        HostChunk &H = *ch[c];
+        mine_out out{H.o_off.p, H.o_i.p, H.o_j.p, H.o_s.p, H.o_score.p, std::max<int64_t>(H.plan->link_cap, 1)};
+        int r = mine_pairs(H.plan, params, &out, stream);
+        if (r != MINE_OK) return r;
+        MINE_CK(cudaEventCreateWithFlags(&mined[c], cudaEventDisableTiming));
+        MINE_CK(cudaEventRecord(mined[c], st));
+        return MINE_OK;
+    };
+    int r = make_plan(0);
+    if (r == MINE_OK) r = mine(0);
+    if (r != MINE_OK) return r;
+    int64_t base = 0;
+    for (int c = 0; c < nc; ++c) {
+        // the next chunk's plan is built (its validation waits for its upload)
+        // and its mining queued behind this chunk's
+        if (c + 1 < nc) {
+            r = make_plan(c + 1);
+            if (r == MINE_OK) r = mine(c + 1);
+            if (r != MINE_OK) return r;
+        }
+        // this chunk's results, its links after those of the chunks before it
+        HostChunk &H = *ch[c];
+        const int64_t nk = H.k1 - H.k0;
+        int64_t total = 0;
+        MINE_CK(cudaStreamWaitEvent(S.ps, mined[c], 0));
+        if (nk > 0) {
+            MINE_CK(cudaMemcpyAsync(link_off + H.k0, H.o_off.p, nk * 8, cudaMemcpyDeviceToHost, S.ps));
+            MINE_CK(cudaMemcpyAsync(pair_score + H.k0, H.o_score.p, nk * 4, cudaMemcpyDeviceToHost, S.ps));
+        }
+        MINE_CK(cudaMemcpyAsync(&total, H.o_off.p + nk, 8, cudaMemcpyDeviceToHost, S.ps));
+        r = mine_plan_check(H.plan, (miner_stream_t)S.ps);  // synchronises ps
+        if (r != MINE_OK) return r;
+        if (total < 0 || total > link_capacity - base) return MINE_EINVAL;
+        if (total > 0) {
+            MINE_CK(cudaMemcpyAsync(link_i + base, H.o_i.p, total * 4, cudaMemcpyDeviceToHost, S.ps));
+            MINE_CK(cudaMemcpyAsync(link_j + base, H.o_j.p, total * 4, cudaMemcpyDeviceToHost, S.ps));
+            MINE_CK(cudaMemcpyAsync(link_s + base, H.o_s.p, total * 4, cudaMemcpyDeviceToHost, S.ps));
+        }
+        for (int64_t x = 0; x < nk; ++x) link_off[H.k0 + x] += base;
+        base += total;
+    }
+    link_off[n] = base;
+    MINE_CK(cudaStreamSynchronize(S.ps));
     return MINE_OK;
 }

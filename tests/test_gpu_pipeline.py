@@ -76,3 +76,30 @@ def test_host_buffer_entry_point_equals_plan_mine(pinned):
         short[k] = short[k][:cap - 1].clone()
     with pytest.raises(miner.MinerError):
         miner.mine_host(host, b.dic.v_src, b.dic.v_tgt, params, out=short)
+
+
+@pytest.mark.parametrize("chunks", [2, 3, 7])
+def test_host_entry_in_chunks_equals_plan_mine(chunks):
+    """mine_pairs_host mining the batch as 2, 3 or 7 chunks of pairs (each
+    with its own plan, the next chunk's upload and plan overlapping the
+    current chunk's mining) gives exactly the links and scores of one plan
+    over the batch; pairs of every size, empty documents included."""
+    import torch
+    from paper_1512_01641_gb300 import miner
+    sizes = np.array([0, 3, 40, 1, 70, 5, 0, 33, 12, 90, 7, 2, 64, 31, 20, 9, 1, 45, 3, 0, 28])
+    b = synth.make_batch(98, len(sizes), v_src=3000, v_tgt=3000, src_sizes=sizes)
+    params = miner.MineParams()
+    with miner.Plan(miner.DeviceBatch.from_batch(b)) as plan:
+        out = plan.mine(params)
+        n = int(out["link_off"][-1])
+        ref = {"link_off": out["link_off"].cpu(), "pair_score": out["pair_score"][:plan.n_pairs].cpu(),
+               "link_i": out["link_i"][:n].cpu(), "link_j": out["link_j"][:n].cpu(), "link_s": out["link_s"][:n].cpu()}
+    host = [b.src.doc_sent_off, b.src.sent_tok_off, b.src.tok, b.tgt.doc_sent_off, b.tgt.sent_tok_off, b.tgt.tok,
+            b.dic.off, b.dic.tgt]
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in host]
+    got = miner.mine_host(host, b.dic.v_src, b.dic.v_tgt, params, options={"host_chunks": chunks})
+    assert int(got["link_off"][-1]) == n
+    assert torch.equal(got["link_off"], ref["link_off"])
+    assert torch.equal(got["pair_score"][:b.n_pairs], ref["pair_score"])
+    for k in ("link_i", "link_j", "link_s"):
+        assert torch.equal(got[k][:n], ref[k]), k
