@@ -295,6 +295,9 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
                                        list's order) is never published, so the strips that wait
                                        on it give up after MINE_OPT_WAIT_LIMIT polls and
                                        mine_plan_check reports MINE_ETIMEOUT (-1: off) */
+#define MINE_OPT_SOFT_SPLIT_Q4 13  /* soft split mode 1: a pair is split when its serial chain
+                                      exceeds this many quarters of the mean chain per warp
+                                      (4: the mean); 1 .. 4096.  Same results at any value. */
 #define MINE_OPT_HOST_CHUNKS 12   /* mine_pairs_host only (not a plan option): the batch is
                                      mined as this many contiguous chunks of pairs of about
                                      equal cells, the upload and the plan of the next chunk

@@ -174,6 +174,7 @@ struct SoftArgs {
     int64_t wait_limit;  // bounded spins of a strip wait (split pairs)
     uint32_t *status;    // plan status word (timeout bit)
     int split;           // 0: one warp per pair, 1: split long pairs, 2: split every pair of >= 2 strips
+    int split_q4;        // split = 1: a pair splits when its chain exceeds split_q4 / 4 of the mean per warp
     int64_t skip_ctr;    // fault injection: this forward progress counter is never published (-1: off)
     float *hvp;          // backward: per cell H u (null: not wanted)
 };

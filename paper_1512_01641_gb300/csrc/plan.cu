@@ -147,6 +147,7 @@ struct PlanKnobs {
     int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
     int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
     int soft_split = 1;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs split over warps
+    int soft_split_q4 = 4;             // split = 1: above this many quarters of the mean chain per warp
     int64_t skip_soft = -1;            // fault injection: soft progress counter never published (tests)
 };
 
@@ -475,6 +476,10 @@ static int knob_apply(PlanKnobs &k, int option, int64_t value, int *effect) {
             return MINE_OK;
         case MINE_OPT_FAULT_SKIP_SOFT:
             k.skip_soft = value < 0 ? -1 : value;
+            return MINE_OK;
+        case MINE_OPT_SOFT_SPLIT_Q4:
+            if (value < 1 || value > 4096) return MINE_EINVAL;
+            k.soft_split_q4 = (int)value;
             return MINE_OK;
         default:
             return MINE_EINVAL;
@@ -894,6 +899,7 @@ static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, con
     A.wait_limit = p->knobs.wait_limit;
     A.status = p->S.status;
     A.split = p->knobs.soft_split;
+    A.split_q4 = p->knobs.soft_split_q4;
     A.skip_ctr = p->knobs.skip_soft;
     A.hvp = nullptr;
     int64_t cells = p->n_cells;
@@ -1029,6 +1035,7 @@ int64_t mine_plan_get_option(const mine_plan *p, int option) {
         case MINE_OPT_N_TILE_FLAGS: return p->n_flags;
         case MINE_OPT_SOFT_SPLIT: return p->knobs.soft_split;
         case MINE_OPT_FAULT_SKIP_SOFT: return p->knobs.skip_soft;
+        case MINE_OPT_SOFT_SPLIT_Q4: return p->knobs.soft_split_q4;
         default: return MINE_EINVAL;
     }
 }

@@ -753,15 +753,16 @@ __device__ int64_t block_scan(int64_t v, int64_t &total) {
 }
 
 // Work lists of one sweep (one block).  A listed pair of S >= 2 strips is
-// split when its serial chain S (M + 32) exceeds the mean chain per warp
-// (split = 1; every such pair with split = 2, none with split = 0).  Split
+// split when its serial chain S (M + 32) exceeds split_q4 / 4 of the mean
+// chain per warp (split = 1; every such pair with split = 2, none with
+// split = 0).  Split
 // pairs come first, each as S value-sweep items (top-down) followed by S
 // adjoint items (bottom-up), then the whole pairs in list order.  Every
 // listed pair with cells gets S slots of per-strip partial sums, in list
 // order.  Zeroes the progress counters and the work counter.
 __global__ void __launch_bounds__(1024)
 soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs,
-                  int64_t n_warps, int split, uint32_t *status, SoftScratch W) {
+                  int64_t n_warps, int split, int split_q4, uint32_t *status, SoftScratch W) {
     auto strips = [&](int64_t pos, int32_t &n, int32_t &m) {
         const PairGeom g = geom[order[pos]];
         n = g.n;
@@ -775,7 +776,8 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
         chain += S * (m + 32);
     }
     (void)block_scan(chain, tot);
-    const int64_t thr = split == 2 ? 0 : (split == 1 ? tot / (n_warps > 0 ? n_warps : 1) : INT64_MAX);
+    const int64_t thr =
+        split == 2 ? 0 : (split == 1 ? tot * split_q4 / (4 * (n_warps > 0 ? n_warps : 1)) : INT64_MAX);
     auto counts = [&](int64_t pos, int64_t &si, int64_t &sc, int64_t &wi, int64_t &sl) {
         int32_t n, m;
         const int64_t S = strips(pos, n, m);
@@ -927,7 +929,7 @@ static cudaError_t set_soft_smem(const void *kern, size_t bytes) {
 
 static void launch_soft_items(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const SoftArgs &A,
                               const SoftScratch &W, int n_sms, cudaStream_t st) {
-    soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.status, W);
+    soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.split_q4, A.status, W);
 }
 
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,

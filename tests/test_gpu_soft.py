@@ -212,6 +212,13 @@ def test_split_sweeps_are_bit_identical_to_one_warp_per_pair():
         for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
             assert np.array_equal(a, b), (split, name, np.abs(a - b).max())
     assert plan.get_option("soft_split") == 2
+    # mode 1 with other split thresholds (quarters of the mean chain per warp)
+    for q4 in (1, 64):
+        plan.set_option("soft_split_q4", q4)
+        got = _soft_all(plan, counts, gold, 0.1, 1)
+        for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
+            assert np.array_equal(a, b), (q4, name, np.abs(a - b).max())
+    assert plan.get_option("soft_split_q4") == 64
 
 
 def test_split_sweep_multi_strip_pair_vs_oracle():
