@@ -298,6 +298,13 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
 #define MINE_OPT_SOFT_SPLIT_Q4 13  /* soft split mode 1: a pair is split when its serial chain
                                       exceeds this many quarters of the mean chain per warp
                                       (4: the mean); 1 .. 4096.  Same results at any value. */
+#define MINE_OPT_SOFT_ORDER 14    /* soft work list with split pairs: 0 each split pair's
+                                     value-sweep strips then its adjoint strips, whole pairs
+                                     last; 1 (default) every value-sweep strip, the whole pairs,
+                                     every adjoint strip (the adjoint strips then seldom wait
+                                     for their value sweep); 2 value sweeps, adjoints, whole.
+                                     Every wait is on an item listed earlier in all three; same
+                                     results in every order. */
 #define MINE_OPT_HOST_CHUNKS 12   /* mine_pairs_host only (not a plan option): the batch is
                                      mined as this many contiguous chunks of pairs of about
                                      equal cells, the upload and the plan of the next chunk

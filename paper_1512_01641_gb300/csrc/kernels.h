@@ -175,6 +175,8 @@ struct SoftArgs {
     uint32_t *status;    // plan status word (timeout bit)
     int split;           // 0: one warp per pair, 1: split long pairs, 2: split every pair of >= 2 strips
     int split_q4;        // split = 1: a pair splits when its chain exceeds split_q4 / 4 of the mean per warp
+    int order;           // work list: 0 per split pair (its value sweep, then its adjoint), whole pairs last;
+                         // 1 every value sweep, the whole pairs, every adjoint; 2 value sweeps, adjoints, whole
     int64_t skip_ctr;    // fault injection: this forward progress counter is never published (-1: off)
     float *hvp;          // backward: per cell H u (null: not wanted)
 };

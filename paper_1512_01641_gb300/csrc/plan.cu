@@ -148,6 +148,7 @@ struct PlanKnobs {
     int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
     int soft_split = 1;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs split over warps
     int soft_split_q4 = 4;             // split = 1: above this many quarters of the mean chain per warp
+    int soft_order = 1;                // soft work list: 0 per pair, 1 value sweeps/whole/adjoints, 2 value/adjoints/whole
     int64_t skip_soft = -1;            // fault injection: soft progress counter never published (tests)
 };
 
@@ -480,6 +481,10 @@ static int knob_apply(PlanKnobs &k, int option, int64_t value, int *effect) {
         case MINE_OPT_SOFT_SPLIT_Q4:
             if (value < 1 || value > 4096) return MINE_EINVAL;
             k.soft_split_q4 = (int)value;
+            return MINE_OK;
+        case MINE_OPT_SOFT_ORDER:
+            if (value < 0 || value > 2) return MINE_EINVAL;
+            k.soft_order = (int)value;
             return MINE_OK;
         default:
             return MINE_EINVAL;
@@ -900,6 +905,7 @@ static bool soft_args(const mine_plan *p, const softnw_opts *o, SoftArgs &A, con
     A.status = p->S.status;
     A.split = p->knobs.soft_split;
     A.split_q4 = p->knobs.soft_split_q4;
+    A.order = p->knobs.soft_order;
     A.skip_ctr = p->knobs.skip_soft;
     A.hvp = nullptr;
     int64_t cells = p->n_cells;
@@ -1036,6 +1042,7 @@ int64_t mine_plan_get_option(const mine_plan *p, int option) {
         case MINE_OPT_SOFT_SPLIT: return p->knobs.soft_split;
         case MINE_OPT_FAULT_SKIP_SOFT: return p->knobs.skip_soft;
         case MINE_OPT_SOFT_SPLIT_Q4: return p->knobs.soft_split_q4;
+        case MINE_OPT_SOFT_ORDER: return p->knobs.soft_order;
         default: return MINE_EINVAL;
     }
 }

@@ -755,14 +755,17 @@ __device__ int64_t block_scan(int64_t v, int64_t &total) {
 // Work lists of one sweep (one block).  A listed pair of S >= 2 strips is
 // split when its serial chain S (M + 32) exceeds split_q4 / 4 of the mean
 // chain per warp (split = 1; every such pair with split = 2, none with
-// split = 0).  Split
-// pairs come first, each as S value-sweep items (top-down) followed by S
-// adjoint items (bottom-up), then the whole pairs in list order.  Every
+// split = 0).  List order 1: the value-sweep items of every split pair
+// (S per pair, top-down), the whole pairs, then the adjoint items of every
+// split pair (S per pair, bottom-up), so that an adjoint strip seldom waits
+// for its own value sweep; order 0: each split pair's value-sweep items then
+// its adjoint items, the whole pairs last; order 2: value sweeps, adjoints,
+// whole pairs.  Every wait is on an item listed earlier.  Every
 // listed pair with cells gets S slots of per-strip partial sums, in list
 // order.  Zeroes the progress counters and the work counter.
 __global__ void __launch_bounds__(1024)
 soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n_pairs,
-                  int64_t n_warps, int split, int split_q4, uint32_t *status, SoftScratch W) {
+                  int64_t n_warps, int split, int split_q4, int list_order, uint32_t *status, SoftScratch W) {
     auto strips = [&](int64_t pos, int32_t &n, int32_t &m) {
         const PairGeom g = geom[order[pos]];
         n = g.n;
@@ -824,16 +827,21 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
         c_wi += t2;
         c_sl += t3;
         if (pos >= n_pairs) continue;
+        // item positions of the list order (T[1] value-sweep items, as many
+        // adjoint items, T[2] whole pairs)
+        const int64_t b1 = list_order == 0 ? o_si : o_sc;  // first value-sweep item of the pair
+        const int64_t b2 = list_order == 0 ? o_si + sc : (list_order == 1 ? T[1] + T[2] + o_sc : T[1] + o_sc);
+        const int64_t b0 = list_order == 2 ? 2 * T[1] : T[1];  // first whole pair (T[0] = 2 T[1])
         if (si) {
             const int32_t S = (int32_t)sc;
             for (int32_t s = 0; s < S; ++s) {
-                W.items[o_si + s] = SoftItem{(int32_t)pos, s, 1, (int32_t)o_sc, (int32_t)o_sl};
-                W.items[o_si + 2 * S - 1 - s] = SoftItem{(int32_t)pos, s, 2, (int32_t)o_sc, (int32_t)o_sl};
+                W.items[b1 + s] = SoftItem{(int32_t)pos, s, 1, (int32_t)o_sc, (int32_t)o_sl};
+                W.items[b2 + S - 1 - s] = SoftItem{(int32_t)pos, s, 2, (int32_t)o_sc, (int32_t)o_sl};
                 W.prog1[o_sc + s] = 0;
                 W.prog2[o_sc + s] = 0;
             }
         } else {
-            W.items[T[0] + o_wi] = SoftItem{(int32_t)pos, 0, 0, 0, (int32_t)o_sl};
+            W.items[(list_order == 0 ? T[0] : b0) + o_wi] = SoftItem{(int32_t)pos, 0, 0, 0, (int32_t)o_sl};
         }
     }
     if (threadIdx.x == 0) {
@@ -929,7 +937,8 @@ static cudaError_t set_soft_smem(const void *kern, size_t bytes) {
 
 static void launch_soft_items(const PairGeom *geom, const int32_t *order, int64_t n_pairs, const SoftArgs &A,
                               const SoftScratch &W, int n_sms, cudaStream_t st) {
-    soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.split_q4, A.status, W);
+    soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.split_q4, A.order,
+                                          A.status, W);
 }
 
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,

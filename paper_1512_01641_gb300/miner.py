@@ -19,7 +19,7 @@ MINE_OK, MINE_EINVAL, MINE_ENOMEM, MINE_ECUDA, MINE_ETIMEOUT, MINE_ENOTSUP = 0, 
 OPTIONS = {"tile_cols": 1, "tile_min_cells": 2, "tile_min_rows": 3, "wait_limit": 4, "link_recount": 5,
            "use_graph": 6, "graph_captures": 7, "fault_skip_flag": 8, "n_tile_flags": 9,
            "soft_split": 10, "fault_skip_soft": 11, "host_chunks": 12,
-           "soft_split_q4": 13}
+           "soft_split_q4": 13, "soft_order": 14}
 
 
 class MinerError(RuntimeError):

@@ -219,6 +219,14 @@ def test_split_sweeps_are_bit_identical_to_one_warp_per_pair():
         for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
             assert np.array_equal(a, b), (q4, name, np.abs(a - b).max())
     assert plan.get_option("soft_split_q4") == 64
+    # the other work-list orders (value sweeps and adjoints per pair; adjoints before whole pairs)
+    plan.set_option("soft_split_q4", 4)
+    for order in (0, 2):
+        plan.set_option("soft_order", order)
+        for split in (1, 2):
+            got = _soft_all(plan, counts, gold, 0.1, split)
+            for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
+                assert np.array_equal(a, b), (order, split, name, np.abs(a - b).max())
 
 
 def test_split_sweep_multi_strip_pair_vs_oracle():
