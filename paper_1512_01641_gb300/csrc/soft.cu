@@ -52,7 +52,7 @@ namespace gbm {
 namespace {
 
 constexpr int kSoftWarps = 4;
-constexpr int kSoftBwdWarps = 2;  // 23 KB of shared memory per warp: four 2-warp CTAs per SM
+constexpr int kSoftBwdWarps = 2;  // 15 KB of shared memory per warp: six 2-warp CTAs per SM
 constexpr int kWin = 8;  // steps of a window of the adjoint sweep's recompute
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -75,7 +75,6 @@ struct SoftCtx {
     float *hvp;            // pair's H u output (backward, may be null)
     SimCol (*colb)[32];    // shared: column constants of the current and previous block [2][col]
     float (*svb)[32][32];  // shared: similarities of the current and previous block [2][row][col]
-    float (*ub)[32][32];   // shared: u of the current and previous block (TAN)
     float (*wb)[kWin][32]; // shared: the recomputed window's per-cell weights [component][step][lane]
     int64_t wait_limit;    // bounded spins of a strip wait
     uint32_t *status;      // timeout bit
@@ -132,9 +131,9 @@ __device__ __forceinline__ float cell_dldp(float E, float sv, int g, const SoftC
     return __fmul_rn(g ? -rcp_approx(Pr) : rcp_approx(__fsub_rn(1.0f, Pr)), C.inv_cells);
 }
 
-// Similarities (and, TAN, u = dL/dE from E and the gold links) of block jb
-// of the current strip into shared buffer jb & 1 with the block's column
-// constants; lane = row, columns written in rotated order.
+// Similarities of block jb of the current strip into shared buffer jb & 1
+// with the block's column constants; lane = row, columns written in rotated
+// order.
 template <bool TAN>
 __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv, int jb) {
     const int lane = C.lane;
@@ -144,26 +143,44 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv
     cv[lane] = sim_col(col0 + lane < C.M ? (int)(C.tsent[col0 + lane + 1] - C.tsent[col0 + lane]) : 1, C.P);
     __syncwarp();
     float(*sv)[32] = C.svb[jb & 1];
-    float(*ub)[32] = C.ub[jb & 1];
     const uchar2 *rowc = C.cnt + (int64_t)r * C.M;
 #pragma unroll 8
     for (int x = 0; x < 32; ++x) {
         const int c = (x + lane) & 31;
         const int col = col0 + c;
-        float v = 0.0f, u = 0.0f;
+        float v = 0.0f;
         if (rv && col < C.M) {
             const uchar2 q = rowc[col];
             v = similarity(q.x, q.y, C.row, cv[c], C.K);
-            if (TAN) {
-                const int64_t cell = (int64_t)r * C.M + col;
-                float G;
-                u = __fmul_rn(cell_dldp(C.E[cell], v, C.gold[cell], C, G, nullptr), G);
-            }
         }
         sv[lane][c] = v;
-        if (TAN) ub[lane][c] = u;
     }
     __syncwarp();
+}
+
+// The inputs of u = dL/dE for the lane's cells of the kWin forward steps
+// from t0 (column t0 + k - lane at step t0 + k): E and the gold links,
+// loaded a window ahead of their use so that their latency overlaps a
+// window of steps.
+struct UIn {
+    float e[kWin];
+    uint32_t g;  // bit k: gold link of step k's cell
+};
+__device__ __forceinline__ void soft_u_inputs(const SoftCtx &C, int s, int t0, UIn &X) {
+    const int lane = C.lane;
+    const int r = 32 * s + lane;
+    const bool rv = r < C.N;
+    X.g = 0u;
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) {
+        const int j = t0 + k - lane;
+        X.e[k] = 0.0f;
+        if (rv && j >= 0 && j < C.M) {
+            const int64_t c = (int64_t)r * C.M + j;
+            X.e[k] = C.E[c];
+            X.g |= (uint32_t)(C.gold[c] != 0) << k;
+        }
+    }
 }
 
 // One cell of the forward recurrence (lane's row, column j): the soft max
@@ -176,7 +193,7 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv
 template <bool TAN>
 __device__ __forceinline__ void soft_cell(const SoftCtx &C, int lane, int j, float a_up, float at_up, float &b,
                                           float &bt, float &a_down, float &at_down, float &wd, float &wu, float &wl,
-                                          float &cd, float &cu, float &cl) {
+                                          float &cd, float &cu, float &cl, float ue = 0.0f, int ug = 0) {
     const int bb = (j >> 5) & 1, c = j & 31;
     const float sv = C.svb[bb][lane][c];
     const float D = soft3(sv, a_up, b, C, wd, wu, wl);
@@ -185,7 +202,8 @@ __device__ __forceinline__ void soft_cell(const SoftCtx &C, int lane, int j, flo
     a_down = __fsub_rn(e, b);
     cd = cu = cl = 0.0f;
     if (TAN) {
-        const float uu = C.ub[bb][lane][c];
+        float G;  // u = dL/dE of the cell, from its E, similarity and gold link
+        const float uu = __fmul_rn(cell_dldp(ue, sv, ug, C, G, nullptr), G);
         const float dua = __fsub_rn(uu, at_up), dub = __fsub_rn(uu, bt), dab = __fsub_rn(at_up, bt);
         cd = __fmaf_rn(wu, dua, __fmul_rn(wl, dub));
         cu = __fmaf_rn(wl, dab, -__fmul_rn(wd, dua));
@@ -224,6 +242,8 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
     float b = -C.two_p, a_down = 0.0f;
     float bt = 0.0f, at_down = 0.0f;
     int have = 0;
+    UIn Ucur, Unext;  // TAN: inputs of u for the current and the next window
+    if (TAN) soft_u_inputs(C, s, 0, Ucur);
     for (int jb = 0; jb <= nb; ++jb) {
         if (jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
         const int colx = 32 * jb + lane;
@@ -231,10 +251,13 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
         if (wait_top && 32 * jb < C.M) soft_wait(C, wait_top, min(32 * jb + 32, C.M), have);
         const float hv = top ? __ldcg(ckv_top + colx) : -C.two_p;
         const float htv = (TAN && top) ? __ldcg(ckt_top + colx) : 0.0f;
-#pragma unroll 4
-        for (int u = 0; u < 32; ++u) {
+        for (int wi = 0; wi < 32 / kWin; ++wi) {
+        if (TAN) soft_u_inputs(C, s, 32 * jb + kWin * (wi + 1), Unext);
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+            const int u = kWin * wi + k;
             const int t = 32 * jb + u;
-            if (ckw_out && (u % kWin) == 0) {
+            if (ckw_out && k == 0) {
                 float *q = ckw_out + (int64_t)(t / kWin) * 128 + lane;
                 q[0] = b;
                 q[32] = a_down;
@@ -254,13 +277,16 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
             const int j = t - lane;
             if (rv && j >= 0 && j < C.M) {
                 float wd, wu, wl, cd, cu, cl;
-                soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl);
+                soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl,
+                               TAN ? Ucur.e[k] : 0.0f, TAN ? (int)((Ucur.g >> k) & 1u) : 0);
                 if (lane == 31 && ckv_out) {
                     __stcg(ckv_out + j, a_down);
                     if (TAN) __stcg(ckt_out + j, at_down);
                 }
                 if (vlast && r == C.N - 1) __stcg(vlast + j, a_down);
             }
+        }
+        if (TAN) Ucur = Unext;
         }
         if (pub && lane == 31) st_release(pub, min(32 * jb + 1, C.M));
     }
@@ -314,7 +340,7 @@ struct SoftAcc {
 
 template <bool TAN>
 __device__ __forceinline__ void soft_fwd_window(SoftCtx &C, int s, int t0, float hv, float htv,
-                                                const float *__restrict__ ckw_w) {
+                                                const float *__restrict__ ckw_w, const UIn &U) {
     const int lane = C.lane;
     const bool rv = 32 * s + lane < C.N;
     float b = ckw_w[lane], a_down = ckw_w[32 + lane];
@@ -334,7 +360,8 @@ __device__ __forceinline__ void soft_fwd_window(SoftCtx &C, int s, int t0, float
         const int j = t - lane;
         if (rv && j >= 0 && j < C.M) {
             float wd, wu, wl, cd, cu, cl;
-            soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl);
+            soft_cell<TAN>(C, lane, j, a_up, at_up, b, bt, a_down, at_down, wd, wu, wl, cd, cu, cl,
+                           TAN ? U.e[k] : 0.0f, TAN ? (int)((U.g >> k) & 1u) : 0);
             C.wb[0][k][lane] = wd;
             C.wb[1][k][lane] = wu;
             C.wb[2][k][lane] = wl;
@@ -493,6 +520,8 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
     int have = 0;
     int cur = -1;  // the block whose windows run (blocks cur and cur - 1 are prepared)
     float hv = 0.0f, htv = 0.0f;
+    UIn Ucur, Unext;  // TAN: inputs of u for the current and the next (left) window
+    if (TAN) soft_u_inputs(C, s, ((C.M + 30) / kWin) * kWin, Ucur);
     for (int w = (C.M + 30) / kWin; w >= 0; --w) {
         const int t0 = w * kWin, jb = t0 >> 5;
         if (jb != cur) {
@@ -507,12 +536,14 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
             hv = top ? __ldcg(ckv_top + colx) : -C.two_p;
             htv = (TAN && top) ? __ldcg(ckt_top + colx) : 0.0f;
         }
+        if (TAN && w > 0) soft_u_inputs(C, s, t0 - kWin, Unext);
         CellIn X;
         soft_cell_inputs<TAN>(C, s, t0, X);
-        soft_fwd_window<TAN>(C, s, t0, hv, htv, ckw + (int64_t)w * 128);
+        soft_fwd_window<TAN>(C, s, t0, hv, htv, ckw + (int64_t)w * 128, Ucur);
         __syncwarp();
         soft_rev_window<TAN>(C, s, t0, R, Z, X, qrow, qtrow, rgamma, wait_below, pub, have);
         __syncwarp();
+        if (TAN) Ucur = Unext;
     }
     Z.fold<NV>();
 }
@@ -583,7 +614,6 @@ struct SoftSmemFwd {
 };
 struct SoftSmemBwd {
     float sv[2][32][32];
-    float ub[2][32][32];
     float wb[6][kWin][32];
     SimCol colv[2][32];
 };
@@ -593,13 +623,11 @@ __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
     if (TAN) {
         SoftSmemBwd &sm = reinterpret_cast<SoftSmemBwd *>(raw)[threadIdx.x >> 5];
         C.svb = sm.sv;
-        C.ub = sm.ub;
         C.wb = sm.wb;
         C.colb = sm.colv;
     } else {
         SoftSmemFwd &sm = reinterpret_cast<SoftSmemFwd *>(raw)[threadIdx.x >> 5];
         C.svb = sm.sv;
-        C.ub = nullptr;
         C.wb = sm.wb;
         C.colb = sm.colv;
     }
@@ -664,8 +692,9 @@ soft_forward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ g
 }
 
 // Sweep 3 (value + tangent, checkpoints) + sweep 4 (adjoint and its tangent):
-// H u for every cell, written over u.  Same work list as the forward.
-__global__ void __launch_bounds__(32 * kSoftBwdWarps)
+// H u for every cell (to the optional output) and the H u part of the
+// gradient.  Same work list as the forward.
+__global__ void __launch_bounds__(32 * kSoftBwdWarps, 6)
 soft_backward_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom, const int32_t *__restrict__ order,
                      DevParams P, SoftArgs A, const uint8_t *__restrict__ counts, const uint8_t *__restrict__ gold,
                      SoftScratch W) {
