@@ -609,6 +609,15 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
     PLAN_CK(dalloc(&p->S.diag_off, n + 1, p->device, st));
     PLAN_CK(dalloc(&p->S.n_links, n, p->device, st));
     PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
+    // the strip count kernel's items (used if the validation's statistics
+    // allow it), built while the validation kernels run
+    std::vector<CountStripItem> sitems;
+    sitems.reserve((size_t)p->soft_strips);
+    for (int32_t k : p->pair_order_h) {  // largest pairs first
+        if (p->geom_h[k].m == 0) continue;
+        const int ns = (p->geom_h[k].n + 31) / 32;
+        for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
+    }
 
     uint32_t status[4];
     int32_t stats[4];
@@ -630,13 +639,6 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
         PLAN_CK(dalloc(&p->count_queue, 1, p->device, st));
     }
     if (p->use_strips) {
-        std::vector<CountStripItem> sitems;
-        sitems.reserve((size_t)p->soft_strips);
-        for (int32_t k : p->pair_order_h) {  // largest pairs first
-            if (p->geom_h[k].m == 0) continue;
-            const int ns = (p->geom_h[k].n + 31) / 32;
-            for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
-        }
         p->n_strip_items = (int64_t)sitems.size();
         PLAN_CK(dalloc(&p->strip_items, sitems.size(), p->device, st));
         PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
