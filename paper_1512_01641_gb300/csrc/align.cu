@@ -46,7 +46,7 @@ __device__ bool wait_flag(const int32_t *f, int64_t limit) {
     return false;
 }
 
-__global__ void __launch_bounds__(32 * kFillWarps, 3)
+__global__ void __launch_bounds__(32 * kFillWarps, 4)
 fill_kernel(DevCorpus src, DevCorpus tgt, const PairGeom *__restrict__ geom,
             const FillItem *__restrict__ items, int64_t n_items, DevParams P,
             const uint8_t *__restrict__ counts, int64_t counts_bytes, bool blocked, AlignScratch S,
