@@ -598,20 +598,20 @@ constexpr int kTilePosRounds = (kPosCap + kTileThreads - 1) / kTileThreads;
 constexpr int kTileTokRounds = (kTokCap + kTileThreads - 1) / kTileThreads;
 
 struct alignas(16) TileSmem {
-    uint64_t bar[2];                // completion barriers of the staged target tokens, per buffer
+    uint64_t bar;                   // completion barrier of the staged target tokens
     int32_t n_ent;                  // translation entries of the row group
-    int32_t tsh[2];                 // staged block: index in tg of its first token | bulk << 30
+    int32_t tsh;                    // staged block: index in tg of its first token | bulk << 30
     int2 ent[kTileSlots];           // hash table: (target id, row mask of the rows translating to it)
     uint32_t cm[kTileSlots + 4];    // column masks of the current block; cm[kTileZero] stays 0
     uint2 prec[kPosCap];            // per source position: byte offsets into cm of its translations' slots
-    uint32_t tg[2][kTokCap + 8];    // staged target tokens (block parity), replaced in place by their row masks
+    uint32_t tg[kTokCap + 8];       // staged target tokens, replaced in place by their row masks
     uint32_t part[kTileWarps][4][32];  // per warp: 4 planes of its quarter counters; then the output tile
     uint8_t mt_t[32][36];           // mt bytes [column][row]
-    uint8_t colid[2][kTokCap];
+    uint8_t colid[kTokCap];
     uint8_t rowid[kPosCap];
-    int32_t ctpre[2][33];           // per column of a staged block: first token index; [32] = total
+    int32_t ctpre[33];              // per column of the staged block: first token index; [32] = total
 };
-static_assert(offsetof(TileSmem, tg) % 16 == 0 && sizeof(TileSmem::tg[0]) % 16 == 0 && offsetof(TileSmem, ent) % 16 == 0 &&
+static_assert(offsetof(TileSmem, tg) % 16 == 0 && offsetof(TileSmem, ent) % 16 == 0 &&
                   offsetof(TileSmem, cm) % 16 == 0 && 4 * (kTileSlots + 3) < 65536,
               "tile kernel shared layout");
 
@@ -690,21 +690,18 @@ __global__ void dict4_kernel(DevDict d, int32_t v_src, int4 *__restrict__ out) {
 }
 
 template <bool BLOCKED>
-__global__ void __launch_bounds__(kTileThreads, 4)
+__global__ void __launch_bounds__(kTileThreads, 5)
 count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, const PairGeom *__restrict__ geom,
                   const CountStripItem *__restrict__ items, int64_t n_items, int32_t *queue, bool bulk_ok,
                   uint8_t *__restrict__ counts, uint32_t *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem &sm = *reinterpret_cast<TileSmem *>(smem_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) {
-        mbar_init(&sm.bar[0]);
-        mbar_init(&sm.bar[1]);
-    }
+    if (tid == 0) mbar_init(&sm.bar);
     for (int x = tid; x < (kTileSlots + 4) / 4; x += kTileThreads)
         reinterpret_cast<uint4 *>(sm.cm)[x] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+    uint32_t phase = 0;
     __shared__ int32_t item_sh;
 
     for (;;) {
@@ -802,31 +799,23 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     nx_lo = nx_hi = 0;
                 }
             };
-            // into buffer jb & 1 (that buffer's previous block, jb - 2, has
-            // been read by every thread)
             auto stage_block = [&](int jb) {
-                const int bf = jb & 1;
                 const int nc = min(32, g.m - 32 * jb);
                 const int my_lt = lane < nc ? (int)(nx_hi - nx_lo) : 0;
                 const int64_t ttok0 = __shfl_sync(kFull, nx_lo, 0);
                 int n_tok;
                 const int tpre = warp_excl_scan(my_lt, lane, n_tok);
-                sm.ctpre[bf][lane] = tpre;
-                if (lane == 0) sm.ctpre[bf][32] = n_tok;
-                for (int t = 0; t < my_lt; ++t) sm.colid[bf][tpre + t] = (uint8_t)lane;
+                sm.ctpre[lane] = tpre;
+                if (lane == 0) sm.ctpre[32] = n_tok;
+                for (int t = 0; t < my_lt; ++t) sm.colid[tpre + t] = (uint8_t)lane;
                 bool bulk_b;
-                const int sh =
-                    stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.tg[bf], &sm.bar[bf], bulk_ok, lane, bulk_b);
-                if (lane == 0) sm.tsh[bf] = sh | (bulk_b ? 1 << 30 : 0);
+                const int sh = stage_issue(tgt.tok, tgt.n_tok, ttok0, n_tok, sm.tg, &sm.bar, bulk_ok, lane, bulk_b);
+                if (lane == 0) sm.tsh = sh | (bulk_b ? 1 << 30 : 0);
             };
             if (warp == kTileWarps - 1) {
                 offsets(0);
                 stage_block(0);
                 offsets(1);
-                if (nblk > 1) {
-                    stage_block(1);
-                    offsets(2);
-                }
             }
             fence_proxy_async();
             __syncthreads();  // table, position records and block 0's staging complete
@@ -839,17 +828,10 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
             for (int jb = 0; jb < nblk; ++jb) {
                 const int c0 = jb * 32;
                 const int nc = min(32, g.m - c0);
-                const int bf = jb & 1;
-                const int tshw = sm.tsh[bf];
-                {
-                    uint32_t ph = (phase >> bf) & 1u;
-                    stage_wait_own((tshw >> 30) & 1, &sm.bar[bf], ph, status);
-                    phase = (phase & ~(1u << bf)) | (ph << bf);
-                }
-                const int n_tok = sm.ctpre[bf][32];
-                const int32_t *ctpre = sm.ctpre[bf];
-                const uint8_t *colid = sm.colid[bf];
-                uint32_t *tg = sm.tg[bf] + (tshw & ((1 << 30) - 1));
+                const int tshw = sm.tsh;
+                stage_wait_own((tshw >> 30) & 1, &sm.bar, phase, status);
+                const int n_tok = sm.ctpre[32];
+                uint32_t *tg = sm.tg + (tshw & ((1 << 30) - 1));
                 // column pass
                 const int trounds = (n_tok + kTileThreads - 1) / kTileThreads;  // the same in every thread
                 uint32_t hit[kTileTokRounds];
@@ -880,7 +862,7 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                                 slot = ent_find_from(sm.ent, tk[k], (hs[k] + 1) & (kTileSlots - 1), rm);
                             }
                             if (slot >= 0) {
-                                atomicOr(&sm.cm[slot], 1u << colid[x]);
+                                atomicOr(&sm.cm[slot], 1u << sm.colid[x]);
                                 hit[k] = (uint32_t)slot;
                             }
                             tg[x] = rm;
@@ -893,8 +875,8 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     BitCounter<4> q4;
                     q4.clear();
                     if (!ms_warp && lane < nc) {
-                        const int t0 = ctpre[lane];
-                        const int t1 = lane < 31 ? ctpre[lane + 1] : n_tok;
+                        const int t0 = sm.ctpre[lane];
+                        const int t1 = lane < 31 ? sm.ctpre[lane + 1] : n_tok;
                         const int L = t1 - t0;
                         acc_words(q4, tg + t0 + ((quarter * L) >> 2), (((quarter + 1) * L) >> 2) - ((quarter * L) >> 2));
                     }
@@ -916,7 +898,7 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) sm.part[warp][k][lane] = q4.p[k];
                 }
-                fence_proxy_async();  // this block's accesses to its buffers come before block jb + 2's copy into them
+                fence_proxy_async();  // this block's accesses to tg come before the next block's copy into it
                 __syncthreads();
                 // column masks back to zero (every hit slot; repeats are harmless)
 #pragma unroll
@@ -924,10 +906,10 @@ count_tile_kernel(DevCorpus src, DevCorpus tgt, const int4 *__restrict__ dict4, 
                     if (k >= trounds) break;
                     if (tid + kTileThreads * k < n_tok) sm.cm[hit[k]] = 0u;
                 }
-                // block jb + 2's tokens go out now into this block's buffers (free)
-                if (warp == kTileWarps - 1 && jb + 2 < nblk) {
-                    stage_block(jb + 2);
-                    offsets(jb + 3);
+                // the next block's tokens go out now (tg, ctpre, colid are free)
+                if (warp == kTileWarps - 1 && jb + 1 < nblk) {
+                    stage_block(jb + 1);
+                    offsets(jb + 2);
                 }
                 // combine the quarters; expand a quarter of the bytes: ms warps
                 // columns 8q .. 8q+7 of row `lane`, mt warps rows 8q .. 8q+7 of
