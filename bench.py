@@ -730,7 +730,7 @@ def main():
 
     bi_rec = None
     if not args.no_bi:
-        bi_rec = run_bi(args, params, dict(tuned["best"]) if tuned else {})
+        bi_rec = run_bi(args, params, {})  # its own 10,000-pair batch: the plan defaults
 
     e2e = None
     if not args.no_e2e:

@@ -268,8 +268,8 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
  * the host and replaces them on the device after the plan's last enqueued
  * work (synchronous: returns once they are in place); set tiling options at
  * creation (mine_plan_create_with_options) where they are known then. */
-#define MINE_OPT_TILE_COLS 1      /* fill tile width in columns, multiple of 32 (128) */
-#define MINE_OPT_TILE_MIN_CELLS 2 /* a pair with at least this many cells ... (262144) */
+#define MINE_OPT_TILE_COLS 1      /* fill tile width in columns, multiple of 32 (64) */
+#define MINE_OPT_TILE_MIN_CELLS 2 /* a pair with at least this many cells ... (65536) */
 #define MINE_OPT_TILE_MIN_ROWS 3  /* ... and this many rows is filled as tiles (64) */
 #define MINE_OPT_WAIT_LIMIT 4     /* spin iterations before a tile wait gives up (2^24) */
 #define MINE_OPT_LINK_RECOUNT 5   /* 1: recount the overlaps of aligned pairs by warp

@@ -19,7 +19,7 @@ import numpy as np
 
 from . import miner
 
-CANDIDATES = {"tile_cols": [32, 64, 128], "tile_min_cells": [1 << 17, 1 << 18, 1 << 20]}
+CANDIDATES = {"tile_cols": [32, 64, 128], "tile_min_cells": [1 << 16, 1 << 17, 1 << 18, 1 << 20]}
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gb300_miner", "autotune.json")
 
 

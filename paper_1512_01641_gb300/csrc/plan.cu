@@ -139,9 +139,9 @@ using namespace gbm;
 
 // Planner knobs (defaults; the tuner may override them per plan).
 struct PlanKnobs {
-    int64_t tile_min_cells = 1 << 18;  // pairs with at least this many cells are tiled
+    int64_t tile_min_cells = 1 << 16;  // pairs with at least this many cells are tiled
     int tile_min_rows = 64;            // ... and at least this many rows
-    int tile_cols = 128;               // column chunk width of a tile (multiple of 32)
+    int tile_cols = 64;                // column chunk width of a tile (multiple of 32)
     int64_t wait_limit = 1 << 24;      // bounded spin iterations of a tile wait (~200 ns each)
     int link_recount = 0;              // 1: recount link overlaps by warp vote
     int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
