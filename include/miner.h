@@ -288,16 +288,19 @@ int mine_links_combine(mine_plan *fwd, const mine_out *out_fwd, mine_plan *rev, 
 #define MINE_OPT_SOFT_SPLIT 10    /* softnw sweeps: 0 one warp per pair; 1 a pair whose
                                      serial chain (strips x (M + 32) steps) is above the
                                      mean per warp is split over warps, one strip each,
-                                     in a wavefront (1); 2 every pair of two or more
-                                     strips is split.  Same results in every mode. */
+                                     in a wavefront; 2 every pair of two or more strips is
+                                     split; 3 (default) every pair of two or more strips is
+                                     split when some pair's chain is above the mean per
+                                     warp, else none.  Same results in every mode. */
 #define MINE_OPT_FAULT_SKIP_SOFT 11 /* fault injection for tests: the forward progress counter
                                        with this index (strips of split pairs, in the soft work
                                        list's order) is never published, so the strips that wait
                                        on it give up after MINE_OPT_WAIT_LIMIT polls and
                                        mine_plan_check reports MINE_ETIMEOUT (-1: off) */
-#define MINE_OPT_SOFT_SPLIT_Q4 13  /* soft split mode 1: a pair is split when its serial chain
-                                      exceeds this many quarters of the mean chain per warp
-                                      (4: the mean); 1 .. 4096.  Same results at any value. */
+#define MINE_OPT_SOFT_SPLIT_Q4 13  /* soft split modes 1 and 3: the chain threshold (of the
+                                      pair, mode 1; of the longest pair, mode 3) in quarters of
+                                      the mean chain per warp (4: the mean); 1 .. 4096.  Same
+                                      results at any value. */
 #define MINE_OPT_SOFT_ORDER 14    /* soft work list with split pairs: 0 each split pair's
                                      value-sweep strips then its adjoint strips, whole pairs
                                      last; 1 (default) every value-sweep strip, the whole pairs,

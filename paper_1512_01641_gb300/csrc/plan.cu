@@ -146,7 +146,7 @@ struct PlanKnobs {
     int link_recount = 0;              // 1: recount link overlaps by warp vote
     int use_graph = 1;                 // 1: mine_pairs replays a captured CUDA graph
     int64_t skip_flag = -1;            // fault injection: tile flag never published (tests)
-    int soft_split = 1;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs split over warps
+    int soft_split = 3;                // soft sweeps: 0 never / 1 long pairs / 2 all pairs / 3 all once one must
     int soft_split_q4 = 4;             // split = 1: above this many quarters of the mean chain per warp
     int soft_order = 1;                // soft work list: 0 per pair, 1 value sweeps/whole/adjoints, 2 value/adjoints/whole
     int64_t skip_soft = -1;            // fault injection: soft progress counter never published (tests)
@@ -472,7 +472,7 @@ static int knob_apply(PlanKnobs &k, int option, int64_t value, int *effect) {
             *effect = kKnobGraph;
             return MINE_OK;
         case MINE_OPT_SOFT_SPLIT:
-            if (value < 0 || value > 2) return MINE_EINVAL;
+            if (value < 0 || value > 3) return MINE_EINVAL;
             k.soft_split = (int)value;
             return MINE_OK;
         case MINE_OPT_FAULT_SKIP_SOFT:

@@ -74,6 +74,7 @@ struct SoftCtx {
     float *E;              // pair's expected alignment
     float *hvp;            // pair's H u output (backward, may be null)
     SimCol (*colb)[32];    // shared: column constants of the current and previous block [2][col]
+    SimRow *rowv;          // shared: constants of the current strip's 32 rows
     float (*svb)[32][32];  // shared: similarities of the current and previous block [2][row][col]
     float (*wb)[kWin][32]; // shared: the recomputed window's per-cell weights [component][step][lane]
     int64_t wait_limit;    // bounded spins of a strip wait
@@ -131,29 +132,44 @@ __device__ __forceinline__ float cell_dldp(float E, float sv, int g, const SoftC
     return __fmul_rn(g ? -rcp_approx(Pr) : rcp_approx(__fsub_rn(1.0f, Pr)), C.inv_cells);
 }
 
-// Similarities of block jb of the current strip into shared buffer jb & 1
-// with the block's column constants; lane = row, columns written in rotated
-// order.
+// Similarities of block jb of strip s into shared buffer jb & 1 with the
+// block's column constants.  Lane = column here: row i of the block is one
+// coalesced 64-byte load across the warp (a lane-per-row load would touch 32
+// cache lines per instruction), all 32 rows in flight at once; the rows'
+// constants come from the warp's shared copy (rowv), the column's from a
+// register.  sv[i][lane] for fixed i hits 32 distinct banks.
 template <bool TAN>
-__device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int r, bool rv, int jb) {
+__device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int s, int jb) {
     const int lane = C.lane;
-    const int col0 = 32 * jb;
+    const int col = 32 * jb + lane;
+    const bool cok = col < C.M;
+    const int nr = min(32, C.N - 32 * s);
+    const uint16_t *cp = reinterpret_cast<const uint16_t *>(C.cnt) + (int64_t)(32 * s) * C.M + col;
+    const int lt = cok ? (int)(C.tsent[col + 1] - C.tsent[col]) : 1;
+    uint32_t q[16];
     SimCol *cv = C.colb[jb & 1];
-    __syncwarp();
-    cv[lane] = sim_col(col0 + lane < C.M ? (int)(C.tsent[col0 + lane + 1] - C.tsent[col0 + lane]) : 1, C.P);
-    __syncwarp();
     float(*sv)[32] = C.svb[jb & 1];
-    const uchar2 *rowc = C.cnt + (int64_t)r * C.M;
-#pragma unroll 8
-    for (int x = 0; x < 32; ++x) {
-        const int c = (x + lane) & 31;
-        const int col = col0 + c;
-        float v = 0.0f;
-        if (rv && col < C.M) {
-            const uchar2 q = rowc[col];
-            v = similarity(q.x, q.y, C.row, cv[c], C.K);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) q[i] = (cok && i < nr) ? (uint32_t)cp[(int64_t)i * C.M] : 0u;
+    const SimCol sc = sim_col(lt, C.P);
+    __syncwarp();  // the previous readers of buffer jb & 1 are done
+    cv[lane] = sc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t qn[16];
+        if (h == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) qn[i] = (cok && 16 + i < nr) ? (uint32_t)cp[(int64_t)(16 + i) * C.M] : 0u;
         }
-        sv[lane][c] = v;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int row = 16 * h + i;
+            sv[row][lane] = (cok && row < nr) ? similarity_q16(q[i], C.rowv[row], sc, C.K) : 0.0f;
+        }
+        if (h == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) q[i] = qn[i];
+        }
     }
     __syncwarp();
 }
@@ -238,6 +254,8 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
     C.row = sim_row(rv ? (int)(C.ssent[r + 1] - C.ssent[r]) : 1, C.P);
+    __syncwarp();  // the previous strip's last block is prepared
+    C.rowv[lane] = C.row;
     const int nb = (C.M + 31) >> 5;
     float b = -C.two_p, a_down = 0.0f;
     float bt = 0.0f, at_down = 0.0f;
@@ -245,7 +263,7 @@ __device__ __forceinline__ void soft_fwd_strip(SoftCtx &C, int s, const float *_
     UIn Ucur, Unext;  // TAN: inputs of u for the current and the next window
     if (TAN) soft_u_inputs(C, s, 0, Ucur);
     for (int jb = 0; jb <= nb; ++jb) {
-        if (jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
+        if (jb < nb) soft_prep_block<TAN>(C, s, jb);
         const int colx = 32 * jb + lane;
         const bool top = s > 0 && colx < C.M;
         if (wait_top && 32 * jb < C.M) soft_wait(C, wait_top, min(32 * jb + 32, C.M), have);
@@ -515,6 +533,8 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
     const int r = 32 * s + lane;
     const bool rv = r < C.N;
     C.row = sim_row(rv ? (int)(C.ssent[r + 1] - C.ssent[r]) : 1, C.P);
+    __syncwarp();  // the previous strip's last block is prepared
+    C.rowv[lane] = C.row;
     const int nb = (C.M + 31) >> 5;
     RevState R{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     int have = 0;
@@ -528,8 +548,8 @@ __device__ __forceinline__ void soft_adjoint_strip(SoftCtx &C, int s, const floa
             Z.fold<NV>();
             // windows of block jb read blocks jb and jb - 1; going left, block jb
             // is ready from block jb + 1's windows except at the start
-            if (cur < 0 && jb < nb) soft_prep_block<TAN>(C, r, rv, jb);
-            if (jb >= 1) soft_prep_block<TAN>(C, r, rv, jb - 1);
+            if (cur < 0 && jb < nb) soft_prep_block<TAN>(C, s, jb);
+            if (jb >= 1) soft_prep_block<TAN>(C, s, jb - 1);
             cur = jb;
             const int colx = 32 * jb + lane;
             const bool top = s > 0 && colx < C.M;
@@ -611,11 +631,13 @@ struct SoftSmemFwd {
     float sv[2][32][32];
     float wb[3][kWin][32];
     SimCol colv[2][32];
+    SimRow rowv[32];
 };
 struct SoftSmemBwd {
     float sv[2][32][32];
     float wb[6][kWin][32];
     SimCol colv[2][32];
+    SimRow rowv[32];
 };
 
 template <bool TAN>
@@ -625,11 +647,13 @@ __device__ __forceinline__ void bind_smem(SoftCtx &C, unsigned char *raw) {
         C.svb = sm.sv;
         C.wb = sm.wb;
         C.colb = sm.colv;
+        C.rowv = sm.rowv;
     } else {
         SoftSmemFwd &sm = reinterpret_cast<SoftSmemFwd *>(raw)[threadIdx.x >> 5];
         C.svb = sm.sv;
         C.wb = sm.wb;
         C.colb = sm.colv;
+        C.rowv = sm.rowv;
     }
 }
 
@@ -801,15 +825,27 @@ soft_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__
         m = g.m;
         return (int64_t)((g.n + 31) >> 5);
     };
-    int64_t tot = 0, chain = 0;
+    __shared__ unsigned long long longest;  // the longest serial chain of a pair
+    if (threadIdx.x == 0) longest = 0ull;
+    __syncthreads();
+    int64_t tot = 0, chain = 0, mx = 0;
     for (int64_t pos = threadIdx.x; pos < n_pairs; pos += blockDim.x) {
         int32_t n, m;
         const int64_t S = strips(pos, n, m);
         chain += S * (m + 32);
+        mx = max(mx, S * (m + 32));
     }
-    (void)block_scan(chain, tot);
-    const int64_t thr =
-        split == 2 ? 0 : (split == 1 ? tot * split_q4 / (4 * (n_warps > 0 ? n_warps : 1)) : INT64_MAX);
+    atomicMax(&longest, (unsigned long long)mx);
+    (void)block_scan(chain, tot);  // its barriers also order the atomicMax before the read
+    // mode 1: the pairs whose chain passes q4/4 of the mean chain per warp;
+    // mode 3: every pair of two or more strips, once one pair's chain passes
+    // it (that pair's wavefront then sets the pace, and a whole pair sweeping
+    // value and adjoint in series on one warp would trail it), else none
+    const int64_t mean_q = tot * split_q4 / (4 * (n_warps > 0 ? n_warps : 1));
+    const int64_t thr = split == 2   ? 0
+                        : split == 1 ? mean_q
+                        : split == 3 ? ((int64_t)longest > mean_q ? 0 : INT64_MAX)
+                                     : INT64_MAX;
     auto counts = [&](int64_t pos, int64_t &si, int64_t &sc, int64_t &wi, int64_t &sl) {
         int32_t n, m;
         const int64_t S = strips(pos, n, m);

@@ -58,7 +58,7 @@ def test_strerror_without_gpu(libpath):
     [(9, 0)],                        # MINE_OPT_N_TILE_FLAGS is read-only
     [(1, 48)],                       # tile width not a multiple of 32
     [(1, 64), (2, 0)],               # a valid option followed by an invalid one
-    [(10, 3)],                       # soft split mode out of range
+    [(10, 4)],                       # soft split mode out of range
 ])
 def test_create_with_options_rejects_bad_options_before_device_work(libpath, opts):
     # option validation comes before any CUDA call, so this runs without a GPU;

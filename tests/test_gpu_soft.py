@@ -197,7 +197,7 @@ def _soft_all(plan, counts, gold, gamma, split):
 def test_split_sweeps_are_bit_identical_to_one_warp_per_pair():
     """Splitting a pair's strips over warps (a wavefront with progress
     counters) runs the same arithmetic in the same order: loss, V, E, the
-    gradient and H u are bit-identical in all three modes, on pairs of 1 to
+    gradient and H u are bit-identical in all four modes, on pairs of 1 to
     9 strips with ragged last strips and ragged column blocks."""
     import torch
     from paper_1512_01641_gb300 import miner
@@ -207,17 +207,18 @@ def test_split_sweeps_are_bit_identical_to_one_warp_per_pair():
     counts = plan.count()
     gold = torch.from_numpy(miner.gold_cells(batch, plan)).cuda()
     ref = _soft_all(plan, counts, gold, 0.1, 0)
-    for split in (1, 2):
+    for split in (1, 2, 3):
         got = _soft_all(plan, counts, gold, 0.1, split)
         for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
             assert np.array_equal(a, b), (split, name, np.abs(a - b).max())
-    assert plan.get_option("soft_split") == 2
+    assert plan.get_option("soft_split") == 3
     # mode 1 with other split thresholds (quarters of the mean chain per warp)
     for q4 in (1, 64):
         plan.set_option("soft_split_q4", q4)
-        got = _soft_all(plan, counts, gold, 0.1, 1)
-        for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
-            assert np.array_equal(a, b), (q4, name, np.abs(a - b).max())
+        for split in (1, 3):
+            got = _soft_all(plan, counts, gold, 0.1, split)
+            for name, a, b in zip(("loss", "value", "E", "grad", "hvp"), ref, got):
+                assert np.array_equal(a, b), (q4, split, name, np.abs(a - b).max())
     assert plan.get_option("soft_split_q4") == 64
     # the other work-list orders (value sweeps and adjoints per pair; adjoints before whole pairs)
     plan.set_option("soft_split_q4", 4)
