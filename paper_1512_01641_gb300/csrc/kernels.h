@@ -197,7 +197,7 @@ struct SoftScratch {
     SoftItem *items;      // sweep work list
     int32_t *prog1;       // per strip of a split pair: forward columns published
     int32_t *prog2;       // per strip of a split pair: adjoint steps published
-    float *E;             // expected alignment per cell
+    float *E;             // expected alignment per cell, per strip step-major (soft_e_index)
     float *ckv, *ckt;     // checkpoint rows (value, tangent), nstrips * M per pair at soft_off
     float *qrow, *qtrow;  // adjoint boundary rows (value, tangent), at soft_off
     float *ckw;           // per strip: the sweep state at the start of every window
@@ -209,6 +209,7 @@ int64_t soft_warps(int n_sms);
 // (the adjoint sweeps recompute 8-step windows from them).
 __host__ __device__ inline int64_t soft_ckw_floats(int M) { return 128 * (32 * ((M + 31) / 32 + 1) / 8); }
 
+cudaError_t launch_soft_export_e(const PairGeom *geom, int64_t n_pairs, const float *E, float *out, cudaStream_t st);
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
                                 const int32_t *order, int64_t n_pairs, const DevParams &P, const SoftArgs &A,
                                 const uint8_t *counts, const uint8_t *gold, const SoftScratch &W, float *loss,

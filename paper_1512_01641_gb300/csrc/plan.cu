@@ -858,8 +858,8 @@ static SoftLayout soft_layout(const mine_plan *p) {
     o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
     L.prog2 = o;
     o = align_up(o + std::max<int64_t>(L.ctr_cap, 1) * 4, 256);
-    L.E = o;
-    o = align_up(o + std::max<int64_t>(p->n_cells, 1) * 4, 256);
+    L.E = o;  // per strip, step-major: twice the window checkpoints
+    o = align_up(o + std::max<int64_t>(2 * p->soft_ckw, 1) * 4, 256);
     const int64_t rows = std::max<int64_t>(p->soft_rows, 1) * 4;
     L.ckv = o;
     o = align_up(o + rows, 256);
@@ -941,8 +941,7 @@ int softnw_fwd(mine_plan *p, const mine_params *params, const softnw_opts *opts,
         return launch_soft_forward(p->src, p->tgt, p->geom, order, n, P, A, counts, gold, W, loss, value, p->n_sms,
                                    st);
     }));
-    if (expected && p->n_cells > 0)
-        MINE_CK(cudaMemcpyAsync(expected, W.E, p->n_cells * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (expected && p->n_cells > 0) MINE_CK(launch_soft_export_e(p->geom, p->n_pairs, W.E, expected, st));
     return MINE_OK;
 }
 

@@ -178,6 +178,16 @@ __device__ __forceinline__ void soft_prep_block(const SoftCtx &C, int s, int jb)
 // from t0 (column t0 + k - lane at step t0 + k): E and the gold links,
 // loaded a window ahead of their use so that their latency overlaps a
 // window of steps.
+// E's place in the sweeps' layout: per strip, forward step t = j + lane
+// major and lane minor, so that the 32 cells of one step (an anti-diagonal)
+// are one 128-byte line for the reverse steps that write them and the
+// backward's steps that read them (row-major, each step's cells would lie in
+// 32 different lines).  A strip holds 32 (nb + 1) steps, twice its window
+// checkpoints.
+__host__ __device__ __forceinline__ int64_t soft_e_index(int M, int s, int t, int lane) {
+    return (int64_t)s * 2 * soft_ckw_floats(M) + (int64_t)t * 32 + lane;
+}
+
 struct UIn {
     float e[kWin];
     uint32_t g;  // bit k: gold link of step k's cell
@@ -193,7 +203,7 @@ __device__ __forceinline__ void soft_u_inputs(const SoftCtx &C, int s, int t0, U
         X.e[k] = 0.0f;
         if (rv && j >= 0 && j < C.M) {
             const int64_t c = (int64_t)r * C.M + j;
-            X.e[k] = C.E[c];
+            X.e[k] = C.E[soft_e_index(C.M, s, t0 + k, lane)];
             X.g |= (uint32_t)(C.gold[c] != 0) << k;
         }
     }
@@ -496,7 +506,7 @@ __device__ __forceinline__ void soft_rev_window(SoftCtx &C, int s, int t0, RevSt
                 Z.f[4] = __fadd_rn(Z.f[4], dz);
                 Z.f[5] = __fmaf_rn(2.0f, Hu, Z.f[5]);
             } else {
-                C.E[c] = Ec;
+                C.E[soft_e_index(C.M, s, t0 + kk, lane)] = Ec;
                 // the cell's loss term and the part of dL/ds through the gate,
                 // dL/dP E dG/ds, to w (through s(1-s) and the features), b
                 // and thr
@@ -602,7 +612,7 @@ __device__ __forceinline__ void ctx_for_pair(SoftCtx &C, const PairGeom &g, int6
     C.tsent = tgt.sent + tgt.doc[k];
     C.cnt = reinterpret_cast<const uchar2 *>(counts) + g.cell_off;
     C.gold = gold + g.cell_off;
-    C.E = W.E + g.cell_off;
+    C.E = W.E + 2 * g.ckw_off;
     C.hvp = nullptr;
 }
 
@@ -1004,6 +1014,26 @@ static void launch_soft_items(const PairGeom *geom, const int32_t *order, int64_
                               const SoftScratch &W, int n_sms, cudaStream_t st) {
     soft_items_kernel<<<1, 1024, 0, st>>>(geom, order, n_pairs, soft_warps(n_sms), A.split, A.split_q4, A.order,
                                           A.status, W);
+}
+
+// E of every cell of the plan from the sweeps' layout into the caller's
+// row-major cells (one block per pair).
+__global__ void __launch_bounds__(256) soft_export_e_kernel(const PairGeom *__restrict__ geom,
+                                                            const float *__restrict__ E, float *__restrict__ out) {
+    const PairGeom g = geom[blockIdx.x];
+    if (g.n <= 0 || g.m <= 0) return;
+    const float *Ep = E + 2 * g.ckw_off;
+    const int64_t cells = (int64_t)g.n * g.m;
+    for (int64_t c = threadIdx.x; c < cells; c += blockDim.x) {
+        const int i = (int)(c / g.m), j = (int)(c - (int64_t)i * g.m);
+        out[g.cell_off + c] = Ep[soft_e_index(g.m, i >> 5, j + (i & 31), i & 31)];
+    }
+}
+
+cudaError_t launch_soft_export_e(const PairGeom *geom, int64_t n_pairs, const float *E, float *out, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    soft_export_e_kernel<<<(unsigned)n_pairs, 256, 0, st>>>(geom, E, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_soft_forward(const DevCorpus &src, const DevCorpus &tgt, const PairGeom *geom,
