@@ -587,7 +587,20 @@ def e2e_host_abi(batch, params, steps, options=None):
         times.append(time.perf_counter() - t0)
     n = int(out["link_off"][-1])
     d2h = out["link_off"].numel() * 8 + batch.n_pairs * 4 + n * 12
-    return float(np.median(times)), h2d, d2h
+    # the same uploads alone (torch copies of the eight pinned arrays, one
+    # stream): what the host link gives on this machine, beside the call's time
+    dev = [torch.empty_like(t, device="cuda") for t in pinned]
+    copy_ms = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d, t in zip(dev, pinned):
+            d.copy_(t, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        copy_ms.append(e0.elapsed_time(e1))
+    del dev
+    return float(np.median(times)), h2d, d2h, float(np.median(copy_ms))
 
 
 def e2e_pipelined(batch, params, steps, options=None):
@@ -736,7 +749,7 @@ def main():
     if not args.no_e2e:
         plan_keep = plan
         opts = dict(tuned["best"]) if tuned else {}
-        e_abi, h2d, d2h = e2e_host_abi(batch, params, args.e2e_steps, opts)
+        e_abi, h2d, d2h, copy_ms = e2e_host_abi(batch, params, args.e2e_steps, opts)
         e_t, d2h_p = e2e_pipelined(batch, params, args.e2e_stream_steps, opts)
         e2e = {"value": cells_step / world / e_abi * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "seconds_per_step": e_abi,
@@ -744,6 +757,9 @@ def main():
                            "plan creation (validation, geometry, scratch), mining, D2H of links and scores "
                            f"(median of {args.e2e_steps} steps)",
                "plan_options": opts,
+               "h2d_copy_alone": {"ms": copy_ms, "gbs": h2d / copy_ms / 1e6,
+                                  "what": "the eight input arrays copied alone from pinned host memory "
+                                          "(torch copies, one stream, median of 3)"},
                "pipelined": {"value": cells_step / world / e_t * world, "seconds_per_step": e_t,
                              "d2h_bytes_per_step": d2h_p,
                              "includes": "the same work streamed batch after batch through BatchPipeline (the "

@@ -113,6 +113,61 @@ cudaError_t dalloc(T **p, size_t n, int device, cudaStream_t st) {
     return cudaMallocFromPoolAsync((void **)p, n * sizeof(T), pool, st);
 }
 
+// Pinned staging for the tables a plan builds on the host (geometry, pair
+// order, work lists).  A copy from pageable memory goes through the driver's
+// small staging buffers and returns only once the copy engine has taken it,
+// so while a large input upload was in flight (mine_pairs_host) plan creation
+// stalled at its first table copy until the inputs had landed, and its
+// remaining host work ran after them.  From pinned memory the copies are
+// queued and the host goes on.  One grow-only buffer per device, reused once
+// the copies of its previous use have completed.
+struct HostStage {
+    std::mutex mu;
+    char *buf = nullptr;
+    size_t cap = 0;
+    cudaEvent_t used = nullptr;
+};
+HostStage g_stage[kMaxDevices];
+
+struct StagePiece {
+    const void *h;
+    void *d;
+    size_t bytes;
+};
+
+// Copies every piece (host source, device destination, bytes) to the device
+// on st through the device's staging buffer.
+cudaError_t staged_upload(int device, const StagePiece *pcs, int n, cudaStream_t st) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    HostStage &S = g_stage[device];
+    std::lock_guard<std::mutex> lock(S.mu);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) total += (pcs[i].bytes + 255) & ~(size_t)255;
+    cudaError_t e = S.used ? cudaEventSynchronize(S.used) : cudaEventCreateWithFlags(&S.used, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    if (total > S.cap) {
+        if (S.buf) {
+            e = cudaFreeHost(S.buf);
+            S.buf = nullptr;
+            S.cap = 0;
+            if (e != cudaSuccess) return e;
+        }
+        const size_t cap = std::max(total + total / 4, (size_t)1 << 20);
+        e = cudaMallocHost((void **)&S.buf, cap);
+        if (e != cudaSuccess) return e;
+        S.cap = cap;
+    }
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        if (pcs[i].bytes == 0) continue;
+        std::memcpy(S.buf + off, pcs[i].h, pcs[i].bytes);
+        e = cudaMemcpyAsync(pcs[i].d, S.buf + off, pcs[i].bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        off += (pcs[i].bytes + 255) & ~(size_t)255;
+    }
+    return cudaEventRecord(S.used, st);
+}
+
 }  // namespace
 
 void record_cuda_error(int e) { g_last_cuda = e; }
@@ -588,12 +643,26 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
     std::vector<FillItem> fitems;
     int64_t tbw = 0, hrow = 0, vcol = 0;
     build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
+    // the strip count kernel's items (used if the validation's statistics
+    // allow it), built while the validation kernels run
+    std::vector<CountStripItem> sitems;
+    sitems.reserve((size_t)p->soft_strips);
+    for (int32_t k : p->pair_order_h) {  // largest pairs first
+        if (p->geom_h[k].m == 0) continue;
+        const int ns = (p->geom_h[k].n + 31) / 32;
+        for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
+    }
     PLAN_CK(dalloc(&p->geom, n, p->device, st));
-    PLAN_CK(cudaMemcpyAsync(p->geom, p->geom_h.data(), n * sizeof(PairGeom), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->pair_order, n, p->device, st));
-    PLAN_CK(cudaMemcpyAsync(p->pair_order, p->pair_order_h.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PLAN_CK(dalloc(&p->fill_items, fitems.size(), p->device, st));
-    PLAN_CK(cudaMemcpyAsync(p->fill_items, fitems.data(), fitems.size() * sizeof(FillItem), cudaMemcpyHostToDevice, st));
+    PLAN_CK(dalloc(&p->strip_items, sitems.size(), p->device, st));
+    {
+        const StagePiece pcs[4] = {{p->geom_h.data(), p->geom, n * sizeof(PairGeom)},
+                                   {p->pair_order_h.data(), p->pair_order, n * sizeof(int32_t)},
+                                   {fitems.data(), p->fill_items, fitems.size() * sizeof(FillItem)},
+                                   {sitems.data(), p->strip_items, sitems.size() * sizeof(CountStripItem)}};
+        PLAN_CK(staged_upload(p->device, pcs, 4, st));
+    }
 
     // scratch
     p->v_src = dict->v_src;
@@ -609,15 +678,6 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
     PLAN_CK(dalloc(&p->S.diag_off, n + 1, p->device, st));
     PLAN_CK(dalloc(&p->S.n_links, n, p->device, st));
     PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
-    // the strip count kernel's items (used if the validation's statistics
-    // allow it), built while the validation kernels run
-    std::vector<CountStripItem> sitems;
-    sitems.reserve((size_t)p->soft_strips);
-    for (int32_t k : p->pair_order_h) {  // largest pairs first
-        if (p->geom_h[k].m == 0) continue;
-        const int ns = (p->geom_h[k].n + 31) / 32;
-        for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
-    }
 
     uint32_t status[4];
     int32_t stats[4];
@@ -639,11 +699,7 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
         PLAN_CK(dalloc(&p->count_queue, 1, p->device, st));
     }
     if (p->use_strips) {
-        p->n_strip_items = (int64_t)sitems.size();
-        PLAN_CK(dalloc(&p->strip_items, sitems.size(), p->device, st));
-        PLAN_CK(cudaMemcpyAsync(p->strip_items, sitems.data(), sitems.size() * sizeof(CountStripItem),
-                                cudaMemcpyHostToDevice, st));
-        PLAN_CK(cudaStreamSynchronize(st));
+        p->n_strip_items = (int64_t)sitems.size();  // uploaded with the geometry
     } else {
         std::vector<CountItem> citems;
         build_count_items(p, citems);
