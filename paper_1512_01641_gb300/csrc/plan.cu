@@ -443,24 +443,46 @@ static void build_geometry(mine_plan *p, const std::vector<int64_t> &sd, const s
             small.push_back(k);
     }
 
-    // fill items
+    // fill items: anti-diagonal d of the tile wavefronts holds the tiles
+    // (s, c) with s + c = d of every tiled pair (pairs in size order, strips
+    // ascending), and after each diagonal's tiles come per_diag whole small
+    // pairs.  The tiles are bucketed by diagonal in one pass (a counting
+    // sort, stable in pair and strip order), not found by a scan of every
+    // pair's strips for every diagonal.
     fitems.clear();
-    int64_t max_diag = 0;
+    int64_t max_diag = 0, n_tiles = 0;
     for (int32_t k : tiled) {
         const PairGeom &g = p->geom_h[k];
         max_diag = std::max<int64_t>(max_diag, (g.n + 31) / 32 + g.nchunk - 1);
+        n_tiles += (int64_t)((g.n + 31) / 32) * g.nchunk;
     }
+    std::vector<int64_t> dpos((size_t)max_diag + 1, 0);
+    for (int32_t k : tiled) {
+        const PairGeom &g = p->geom_h[k];
+        for (int s = 0; s < (g.n + 31) / 32; ++s) {  // diagonals s .. s + nchunk - 1, one tile each
+            ++dpos[(size_t)s];
+            --dpos[(size_t)(s + g.nchunk)];
+        }
+    }
+    for (int64_t d = 0, run = 0, at = 0; d <= max_diag; ++d) {  // tiles per diagonal -> first index
+        run += dpos[(size_t)d];
+        dpos[(size_t)d] = at;
+        at += run;
+    }
+    std::vector<FillItem> tiles((size_t)n_tiles);
+    {
+        std::vector<int64_t> put(dpos.begin(), dpos.end());
+        for (int32_t k : tiled) {
+            const PairGeom &g = p->geom_h[k];
+            for (int s = 0; s < (g.n + 31) / 32; ++s)
+                for (int32_t cj = 0; cj < g.nchunk; ++cj) tiles[(size_t)put[(size_t)(s + cj)]++] = {k, s, s + 1, cj};
+        }
+    }
+    fitems.reserve((size_t)n_tiles + small.size());
     const int64_t per_diag = max_diag > 0 ? ((int64_t)small.size() + max_diag - 1) / max_diag : 0;
     size_t next_small = 0;
     for (int64_t d = 0; d < max_diag; ++d) {
-        for (int32_t k : tiled) {
-            const PairGeom &g = p->geom_h[k];
-            const int ns = (g.n + 31) / 32;
-            for (int s = 0; s < ns; ++s) {
-                const int64_t cj = d - s;
-                if (cj >= 0 && cj < g.nchunk) fitems.push_back({k, s, s + 1, (int32_t)cj});
-            }
-        }
+        fitems.insert(fitems.end(), tiles.begin() + dpos[(size_t)d], tiles.begin() + dpos[(size_t)d + 1]);
         for (int64_t q = 0; q < per_diag && next_small < small.size(); ++q, ++next_small) {
             const int32_t k = small[next_small];
             fitems.push_back({k, 0, (p->geom_h[k].n + 31) / 32, 0});
