@@ -89,6 +89,10 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
 
 // Fixed-width copy of a dictionary whose lists hold at most four targets.
 cudaError_t launch_dict4(const DevDict &dict, int32_t v_src, int4 *dict4, cudaStream_t st);
+// Every 32-row strip of every pair with targets as a count item, pairs in the
+// given order (cnt: n ints, off: n + 1 int64 of scratch).
+cudaError_t launch_strip_items(const PairGeom *geom, const int32_t *order, int64_t n, int32_t *cnt, int64_t *off,
+                               CountStripItem *items, cudaStream_t st);
 // Tile count kernel (sentences of at most 31 tokens, dictionary fan-out at
 // most 4): blocked = true writes the blocked layout (pair k's 32 x 32 block
 // (s, b) is the 2048-byte tile at byte 64 * tb_off + 2048 * (s * nblk + b),

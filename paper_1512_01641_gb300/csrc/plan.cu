@@ -665,25 +665,14 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
     std::vector<FillItem> fitems;
     int64_t tbw = 0, hrow = 0, vcol = 0;
     build_geometry(p, sd, td, fitems, tbw, hrow, vcol);
-    // the strip count kernel's items (used if the validation's statistics
-    // allow it), built while the validation kernels run
-    std::vector<CountStripItem> sitems;
-    sitems.reserve((size_t)p->soft_strips);
-    for (int32_t k : p->pair_order_h) {  // largest pairs first
-        if (p->geom_h[k].m == 0) continue;
-        const int ns = (p->geom_h[k].n + 31) / 32;
-        for (int sidx = 0; sidx < ns; ++sidx) sitems.push_back({k, sidx, 0, 32});
-    }
     PLAN_CK(dalloc(&p->geom, n, p->device, st));
     PLAN_CK(dalloc(&p->pair_order, n, p->device, st));
     PLAN_CK(dalloc(&p->fill_items, fitems.size(), p->device, st));
-    PLAN_CK(dalloc(&p->strip_items, sitems.size(), p->device, st));
     {
-        const StagePiece pcs[4] = {{p->geom_h.data(), p->geom, n * sizeof(PairGeom)},
+        const StagePiece pcs[3] = {{p->geom_h.data(), p->geom, n * sizeof(PairGeom)},
                                    {p->pair_order_h.data(), p->pair_order, n * sizeof(int32_t)},
-                                   {fitems.data(), p->fill_items, fitems.size() * sizeof(FillItem)},
-                                   {sitems.data(), p->strip_items, sitems.size() * sizeof(CountStripItem)}};
-        PLAN_CK(staged_upload(p->device, pcs, 4, st));
+                                   {fitems.data(), p->fill_items, fitems.size() * sizeof(FillItem)}};
+        PLAN_CK(staged_upload(p->device, pcs, 3, st));
     }
 
     // scratch
@@ -700,6 +689,14 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
     PLAN_CK(dalloc(&p->S.diag_off, n + 1, p->device, st));
     PLAN_CK(dalloc(&p->S.n_links, n, p->device, st));
     PLAN_CK(launch_block_tokens(p->tgt, p->geom, n, p->stats + 2, st));
+    // the strip count kernels' items (used if the validation's statistics
+    // allow it), built on the device while the validation kernels run, in
+    // scratch the walk overwrites later
+    int64_t n_strips = 0;
+    for (int64_t k = 0; k < n; ++k)
+        if (p->geom_h[k].m > 0) n_strips += (p->geom_h[k].n + 31) / 32;
+    PLAN_CK(dalloc(&p->strip_items, n_strips, p->device, st));
+    PLAN_CK(launch_strip_items(p->geom, p->pair_order, n, p->S.n_diag, p->S.diag_off, p->strip_items, st));
 
     uint32_t status[4];
     int32_t stats[4];
@@ -721,7 +718,7 @@ static int plan_create(const mine_corpus *src, const mine_corpus *tgt, const min
         PLAN_CK(dalloc(&p->count_queue, 1, p->device, st));
     }
     if (p->use_strips) {
-        p->n_strip_items = (int64_t)sitems.size();  // uploaded with the geometry
+        p->n_strip_items = n_strips;
     } else {
         std::vector<CountItem> citems;
         build_count_items(p, citems);
