@@ -674,30 +674,6 @@ __device__ __forceinline__ uint32_t nibble_bytes(const uint32_t (&p)[5], int m) 
     return w;
 }
 
-// Strip items of the count kernels, built on the device from the plan's
-// geometry and size order: the number of 32-row strips of the pair at each
-// position of the order (0 for a pair without targets) ...
-__global__ void strip_counts_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n,
-                                    int32_t *__restrict__ cnt) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < n; pos += stride) {
-        const PairGeom g = geom[order[pos]];
-        cnt[pos] = g.m > 0 ? (g.n + 31) / 32 : 0;
-    }
-}
-// ... and, from their exclusive scan, every strip's item at its place (pairs
-// largest first, strips in order, the whole 32-row group).
-__global__ void strip_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n,
-                                   const int64_t *__restrict__ off, CountStripItem *__restrict__ items) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < n; pos += stride) {
-        const int32_t k = order[pos];
-        const PairGeom g = geom[k];
-        const int ns = g.m > 0 ? (g.n + 31) / 32 : 0;
-        for (int sidx = 0; sidx < ns; ++sidx) items[off[pos] + sidx] = CountStripItem{k, sidx, 0, 32};
-    }
-}
-
 // Fixed-width dictionary: entry v holds the translations of source id v, -1
 // padded (every list has at most four entries).
 __global__ void dict4_kernel(DevDict d, int32_t v_src, int4 *__restrict__ out) {
@@ -1051,17 +1027,6 @@ cudaError_t launch_count_strips(const DevCorpus &src, const DevCorpus &tgt, cons
                    ? launch_strip_t<11, 5>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st)
                    : launch_strip_t<11, 8>(src, tgt, dict, geom, items, n_items, bulk_ok, counts, status, n_sms, st);
     return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_strip_items(const PairGeom *geom, const int32_t *order, int64_t n, int32_t *cnt, int64_t *off,
-                               CountStripItem *items, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
-    strip_counts_kernel<<<grid, 256, 0, st>>>(geom, order, n, cnt);
-    cudaError_t e = launch_scan(cnt, n, off, st);
-    if (e != cudaSuccess) return e;
-    strip_items_kernel<<<grid, 256, 0, st>>>(geom, order, n, off, items);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_dict4(const DevDict &dict, int32_t v_src, int4 *dict4, cudaStream_t st) {

@@ -1385,6 +1385,41 @@ int mine_align_unconstrained(mine_plan *p, const mine_params *params, const uint
 
 // ------------------------------------------------------- host-buffer mining
 namespace gbm {
+// Strip items of the count kernels, built on the device from the plan's
+// geometry and size order: the number of 32-row strips of the pair at each
+// position of the order (0 for a pair without targets) ...
+__global__ void strip_counts_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n,
+                                    int32_t *__restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < n; pos += stride) {
+        const PairGeom g = geom[order[pos]];
+        cnt[pos] = g.m > 0 ? (g.n + 31) / 32 : 0;
+    }
+}
+// ... and, from their exclusive scan, every strip's item at its place (pairs
+// largest first, strips in order, the whole 32-row group).
+__global__ void strip_items_kernel(const PairGeom *__restrict__ geom, const int32_t *__restrict__ order, int64_t n,
+                                   const int64_t *__restrict__ off, CountStripItem *__restrict__ items) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pos < n; pos += stride) {
+        const int32_t k = order[pos];
+        const PairGeom g = geom[k];
+        const int ns = g.m > 0 ? (g.n + 31) / 32 : 0;
+        for (int sidx = 0; sidx < ns; ++sidx) items[off[pos] + sidx] = CountStripItem{k, sidx, 0, 32};
+    }
+}
+
+cudaError_t launch_strip_items(const PairGeom *geom, const int32_t *order, int64_t n, int32_t *cnt, int64_t *off,
+                               CountStripItem *items, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    strip_counts_kernel<<<grid, 256, 0, st>>>(geom, order, n, cnt);
+    cudaError_t e = launch_scan(cnt, n, off, st);
+    if (e != cudaSuccess) return e;
+    strip_items_kernel<<<grid, 256, 0, st>>>(geom, order, n, off, items);
+    return cudaGetLastError();
+}
+
 // In place: x[i] -= base (a chunk's sentence offsets, rebased to its first token).
 __global__ void rebase_offsets_kernel(int64_t *x, int64_t count, int64_t base) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
