@@ -71,7 +71,7 @@ struct SoftCtx {
     const int64_t *ssent, *tsent;
     const uchar2 *cnt;     // pair's counts
     const uint8_t *gold;   // pair's gold links (0/1 per cell)
-    float *E;              // pair's expected alignment
+    float *E;              // pair's expected alignment, step-major per strip (soft_e_index)
     float *hvp;            // pair's H u output (backward, may be null)
     SimCol (*colb)[32];    // shared: column constants of the current and previous block [2][col]
     SimRow *rowv;          // shared: constants of the current strip's 32 rows
